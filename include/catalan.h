@@ -1,0 +1,177 @@
+/*
+ * catalan.h -- C ABI of libcatalan, a GB300 (sm_103a) library for exact
+ * Catalan numbers C(n), central binomials C(2n, n) and factorials n!, built on
+ * the two-phase prime-exponent method of arXiv 2601.11621.
+ *
+ *   Phase 1 (Sec. 3.1, Algorithm 1): sieve the primes p <= 2n, compute
+ *   e_p = v_p((2n)!) - 2 v_p(n!) - v_p(n+1) by Legendre's formula (Sec. 2),
+ *   drop e_p = 0 and group the primes by exponent.
+ *   Phase 2 (Sec. 3.2, Algorithm 2): Q_e = BalancedProductTree(G_e),
+ *   P_e = Q_e^e, C(n) = BalancedProductTree({P_e}).
+ *
+ * Conventions shared by every entry point
+ *   - Big integers are arrays of little-endian uint32_t limbs.  Lengths
+ *     written back through *out_len are normalised: the top limb is non-zero;
+ *     zero has length 0 and one is {1} with length 1.  Input lengths may
+ *     include leading zero limbs.
+ *   - Every data pointer (inputs and outputs) is a DEVICE pointer owned by
+ *     the caller, unless the function name ends in _host.  Inputs are read
+ *     only and must not overlap the output.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All work
+ *     is issued on it.  The functions plan on the host from small device
+ *     read-backs, so they return only after the result has been computed;
+ *     the output is complete and visible on `stream` when they return CAT_OK.
+ *   - Scratch memory comes from the context's pool (stream-ordered, cached),
+ *     bounded by the context's HBM budget.
+ *   - Errors: argument errors are reported before any work is issued.  A
+ *     CUDA error is reported as CAT_ECUDA and its text is kept in the
+ *     context (cat_last_error).  After an error the output contents are
+ *     unspecified.
+ *   - Supported n: 0 <= n <= 2^31 - 1, so every prime involved is < 2^32.
+ *   - One context must not be used by two host threads at the same time.
+ */
+#ifndef CATALAN_H
+#define CATALAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CAT_OK = 0,
+    CAT_EINVAL = -1,        /* bad argument (null pointer, n out of range, ...) */
+    CAT_ENOMEM = -2,        /* device allocation failed or HBM budget exceeded  */
+    CAT_ERANGE = -3,        /* output capacity too small; *out_len = needed     */
+    CAT_ENOTINTEGRAL = -4,  /* a prime exponent came out negative (Sec. 6.3)    */
+    CAT_ETIMEOUT = -5,      /* a bounded device wait gave up                    */
+    CAT_ECUDA = -6,         /* CUDA runtime error; see cat_last_error           */
+    CAT_EBUSY = -7          /* request still pending                            */
+} cat_status;
+
+/* Quantity selected by its exponent rule (Sec. 2 and the Sec. 6.3 special
+ * cases): Catalan e = v_p((2n)!) - 2 v_p(n!) - v_p(n+1) over p <= 2n;
+ * central binomial e = v_p((2n)!) - 2 v_p(n!) over p <= 2n;
+ * factorial e = v_p(n!) over p <= n. */
+typedef enum {
+    CAT_CATALAN = 0,
+    CAT_CENTRAL_BINOMIAL = 1,
+    CAT_FACTORIAL = 2
+} cat_kind;
+
+typedef struct cat_ctx cat_ctx;
+
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * scratch the context may hold at once (0 = no cap).  The context owns the
+ * NTT twiddle tables and the scratch pool.  Returns CAT_OK and *out, or an
+ * error (CAT_EINVAL, CAT_ECUDA). */
+int cat_ctx_create(int device, size_t hbm_budget_bytes, cat_ctx **out);
+
+/* Frees the context and everything it owns.  NULL is ignored. */
+void cat_ctx_destroy(cat_ctx *ctx);
+
+/* Text of the last error recorded in ctx ("" if none).  Owned by ctx. */
+const char *cat_last_error(const cat_ctx *ctx);
+
+/* Bytes of scratch currently held / the high-water mark since creation. */
+int cat_ctx_memory(const cat_ctx *ctx, size_t *in_use, size_t *peak);
+
+/* Per-kernel device timing (tracing aid, not part of the method).  When on,
+ * every kernel launch is bracketed by CUDA events on its stream; each entry
+ * point resolves them before returning.  Turning it on or off clears the
+ * totals.  Errors: CAT_EINVAL. */
+int cat_ctx_set_profiling(cat_ctx *ctx, int on);
+
+/* Totals for the i-th kernel name seen since profiling was switched on:
+ * launches, summed device milliseconds and summed algorithmic bytes (the
+ * bytes the launch must read and write at minimum).  *name is owned by ctx.
+ * Returns CAT_ERANGE when i is past the last entry. */
+int cat_ctx_profile(const cat_ctx *ctx, size_t i, const char **name, uint64_t *launches,
+                    double *ms, double *bytes);
+
+/* ------------------------------------------------------------------ Phase 1
+ * Grouped prime factorisation of the quantity (Sec. 3.1, Algorithm 1):
+ * the primes with e_p > 0 in CSR form.  Group g has exponent exps[g]
+ * (ascending) and its primes are primes[offsets[g] .. offsets[g+1]) in
+ * ascending order.  Device arrays are owned by the context and released by
+ * cat_factor_free; host_exps / host_offsets are host copies.
+ * primes_sieved = the number of primes <= the sieve limit (2n, or n for n!). */
+typedef struct {
+    uint64_t num_groups;
+    uint64_t num_primes;
+    uint64_t primes_sieved;
+    uint64_t *exps;          /* device, num_groups      */
+    uint64_t *offsets;       /* device, num_groups + 1  */
+    uint32_t *primes;        /* device, num_primes      */
+    uint64_t *host_exps;     /* host,   num_groups      */
+    uint64_t *host_offsets;  /* host,   num_groups + 1  */
+} cat_factorization;
+
+/* Phase 1 on the device: segmented sieve of the primes <= 2n (n for n!),
+ * Legendre exponents by kind, and grouping by exponent.
+ * Errors: CAT_EINVAL (n >= 2^31, bad kind), CAT_ENOMEM, CAT_ENOTINTEGRAL,
+ * CAT_ECUDA. */
+int catalan_factor(cat_ctx *ctx, uint64_t n, int kind, cat_factorization *out,
+                   void *stream);
+
+/* Releases the arrays of a factorisation returned by catalan_factor.  Work
+ * that reads them must have completed. */
+void cat_factor_free(cat_ctx *ctx, cat_factorization *f);
+
+/* Copies the grouped primes of f (num_primes values) into the caller's
+ * device buffer dst of cap entries.  Errors: CAT_EINVAL, CAT_ERANGE. */
+int cat_factor_copy_primes(cat_ctx *ctx, const cat_factorization *f, uint32_t *dst,
+                           size_t cap, void *stream);
+
+/* ------------------------------------------------------------------ Phase 2
+ * out = a * b.  a has na limbs, b has nb limbs (device).  out has room for
+ * cap limbs; na + nb limbs always suffice.  *out_len = normalised length.
+ * Errors: CAT_EINVAL, CAT_ERANGE (cap < normalised length), CAT_ENOMEM,
+ * CAT_ECUDA.  Operands of up to 2^27 limbs each are supported. */
+int bigint_mul(cat_ctx *ctx, const uint32_t *a, size_t na, const uint32_t *b,
+               size_t nb, uint32_t *out, size_t cap, size_t *out_len, void *stream);
+
+/* out = a^e by left-to-right binary exponentiation ("fast pow",
+ * Algorithm 2).  a^0 = 1.  Errors as bigint_mul. */
+int bigint_pow(cat_ctx *ctx, const uint32_t *a, size_t na, uint64_t e,
+               uint32_t *out, size_t cap, size_t *out_len, void *stream);
+
+/* out = product of the count 32-bit values (device array), by the balanced
+ * product tree of Sec. 3.2.  The empty product is 1.  A result of count
+ * limbs always fits.  Errors as bigint_mul. */
+int product_tree(cat_ctx *ctx, const uint32_t *values, size_t count, uint32_t *out,
+                 size_t cap, size_t *out_len, void *stream);
+
+/* Algorithm 2 on a factorisation: out = prod_g (prod_{p in G_g} p)^exps[g].
+ * The P_e are combined by always multiplying the two shortest, which keeps
+ * every intermediate as short as possible (the aim Sec. 3.2 states for the
+ * balanced tree). */
+int cat_reconstruct(cat_ctx *ctx, const cat_factorization *f, uint32_t *out,
+                    size_t cap, size_t *out_len, void *stream);
+
+/* Upper bound on the limb count of the quantity (from log-gamma with a
+ * safety margin); a buffer of that many limbs always suffices.
+ * Errors: CAT_EINVAL. */
+int cat_bound_limbs(uint64_t n, int kind, size_t *limbs);
+
+/* Phase 1 + Phase 2 end to end for one kind: out = the exact quantity.
+ * Errors: those of catalan_factor and bigint_mul. */
+int cat_exact(cat_ctx *ctx, int kind, uint64_t n, uint32_t *out, size_t cap,
+              size_t *out_len, void *stream);
+
+/* cat_exact for the Catalan number C(n) = (2n)! / (n! (n+1)!). */
+int catalan_exact(cat_ctx *ctx, uint64_t n, uint32_t *out, size_t cap,
+                  size_t *out_len, void *stream);
+
+/* cat_exact writing into a HOST buffer: the device result is copied back
+ * before returning (the copy is part of the call). */
+int cat_exact_host(cat_ctx *ctx, int kind, uint64_t n, uint32_t *host_out,
+                   size_t cap, size_t *out_len, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CATALAN_H */

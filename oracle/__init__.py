@@ -57,6 +57,8 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(ctypes.c_int64))
         L.orc_sieve.argtypes = [u64, u32p, u64]
         L.orc_sieve.restype = u64
+        L.orc_sieve_range.argtypes = [u64, u64, u32p, u64]
+        L.orc_sieve_range.restype = u64
         L.orc_legendre.argtypes = [u64, u64]
         L.orc_legendre.restype = u64
         L.orc_valuation.argtypes = [u64, u64]
@@ -126,6 +128,15 @@ def sieve(limit: int) -> np.ndarray:
     count = L.orc_sieve(limit, None, 0)
     out = np.empty(count, dtype=np.uint32)
     L.orc_sieve(limit, _p32(out), count)
+    return out
+
+
+def sieve_range(lo: int, hi: int) -> np.ndarray:
+    """The primes in [lo, hi], ascending."""
+    L = lib()
+    count = L.orc_sieve_range(lo, hi, None, 0)
+    out = np.empty(count, dtype=np.uint32)
+    L.orc_sieve_range(lo, hi, _p32(out), count)
     return out
 
 

@@ -92,6 +92,49 @@ uint64_t orc_sieve(uint64_t limit, uint32_t *out, uint64_t cap)
     return count;
 }
 
+/* The primes in [lo, hi] (same plain block sieve, started at lo).  Used to
+ * time a bounded slice of a large sieve.  Returns the count; writes at most
+ * cap of them. */
+uint64_t orc_sieve_range(uint64_t lo, uint64_t hi, uint32_t *out, uint64_t cap)
+{
+    if (hi < 2 || hi < lo) return 0;
+    if (lo < 2) lo = 2;
+    uint64_t root = isqrt_u64(hi);
+    unsigned char *small = calloc(root + 1, 1);
+    uint64_t nseeds = 0;
+    uint64_t *seeds = malloc(sizeof(uint64_t) * (root + 1));
+    for (uint64_t i = 2; i <= root; i++) {
+        if (small[i]) continue;
+        seeds[nseeds++] = i;
+        for (uint64_t j = i * i; j <= root; j += i) small[j] = 1;
+    }
+    free(small);
+    const uint64_t block = (uint64_t)1 << 24;
+    unsigned char *seg = malloc(block);
+    uint64_t count = 0;
+    for (uint64_t b = lo; b <= hi; b += block) {
+        uint64_t e = b + block;
+        if (e > hi + 1) e = hi + 1;
+        memset(seg, 0, e - b);
+        for (uint64_t s = 0; s < nseeds; s++) {
+            uint64_t p = seeds[s];
+            uint64_t start = p * p;
+            if (start >= e) break;
+            if (start < b) start = ((b + p - 1) / p) * p;
+            for (uint64_t j = start; j < e; j += p) seg[j - b] = 1;
+        }
+        for (uint64_t x = b; x < e; x++) {
+            if (!seg[x - b]) {
+                if (count < cap) out[count] = (uint32_t)x;
+                count++;
+            }
+        }
+    }
+    free(seg);
+    free(seeds);
+    return count;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Legendre's formula (Sec. 2): v_p(m!) = sum_{k>=1} floor(m / p^k).         */
 /* The loop stops once p^(k+1) would exceed m, so p^k never overflows.       */

@@ -1,0 +1,301 @@
+"""ctypes binding of libcatalan (include/catalan.h).
+
+Same names as the C entry points; each function only converts arguments
+(torch tensors to device pointers, the current torch stream to a
+cudaStream_t) and status codes to exceptions.  Big integers are 1-D int32
+torch tensors holding little-endian uint32 limbs (torch has no general
+uint32 arithmetic; the bits are the same).  There is no CPU fallback: if the
+library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libcatalan.so")
+
+CAT_CATALAN, CAT_CENTRAL_BINOMIAL, CAT_FACTORIAL = 0, 1, 2
+KINDS = {"catalan": CAT_CATALAN, "central_binomial": CAT_CENTRAL_BINOMIAL,
+         "factorial": CAT_FACTORIAL}
+
+STATUS = {0: "CAT_OK", -1: "CAT_EINVAL", -2: "CAT_ENOMEM", -3: "CAT_ERANGE",
+          -4: "CAT_ENOTINTEGRAL", -5: "CAT_ETIMEOUT", -6: "CAT_ECUDA", -7: "CAT_EBUSY"}
+
+EXPORTED = ["cat_ctx_create", "cat_ctx_destroy", "cat_last_error", "cat_ctx_memory",
+            "cat_ctx_set_profiling", "cat_ctx_profile",
+            "catalan_factor", "cat_factor_free", "cat_factor_copy_primes", "bigint_mul", "bigint_pow",
+            "product_tree", "cat_reconstruct", "cat_bound_limbs", "cat_exact",
+            "catalan_exact", "cat_exact_host"]
+
+
+class CatError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Factorization(ctypes.Structure):
+    _fields_ = [("num_groups", ctypes.c_uint64), ("num_primes", ctypes.c_uint64),
+                ("primes_sieved", ctypes.c_uint64),
+                ("exps", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("primes", ctypes.c_void_p),
+                ("host_exps", ctypes.POINTER(ctypes.c_uint64)),
+                ("host_offsets", ctypes.POINTER(ctypes.c_uint64))]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libcatalan.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libcatalan.so not built at {path}; run paper_2601_11621_gb300.build")
+    L = ctypes.CDLL(path)
+    vp, sz, u64, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int
+    szp = ctypes.POINTER(ctypes.c_size_t)
+    L.cat_ctx_create.argtypes = [i32, sz, ctypes.POINTER(vp)]
+    L.cat_ctx_create.restype = i32
+    L.cat_ctx_destroy.argtypes = [vp]
+    L.cat_ctx_destroy.restype = None
+    L.cat_last_error.argtypes = [vp]
+    L.cat_last_error.restype = ctypes.c_char_p
+    L.cat_ctx_memory.argtypes = [vp, szp, szp]
+    L.cat_ctx_memory.restype = i32
+    L.cat_ctx_set_profiling.argtypes = [vp, i32]
+    L.cat_ctx_set_profiling.restype = i32
+    L.cat_ctx_profile.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_char_p),
+                                  ctypes.POINTER(ctypes.c_uint64),
+                                  ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]
+    L.cat_ctx_profile.restype = i32
+    L.catalan_factor.argtypes = [vp, u64, i32, ctypes.POINTER(Factorization), vp]
+    L.catalan_factor.restype = i32
+    L.cat_factor_free.argtypes = [vp, ctypes.POINTER(Factorization)]
+    L.cat_factor_free.restype = None
+    L.cat_factor_copy_primes.argtypes = [vp, ctypes.POINTER(Factorization), vp, sz, vp]
+    L.cat_factor_copy_primes.restype = i32
+    L.bigint_mul.argtypes = [vp, vp, sz, vp, sz, vp, sz, szp, vp]
+    L.bigint_mul.restype = i32
+    L.bigint_pow.argtypes = [vp, vp, sz, u64, vp, sz, szp, vp]
+    L.bigint_pow.restype = i32
+    L.product_tree.argtypes = [vp, vp, sz, vp, sz, szp, vp]
+    L.product_tree.restype = i32
+    L.cat_reconstruct.argtypes = [vp, ctypes.POINTER(Factorization), vp, sz, szp, vp]
+    L.cat_reconstruct.restype = i32
+    L.cat_bound_limbs.argtypes = [u64, i32, szp]
+    L.cat_bound_limbs.restype = i32
+    L.cat_exact.argtypes = [vp, i32, u64, vp, sz, szp, vp]
+    L.cat_exact.restype = i32
+    L.catalan_exact.argtypes = [vp, u64, vp, sz, szp, vp]
+    L.catalan_exact.restype = i32
+    L.cat_exact_host.argtypes = [vp, i32, u64, vp, sz, szp, vp]
+    L.cat_exact_host.restype = i32
+    _lib = L
+    return L
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() else ctypes.c_void_p(0)
+
+
+class Context:
+    """A libcatalan context on one CUDA device (twiddle tables + scratch pool)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        L = load()
+        h = ctypes.c_void_p()
+        rc = L.cat_ctx_create(device, hbm_budget_bytes, ctypes.byref(h))
+        if rc != 0:
+            raise CatError(rc, "cat_ctx_create failed")
+        self.handle = h
+        self.device = device
+
+    def check(self, rc: int):
+        if rc != 0:
+            msg = load().cat_last_error(self.handle) or b""
+            raise CatError(rc, msg.decode(errors="replace"))
+
+    def memory(self) -> tuple[int, int]:
+        a, b = ctypes.c_size_t(), ctypes.c_size_t()
+        self.check(load().cat_ctx_memory(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def set_profiling(self, on: bool):
+        self.check(load().cat_ctx_set_profiling(self.handle, 1 if on else 0))
+
+    def profile(self) -> dict:
+        """{kernel name: (launches, total ms, total algorithmic bytes)}."""
+        out = {}
+        i = 0
+        while True:
+            name = ctypes.c_char_p()
+            n, ms, b = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
+            rc = load().cat_ctx_profile(self.handle, i, ctypes.byref(name), ctypes.byref(n),
+                                        ctypes.byref(ms), ctypes.byref(b))
+            if rc != 0:
+                break
+            out[name.value.decode()] = (n.value, ms.value, b.value)
+            i += 1
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().cat_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _limbs_tensor(x, device):
+    """Accept a torch tensor (int32/uint32 limbs on the device) or a numpy array."""
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.dtype not in (torch.int32,) and str(x.dtype) != "torch.uint32":
+            raise TypeError("limb tensors must be int32 (uint32 bits)")
+        return x.contiguous().view(torch.int32)
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.uint32)).view(np.int32)
+    return torch.from_numpy(a.copy()).to(device)
+
+
+def _empty(n, device):
+    import torch
+    return torch.empty(max(n, 1), dtype=torch.int32, device=device)
+
+
+def cat_bound_limbs(n: int, kind: int = CAT_CATALAN) -> int:
+    out = ctypes.c_size_t()
+    rc = load().cat_bound_limbs(n, kind, ctypes.byref(out))
+    if rc != 0:
+        raise CatError(rc, "cat_bound_limbs")
+    return out.value
+
+
+def bigint_mul(ctx: Context, a, b, stream=None):
+    dev = f"cuda:{ctx.device}"
+    ta, tb = _limbs_tensor(a, dev), _limbs_tensor(b, dev)
+    cap = ta.numel() + tb.numel()
+    out = _empty(cap, dev)
+    n = ctypes.c_size_t()
+    ctx.check(load().bigint_mul(ctx.handle, _ptr(ta), ta.numel(), _ptr(tb), tb.numel(),
+                                _ptr(out), cap, ctypes.byref(n), _stream(stream)))
+    return out[:n.value]
+
+
+def bigint_pow(ctx: Context, a, e: int, stream=None):
+    dev = f"cuda:{ctx.device}"
+    ta = _limbs_tensor(a, dev)
+    na = ta.numel()
+    bits = na * 32
+    cap = max(1, (bits * e) // 32 + 2) if e else 1
+    out = _empty(cap, dev)
+    n = ctypes.c_size_t()
+    ctx.check(load().bigint_pow(ctx.handle, _ptr(ta), na, e, _ptr(out), cap,
+                                ctypes.byref(n), _stream(stream)))
+    return out[:n.value]
+
+
+def product_tree(ctx: Context, values, stream=None):
+    dev = f"cuda:{ctx.device}"
+    tv = _limbs_tensor(values, dev)
+    cap = max(1, tv.numel())
+    out = _empty(cap, dev)
+    n = ctypes.c_size_t()
+    ctx.check(load().product_tree(ctx.handle, _ptr(tv), tv.numel(), _ptr(out), cap,
+                                  ctypes.byref(n), _stream(stream)))
+    return out[:n.value]
+
+
+class FactorResult:
+    """Grouped factorisation (CSR) returned by catalan_factor; owns the
+    device arrays until free() (or garbage collection)."""
+
+    def __init__(self, ctx: Context, f: Factorization):
+        self.ctx = ctx
+        self.f = f
+        ng = f.num_groups
+        self.exps = np.array([f.host_exps[i] for i in range(ng)], dtype=np.uint64)
+        self.offsets = np.array([f.host_offsets[i] for i in range(ng + 1)], dtype=np.uint64)
+        self.num_primes = f.num_primes
+        self.primes_sieved = f.primes_sieved
+
+    def primes(self):
+        """Device copy of the grouped primes as an int32 tensor (uint32 bits)."""
+        out = _empty(self.num_primes, f"cuda:{self.ctx.device}")
+        self.ctx.check(load().cat_factor_copy_primes(self.ctx.handle, ctypes.byref(self.f),
+                                                     _ptr(out), self.num_primes,
+                                                     _stream(None)))
+        return out[:self.num_primes]
+
+    def free(self):
+        if self.f is not None and self.ctx.handle:
+            load().cat_factor_free(self.ctx.handle, ctypes.byref(self.f))
+        self.f = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def catalan_factor(ctx: Context, n: int, kind: int = CAT_CATALAN, stream=None) -> FactorResult:
+    f = Factorization()
+    ctx.check(load().catalan_factor(ctx.handle, n, kind, ctypes.byref(f), _stream(stream)))
+    return FactorResult(ctx, f)
+
+
+def cat_reconstruct(ctx: Context, fact: FactorResult, cap: int, stream=None):
+    out = _empty(cap, f"cuda:{ctx.device}")
+    n = ctypes.c_size_t()
+    ctx.check(load().cat_reconstruct(ctx.handle, ctypes.byref(fact.f), _ptr(out), cap,
+                                     ctypes.byref(n), _stream(stream)))
+    return out[:n.value]
+
+
+def cat_exact(ctx: Context, kind: int, n: int, out=None, stream=None):
+    """The exact quantity as an int32 device tensor of uint32 limbs.  `out`
+    may be a preallocated int32 device tensor of at least cat_bound_limbs."""
+    if out is None:
+        out = _empty(cat_bound_limbs(n, kind), f"cuda:{ctx.device}")
+    m = ctypes.c_size_t()
+    ctx.check(load().cat_exact(ctx.handle, kind, n, _ptr(out), out.numel(),
+                               ctypes.byref(m), _stream(stream)))
+    return out[:m.value]
+
+
+def catalan_exact(ctx: Context, n: int, out=None, stream=None):
+    return cat_exact(ctx, CAT_CATALAN, n, out=out, stream=stream)
+
+
+def cat_exact_host(ctx: Context, kind: int, n: int, out: np.ndarray | None = None,
+                   stream=None) -> np.ndarray:
+    """The exact quantity copied into a host uint32 array (pinned if given)."""
+    if out is None:
+        out = np.empty(cat_bound_limbs(n, kind), dtype=np.uint32)
+    m = ctypes.c_size_t()
+    ctx.check(load().cat_exact_host(ctx.handle, kind, n,
+                                    out.ctypes.data_as(ctypes.c_void_p), out.size,
+                                    ctypes.byref(m), _stream(stream)))
+    return out[:m.value]
+
+
+def to_numpy(t) -> np.ndarray:
+    """Device limb tensor -> host uint32 numpy array."""
+    return t.detach().cpu().numpy().view(np.uint32)

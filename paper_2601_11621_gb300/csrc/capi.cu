@@ -1,0 +1,255 @@
+// capi.cu -- the extern "C" entry points of libcatalan (include/catalan.h).
+// Each converts the internal exceptions into status codes and records the
+// message in the context.
+#include "cat_internal.cuh"
+
+#include <string.h>
+
+#include <new>
+
+struct cat_ctx {
+    cat::Ctx c;
+};
+
+namespace cat {
+void ctx_init(Ctx &c, int device, size_t budget);
+void ctx_release(Ctx &c);
+}  // namespace cat
+
+namespace {
+
+template <typename F>
+int guarded(cat_ctx *ctx, F &&body)
+{
+    try {
+        if (ctx) {
+            ctx->c.last_error.clear();
+            cat::check_cuda(cudaSetDevice(ctx->c.device), "cudaSetDevice");
+        }
+        body();
+        if (ctx) cat::prof_resolve(ctx->c);
+        return CAT_OK;
+    } catch (const cat::Error &e) {
+        if (ctx) {
+            ctx->c.last_error = e.msg;
+            cat::prof_resolve(ctx->c);
+        }
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        if (ctx) ctx->c.last_error = "host allocation failed";
+        return CAT_ENOMEM;
+    } catch (...) {
+        if (ctx) ctx->c.last_error = "unexpected internal error";
+        return CAT_ECUDA;
+    }
+}
+
+inline cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+void copy_out(cat::Ctx &c, const cat::Big &r, uint32_t *out, size_t cap, size_t *out_len,
+              cudaStream_t s)
+{
+    *out_len = r.n;
+    if (r.n > cap) cat::fail(CAT_ERANGE, "output capacity too small");
+    if (r.n)
+        CAT_CUDA(cudaMemcpyAsync(out, r.buf.get(), 4 * r.n, cudaMemcpyDeviceToDevice, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    (void)c;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cat_ctx_create(int device, size_t hbm_budget_bytes, cat_ctx **out)
+{
+    if (!out) return CAT_EINVAL;
+    *out = nullptr;
+    cat_ctx *ctx = new (std::nothrow) cat_ctx;
+    if (!ctx) return CAT_ENOMEM;
+    int rc = guarded(nullptr, [&] { cat::ctx_init(ctx->c, device, hbm_budget_bytes); });
+    if (rc != CAT_OK) {
+        cat::ctx_release(ctx->c);
+        delete ctx;
+        return rc;
+    }
+    *out = ctx;
+    return CAT_OK;
+}
+
+void cat_ctx_destroy(cat_ctx *ctx)
+{
+    if (!ctx) return;
+    cat::ctx_release(ctx->c);
+    delete ctx;
+}
+
+const char *cat_last_error(const cat_ctx *ctx)
+{
+    return ctx ? ctx->c.last_error.c_str() : "";
+}
+
+int cat_ctx_memory(const cat_ctx *ctx, size_t *in_use, size_t *peak)
+{
+    if (!ctx) return CAT_EINVAL;
+    if (in_use) *in_use = ctx->c.in_use;
+    if (peak) *peak = ctx->c.peak;
+    return CAT_OK;
+}
+
+int cat_ctx_set_profiling(cat_ctx *ctx, int on)
+{
+    if (!ctx) return CAT_EINVAL;
+    ctx->c.profiling = on != 0;
+    ctx->c.prof.clear();
+    return CAT_OK;
+}
+
+int cat_ctx_profile(const cat_ctx *ctx, size_t i, const char **name, uint64_t *launches,
+                    double *ms, double *bytes)
+{
+    if (!ctx) return CAT_EINVAL;
+    if (i >= ctx->c.prof.size()) return CAT_ERANGE;
+    const cat::ProfEntry &e = ctx->c.prof[i];
+    if (name) *name = e.name.c_str();
+    if (launches) *launches = e.launches;
+    if (ms) *ms = e.ms;
+    if (bytes) *bytes = e.bytes;
+    return CAT_OK;
+}
+
+int catalan_factor(cat_ctx *ctx, uint64_t n, int kind, cat_factorization *out, void *stream)
+{
+    if (!ctx || !out) return CAT_EINVAL;
+    return guarded(ctx, [&] { cat::factor(ctx->c, n, kind, out, as_stream(stream)); });
+}
+
+void cat_factor_free(cat_ctx *ctx, cat_factorization *f)
+{
+    if (!ctx || !f) return;
+    cudaSetDevice(ctx->c.device);
+    cat::factor_free(ctx->c, f);
+}
+
+int cat_factor_copy_primes(cat_ctx *ctx, const cat_factorization *f, uint32_t *dst,
+                           size_t cap, void *stream)
+{
+    if (!ctx || !f || (cap && !dst)) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        if (f->num_primes > cap) cat::fail(CAT_ERANGE, "destination too small");
+        cudaStream_t s = as_stream(stream);
+        if (f->num_primes)
+            CAT_CUDA(cudaMemcpyAsync(dst, f->primes, 4 * f->num_primes,
+                                     cudaMemcpyDeviceToDevice, s));
+        CAT_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int bigint_mul(cat_ctx *ctx, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
+               uint32_t *out, size_t cap, size_t *out_len, void *stream)
+{
+    if (!ctx || !out_len || (na && !a) || (nb && !b) || (cap && !out)) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        cudaStream_t s = as_stream(stream);
+        cat::Big r;
+        const size_t n = na + nb;
+        r.buf = cat::DevBuf<uint32_t>(ctx->c, n ? n : 1, s);
+        cat::mul_into(ctx->c, a, na, b, nb, r.buf.get(), s);
+        r.n = cat::normalized_length(ctx->c, r.buf.get(), n, s);
+        copy_out(ctx->c, r, out, cap, out_len, s);
+    });
+}
+
+int bigint_pow(cat_ctx *ctx, const uint32_t *a, size_t na, uint64_t e, uint32_t *out,
+               size_t cap, size_t *out_len, void *stream)
+{
+    if (!ctx || !out_len || (na && !a) || (cap && !out)) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        cudaStream_t s = as_stream(stream);
+        cat::Big r = cat::power(ctx->c, a, na, e, s);
+        copy_out(ctx->c, r, out, cap, out_len, s);
+    });
+}
+
+int product_tree(cat_ctx *ctx, const uint32_t *values, size_t count, uint32_t *out,
+                 size_t cap, size_t *out_len, void *stream)
+{
+    if (!ctx || !out_len || (count && !values) || (cap && !out)) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        cudaStream_t s = as_stream(stream);
+        cat::Big r = cat::tree_product(ctx->c, values, count, s);
+        copy_out(ctx->c, r, out, cap, out_len, s);
+    });
+}
+
+int cat_reconstruct(cat_ctx *ctx, const cat_factorization *f, uint32_t *out, size_t cap,
+                    size_t *out_len, void *stream)
+{
+    if (!ctx || !f || !out_len || (cap && !out)) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        cudaStream_t s = as_stream(stream);
+        cat::Big r = cat::reconstruct(ctx->c, f, s);
+        copy_out(ctx->c, r, out, cap, out_len, s);
+    });
+}
+
+int cat_bound_limbs(uint64_t n, int kind, size_t *limbs)
+{
+    if (!limbs || n >= (1ull << 31) || kind < CAT_CATALAN || kind > CAT_FACTORIAL)
+        return CAT_EINVAL;
+    *limbs = cat::bound_limbs(n, kind);
+    return CAT_OK;
+}
+
+int cat_exact(cat_ctx *ctx, int kind, uint64_t n, uint32_t *out, size_t cap,
+              size_t *out_len, void *stream)
+{
+    if (!ctx || !out_len || (cap && !out)) return CAT_EINVAL;
+    if (n >= (1ull << 31) || kind < CAT_CATALAN || kind > CAT_FACTORIAL) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        cudaStream_t s = as_stream(stream);
+        cat_factorization f{};
+        cat::factor(ctx->c, n, kind, &f, s);
+        try {
+            cat::Big r = cat::reconstruct(ctx->c, &f, s);
+            cat::factor_free(ctx->c, &f);
+            copy_out(ctx->c, r, out, cap, out_len, s);
+        } catch (...) {
+            cat::factor_free(ctx->c, &f);
+            throw;
+        }
+    });
+}
+
+int catalan_exact(cat_ctx *ctx, uint64_t n, uint32_t *out, size_t cap, size_t *out_len,
+                  void *stream)
+{
+    return cat_exact(ctx, CAT_CATALAN, n, out, cap, out_len, stream);
+}
+
+int cat_exact_host(cat_ctx *ctx, int kind, uint64_t n, uint32_t *host_out, size_t cap,
+                   size_t *out_len, void *stream)
+{
+    if (!ctx || !out_len || (cap && !host_out)) return CAT_EINVAL;
+    if (n >= (1ull << 31) || kind < CAT_CATALAN || kind > CAT_FACTORIAL) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        cudaStream_t s = as_stream(stream);
+        cat_factorization f{};
+        cat::factor(ctx->c, n, kind, &f, s);
+        cat::Big r;
+        try {
+            r = cat::reconstruct(ctx->c, &f, s);
+        } catch (...) {
+            cat::factor_free(ctx->c, &f);
+            throw;
+        }
+        cat::factor_free(ctx->c, &f);
+        *out_len = r.n;
+        if (r.n > cap) cat::fail(CAT_ERANGE, "output capacity too small");
+        if (r.n)
+            CAT_CUDA(cudaMemcpyAsync(host_out, r.buf.get(), 4 * r.n, cudaMemcpyDeviceToHost, s));
+        CAT_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+}  // extern "C"

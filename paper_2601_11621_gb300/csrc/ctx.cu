@@ -1,0 +1,233 @@
+// ctx.cu -- context, error plumbing, the stream-ordered scratch pool and the
+// NTT twiddle tables.
+#include "cat_internal.cuh"
+
+#include <math.h>
+#include <stdio.h>
+
+#include <string>
+#include <vector>
+
+namespace cat {
+
+void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess) {
+        std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+        if (e == cudaErrorMemoryAllocation) fail(CAT_ENOMEM, m);
+        fail(CAT_ECUDA, m);
+    }
+}
+
+// ------------------------------------------------------------------ memory
+
+namespace {
+struct PoolHolder {
+    cudaMemPool_t pool = nullptr;
+};
+}  // namespace
+
+static cudaMemPool_t g_pools[64] = {};
+
+static cudaMemPool_t pool_for(int device)
+{
+    if (device < 0 || device >= 64) fail(CAT_EINVAL, "device index out of range");
+    if (!g_pools[device]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t p;
+        CAT_CUDA(cudaMemPoolCreate(&p, &props));
+        uint64_t thr = UINT64_MAX;  // keep freed blocks cached in the pool
+        CAT_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr));
+        g_pools[device] = p;
+    }
+    return g_pools[device];
+}
+
+void *dev_alloc(Ctx &c, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) return nullptr;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (c.budget && c.in_use + bytes > c.budget)
+        fail(CAT_ENOMEM, "scratch would exceed the context's HBM budget (" +
+                             std::to_string(c.in_use + bytes) + " > " +
+                             std::to_string(c.budget) + " bytes)");
+    void *p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool_for(c.device), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(CAT_ENOMEM, "device allocation of " + std::to_string(bytes) +
+                             " bytes failed: " + cudaGetErrorString(e));
+    }
+    c.in_use += bytes;
+    if (c.in_use > c.peak) c.peak = c.in_use;
+    return p;
+}
+
+void dev_free(Ctx &c, void *p, size_t bytes, cudaStream_t s)
+{
+    if (!p) return;
+    bytes = (bytes + 255) & ~(size_t)255;
+    cudaFreeAsync(p, s);
+    c.in_use -= bytes;
+}
+
+// --------------------------------------------------------------- profiler
+
+static cudaEvent_t take_event(Ctx &c)
+{
+    if (!c.event_pool.empty()) {
+        cudaEvent_t e = c.event_pool.back();
+        c.event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    CAT_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+int prof_begin(Ctx &c, const char *name, cudaStream_t s)
+{
+    if (!c.profiling) return -1;
+    int idx = -1;
+    for (size_t i = 0; i < c.prof.size(); i++)
+        if (c.prof[i].name == name) { idx = (int)i; break; }
+    if (idx < 0) {
+        c.prof.push_back(ProfEntry{name, 0, 0.0, 0.0});
+        idx = (int)c.prof.size() - 1;
+    }
+    ProfPending p{idx, take_event(c), take_event(c), 0.0};
+    CAT_CUDA(cudaEventRecord(p.a, s));
+    c.pending.push_back(p);
+    return (int)c.pending.size() - 1;
+}
+
+void prof_end(Ctx &c, int token, cudaStream_t s, double bytes)
+{
+    if (token < 0) return;
+    ProfPending &p = c.pending[token];
+    p.bytes = bytes;
+    CAT_CUDA(cudaEventRecord(p.b, s));
+}
+
+void prof_resolve(Ctx &c)
+{
+    for (ProfPending &p : c.pending) {
+        cudaEventSynchronize(p.b);
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            ProfEntry &e = c.prof[p.idx];
+            e.launches++;
+            e.ms += ms;
+            e.bytes += p.bytes;
+        }
+        c.event_pool.push_back(p.a);
+        c.event_pool.push_back(p.b);
+    }
+    c.pending.clear();
+    cudaGetLastError();
+}
+
+// --------------------------------------------------------------- twiddles
+
+static uint32_t find_generator(uint32_t q)
+{
+    std::vector<uint64_t> f;
+    uint64_t m = q - 1;
+    for (uint64_t d = 2; d * d <= m; d++) {
+        if (m % d == 0) {
+            f.push_back(d);
+            while (m % d == 0) m /= d;
+        }
+    }
+    if (m > 1) f.push_back(m);
+    for (uint32_t g = 2;; g++) {
+        bool ok = true;
+        for (uint64_t d : f)
+            if (powmod_u32(g, (q - 1) / d, q) == 1) { ok = false; break; }
+        if (ok) return g;
+    }
+}
+
+// Table layout per (prime i, direction d): entries [0, 2^14) hold w^j and
+// entries [2^14, 2^14 + 2^13) hold w^(j 2^14), where w is the primitive
+// 2^27-th root of unity (d = 0) or its inverse (d = 1).  Each entry is
+// (Montgomery form of the power, that value times q^-1 mod 2^32).
+static void build_twiddles(Ctx &c)
+{
+    std::vector<uint2> h((size_t)kNumPrimes * 2 * kTwPerDir);
+    for (int i = 0; i < kNumPrimes; i++) {
+        uint32_t q = ntt_prime(i), qi = inv32(q);
+        uint32_t g = find_generator(q);
+        uint32_t w = powmod_u32(g, (q - 1) >> kLogMaxNtt, q);
+        if (powmod_u32(w, 1u << (kLogMaxNtt - 1), q) != q - 1)
+            fail(CAT_ECUDA, "twiddle root check failed");
+        for (int d = 0; d < 2; d++) {
+            uint32_t root = d == 0 ? w : powmod_u32(w, (1u << kLogMaxNtt) - 1, q);
+            uint2 *T = &h[((size_t)i * 2 + d) * kTwPerDir];
+            uint64_t x = 1;
+            for (int j = 0; j < kTwLo; j++) {
+                uint32_t m = to_mont_c(x, q);
+                T[j] = make_uint2(m, m * qi);
+                x = x * root % q;
+            }
+            uint32_t step = powmod_u32(root, kTwLo, q);
+            x = 1;
+            for (int j = 0; j < kTwHi; j++) {
+                uint32_t m = to_mont_c(x, q);
+                T[kTwLo + j] = make_uint2(m, m * qi);
+                x = x * step % q;
+            }
+        }
+    }
+    CAT_CUDA(cudaMalloc(&c.twiddles, h.size() * sizeof(uint2)));
+    CAT_CUDA(cudaMemcpy(c.twiddles, h.data(), h.size() * sizeof(uint2),
+                        cudaMemcpyHostToDevice));
+}
+
+void ctx_init(Ctx &c, int device, size_t budget)
+{
+    int ndev = 0;
+    CAT_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) fail(CAT_EINVAL, "no such CUDA device");
+    CAT_CUDA(cudaSetDevice(device));
+    c.device = device;
+    c.budget = budget;
+    CAT_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device));
+    pool_for(device);
+    build_twiddles(c);
+}
+
+void ctx_release(Ctx &c)
+{
+    if (c.twiddles) {
+        cudaSetDevice(c.device);
+        cudaFree(c.twiddles);
+        c.twiddles = nullptr;
+    }
+}
+
+// --------------------------------------------------------------- bounds
+
+// log2 of the quantity from log-gamma, plus a margin of two limbs.  The
+// double-precision error of lgamma at x <= 2^32 is below 1e-5 nats, far inside
+// the margin.
+size_t bound_limbs(uint64_t n, int kind)
+{
+    double x = (double)n, ln;
+    if (kind == CAT_FACTORIAL)
+        ln = lgamma(x + 1.0);
+    else if (kind == CAT_CENTRAL_BINOMIAL)
+        ln = lgamma(2.0 * x + 1.0) - 2.0 * lgamma(x + 1.0);
+    else
+        ln = lgamma(2.0 * x + 1.0) - lgamma(x + 1.0) - lgamma(x + 2.0);
+    if (ln < 0) ln = 0;
+    double bits = ln / log(2.0);
+    return (size_t)(bits / 32.0) + 2;
+}
+
+}  // namespace cat

@@ -1,0 +1,776 @@
+// ntt.cu -- exact big-integer multiplication by a three-prime number-theoretic
+// transform (NTT), Chinese remaindering and carry propagation.
+//
+// This is the multiplication the reconstruction phase spends its time in
+// (Sec. 3.2 and Sec. 6.1: "large-integer multiplications ... consume the
+// majority of the runtime"; Sec. 6.3 names FFT-based multiplication).  The
+// method is the classical one: the limbs of a and b are the coefficients of
+// two polynomials; their cyclic convolution of length L = 2^n >= na + nb is
+// computed modulo three primes q_i (forward transforms, pointwise product,
+// inverse transform), the exact coefficients are recovered by Garner's
+// mixed-radix Chinese remaindering, and their 96-bit values are summed into
+// 32-bit limbs with carry propagation.
+//
+// Transform layout.  The forward transform is an in-place decimation-in-
+// frequency transform (natural order in, bit-reversed order out); the inverse
+// is the matching decimation-in-time transform (bit-reversed in, natural out),
+// so no permutation pass is needed.  A length-2^n transform is split into
+// passes that each run 2^r-point sub-transforms in shared memory (the
+// "four-step" factorisation L = L1 * L2 applied recursively): column passes
+// over strided sub-arrays, each followed by the twiddle w_M^(col * k1), and a
+// final row pass over contiguous runs of 2^r points.  The last forward row
+// pass, the pointwise product and the first inverse row pass are fused.
+// Transforms of up to 2^12 points run entirely inside one thread block,
+// including the remaindering and carries.
+#include "cat_internal.cuh"
+
+#include <algorithm>
+
+namespace cat {
+
+// --------------------------------------------------------------- constants
+
+__constant__ uint32_t c_q[kNumPrimes] = {ntt_prime(0), ntt_prime(1), ntt_prime(2)};
+__constant__ uint32_t c_qinv[kNumPrimes] = {inv32(ntt_prime(0)), inv32(ntt_prime(1)),
+                                            inv32(ntt_prime(2))};
+
+// Garner constants in Montgomery form.
+constexpr uint32_t kQ0 = ntt_prime(0), kQ1 = ntt_prime(1), kQ2 = ntt_prime(2);
+constexpr uint32_t kQinv1 = inv32(kQ1), kQinv2 = inv32(kQ2);
+constexpr uint32_t kInvQ0ModQ1 = to_mont_c(powmod_u32(kQ0 % kQ1, kQ1 - 2, kQ1), kQ1);
+constexpr uint32_t kQ0ModQ2 = to_mont_c(kQ0 % kQ2, kQ2);
+constexpr uint32_t kInvQ0Q1ModQ2 =
+    to_mont_c(powmod_u32(mulmod_u64(kQ0, kQ1, kQ2), kQ2 - 2, kQ2), kQ2);
+static_assert(kQ0 < kQ1 && kQ1 < kQ2, "Garner order assumes q0 < q1 < q2");
+
+// Pointwise scale: Montgomery constant R^2 * 2^-n mod q, so that
+// mont_mul(mont_mul(x, y), scale) = x * y * 2^-n.
+struct Scale {
+    uint32_t c[kNumPrimes];
+};
+
+static Scale make_scale(int n)
+{
+    Scale s;
+    for (int i = 0; i < kNumPrimes; i++) {
+        uint32_t q = ntt_prime(i);
+        uint32_t inv2n = powmod_u32((q + 1) / 2, (uint64_t)n, q);   // 2^-n
+        uint32_t r = to_mont_c(inv2n, q);                            // R 2^-n
+        s.c[i] = to_mont_c(r, q);                                    // R^2 2^-n
+    }
+    return s;
+}
+
+// -------------------------------------------------------------- twiddles
+
+__device__ __forceinline__ const uint2 *tw_table(const uint2 *tw, int p, int dir)
+{
+    return tw + ((size_t)p * 2 + dir) * kTwPerDir;
+}
+
+// w^E for E in [0, 2^27), w the primitive 2^27-th root of the table.
+__device__ __forceinline__ uint2 tw_get(const uint2 *T, uint32_t E, uint32_t q, uint32_t qinv)
+{
+    uint2 lo = __ldg(&T[E & (kTwLo - 1)]);
+    uint2 hi = __ldg(&T[kTwLo + (E >> kTwLoBits)]);
+    uint32_t w = mont_mul_pre(lo.x, hi.x, hi.y, q);
+    return make_uint2(w, w * qinv);
+}
+
+// --------------------------------------------- shared-memory sub-transforms
+
+// In-place DIF on 2^logc interleaved columns of length 2^r, element (row, col)
+// at s[(row << logc) + col].  Stage with half-span h = 2^hl pairs rows
+// (i, i + h) and multiplies the difference by w_{2h}^(i mod h); w_{2h}^j is
+// entry j << (12 - hl) of the table's high part (requires 2h <= 2^13).
+// Caller synchronises before; returns synchronised.
+__device__ void smem_dif(uint32_t *s, int r, int logc, const uint2 *T, uint32_t q)
+{
+    const int C = 1 << logc;
+    const int nb = (1 << (r - 1)) << logc;
+    for (int hl = r - 1; hl >= 0; --hl) {
+        const int h = 1 << hl;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const int col = b & (C - 1);
+            const int jj = b >> logc;
+            const int j = jj & (h - 1);
+            const int row = ((jj >> hl) << (hl + 1)) | j;
+            uint32_t *px = s + (row << logc) + col;
+            uint32_t *py = px + (h << logc);
+            const uint32_t x = *px, y = *py;
+            const uint2 w = __ldg(&T[kTwLo + (j << (12 - hl))]);
+            *px = add_mod(x, y, q);
+            *py = mont_mul_pre(sub_mod(x, y, q), w.x, w.y, q);
+        }
+        __syncthreads();
+    }
+}
+
+// In-place DIT inverse of smem_dif (stages in reverse order, inverse roots,
+// no 1/2 factors).  Caller synchronises before; returns synchronised.
+__device__ void smem_dit(uint32_t *s, int r, int logc, const uint2 *Ti, uint32_t q)
+{
+    const int C = 1 << logc;
+    const int nb = (1 << (r - 1)) << logc;
+    for (int hl = 0; hl < r; ++hl) {
+        const int h = 1 << hl;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const int col = b & (C - 1);
+            const int jj = b >> logc;
+            const int j = jj & (h - 1);
+            const int row = ((jj >> hl) << (hl + 1)) | j;
+            uint32_t *px = s + (row << logc) + col;
+            uint32_t *py = px + (h << logc);
+            const uint32_t x = *px;
+            const uint2 w = __ldg(&Ti[kTwLo + (j << (12 - hl))]);
+            const uint32_t t = mont_mul_pre(*py, w.x, w.y, q);
+            *px = add_mod(x, t, q);
+            *py = sub_mod(x, t, q);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------- column passes
+
+struct ColArgs {
+    uint32_t *data;        // prime p's array at data + p * pstride
+    size_t pstride;
+    int m;                 // block size 2^m (the sub-problem this pass splits)
+    int r;                 // rows 2^r (sub-transform length of this pass)
+    int logc;              // columns per thread block 2^logc
+    const uint32_t *src;   // first forward pass: limb source (else null)
+    size_t src_tstride;    // limbs between consecutive transforms' sources
+    size_t src_len;        // valid limbs per transform (rest are zero)
+    const uint2 *tw;
+};
+
+// Forward column pass: sub-transform over rows (stride S = 2^(m-r)) for
+// 2^logc consecutive columns of one block, then element (row, col) is
+// multiplied by w_M^(col * bitrev(row)).
+__global__ void ntt_col_fwd(ColArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    const int p = blockIdx.y;
+    const uint32_t q = c_q[p], qinv = c_qinv[p];
+    const int R = 1 << a.r, C = 1 << a.logc;
+    const int slog = a.m - a.r;
+    const size_t S = (size_t)1 << slog;
+    const size_t groups = S >> a.logc;
+    const size_t blk = blockIdx.x / groups;
+    const size_t col0 = (blockIdx.x % groups) << a.logc;
+    uint32_t *base = a.data + p * a.pstride + (blk << a.m);
+    const int total = R * C;
+    if (a.src) {
+        const uint32_t *src = a.src + blk * a.src_tstride;
+        for (int v = threadIdx.x; v < total; v += blockDim.x) {
+            const size_t idx = (size_t)(v >> a.logc) * S + col0 + (v & (C - 1));
+            sm[v] = idx < a.src_len ? reduce32(src[idx], q) : 0u;
+        }
+    } else {
+        for (int v = threadIdx.x; v < total; v += blockDim.x) {
+            const size_t idx = (size_t)(v >> a.logc) * S + col0 + (v & (C - 1));
+            sm[v] = base[idx];
+        }
+    }
+    __syncthreads();
+    const uint2 *T = tw_table(a.tw, p, 0);
+    smem_dif(sm, a.r, a.logc, T, q);
+    for (int v = threadIdx.x; v < total; v += blockDim.x) {
+        const int row = v >> a.logc;
+        const uint32_t gcol = (uint32_t)(col0 + (v & (C - 1)));
+        const uint32_t k1 = bitrev((uint32_t)row, a.r);
+        uint32_t x = sm[v];
+        const uint32_t E = (gcol * k1) << (kLogMaxNtt - a.m);
+        if (E) {
+            const uint2 w = tw_get(T, E, q, qinv);
+            x = mont_mul_pre(x, w.x, w.y, q);
+        }
+        base[(size_t)row * S + gcol] = x;
+    }
+}
+
+// Inverse column pass: undo the twiddle, then the DIT sub-transform.
+__global__ void ntt_col_inv(ColArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    const int p = blockIdx.y;
+    const uint32_t q = c_q[p], qinv = c_qinv[p];
+    const int R = 1 << a.r, C = 1 << a.logc;
+    const int slog = a.m - a.r;
+    const size_t S = (size_t)1 << slog;
+    const size_t groups = S >> a.logc;
+    const size_t blk = blockIdx.x / groups;
+    const size_t col0 = (blockIdx.x % groups) << a.logc;
+    uint32_t *base = a.data + p * a.pstride + (blk << a.m);
+    const int total = R * C;
+    const uint2 *Ti = tw_table(a.tw, p, 1);
+    for (int v = threadIdx.x; v < total; v += blockDim.x) {
+        const int row = v >> a.logc;
+        const uint32_t gcol = (uint32_t)(col0 + (v & (C - 1)));
+        const uint32_t k1 = bitrev((uint32_t)row, a.r);
+        uint32_t x = base[(size_t)row * S + gcol];
+        const uint32_t E = (gcol * k1) << (kLogMaxNtt - a.m);
+        if (E) {
+            const uint2 w = tw_get(Ti, E, q, qinv);
+            x = mont_mul_pre(x, w.x, w.y, q);
+        }
+        sm[v] = x;
+    }
+    __syncthreads();
+    smem_dit(sm, a.r, a.logc, Ti, q);
+    for (int v = threadIdx.x; v < total; v += blockDim.x) {
+        const size_t idx = (size_t)(v >> a.logc) * S + col0 + (v & (C - 1));
+        base[idx] = sm[v];
+    }
+}
+
+// ------------------------------------------------------------ row pass
+
+enum { PAIR_ADJACENT = 0, PAIR_SQUARE = 1, PAIR_FIRST_TWO = 2 };
+
+struct RowArgs {
+    const uint32_t *F;  // forward data after the column passes
+    size_t fpstride;
+    uint32_t *G;        // products (transform domain, then inverse rows)
+    size_t gpstride;
+    int n;              // log2 L
+    int r;              // row length 2^r
+    int mode;           // which transforms product k multiplies
+    const uint2 *tw;
+    Scale scale;
+};
+
+// Last forward pass of both operands, pointwise product and first inverse
+// pass, on one contiguous row of 2^r points of product k.
+__global__ void ntt_row_mul(RowArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    const int p = blockIdx.y;
+    const uint32_t q = c_q[p], qinv = c_qinv[p];
+    const int R = 1 << a.r;
+    const size_t rows = (size_t)1 << (a.n - a.r);
+    const size_t k = blockIdx.x / rows;
+    const size_t row = blockIdx.x % rows;
+    size_t ta, tb;
+    if (a.mode == PAIR_ADJACENT) { ta = 2 * k; tb = 2 * k + 1; }
+    else if (a.mode == PAIR_SQUARE) { ta = k; tb = k; }
+    else { ta = 0; tb = 1; }
+    const uint32_t *fa = a.F + p * a.fpstride + (ta << a.n) + row * R;
+    const uint32_t *fb = a.F + p * a.fpstride + (tb << a.n) + row * R;
+    const uint2 *T = tw_table(a.tw, p, 0);
+    const uint2 *Ti = tw_table(a.tw, p, 1);
+    uint32_t *Z = sm + 2 * R;
+    const uint32_t sc = a.scale.c[p];
+    if (a.mode == PAIR_SQUARE) {
+        for (int i = threadIdx.x; i < R; i += blockDim.x) sm[i] = fa[i];
+        __syncthreads();
+        smem_dif(sm, a.r, 0, T, q);
+        for (int i = threadIdx.x; i < R; i += blockDim.x) {
+            const uint32_t x = sm[i];
+            Z[i] = mont_mul(mont_mul(x, x, q, qinv), sc, q, qinv);
+        }
+    } else {
+        for (int i = threadIdx.x; i < R; i += blockDim.x) {
+            sm[2 * i] = fa[i];
+            sm[2 * i + 1] = fb[i];
+        }
+        __syncthreads();
+        smem_dif(sm, a.r, 1, T, q);
+        for (int i = threadIdx.x; i < R; i += blockDim.x)
+            Z[i] = mont_mul(mont_mul(sm[2 * i], sm[2 * i + 1], q, qinv), sc, q, qinv);
+    }
+    __syncthreads();
+    smem_dit(Z, a.r, 0, Ti, q);
+    uint32_t *g = a.G + p * a.gpstride + (k << a.n) + row * R;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) g[i] = Z[i];
+}
+
+// ----------------------------------------------- remaindering and carries
+
+// Garner: the coefficient c < q0 q1 q2 with c = r_i mod q_i, as three words.
+__device__ __forceinline__ void crt3(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t &c0,
+                                     uint32_t &c1, uint32_t &c2)
+{
+    const uint32_t x0 = r0;
+    const uint32_t x1 = mont_mul(sub_mod(r1, x0, kQ1), kInvQ0ModQ1, kQ1, kQinv1);
+    uint32_t t = sub_mod(r2, x0, kQ2);
+    t = sub_mod(t, mont_mul(x1, kQ0ModQ2, kQ2, kQinv2), kQ2);
+    const uint32_t x2 = mont_mul(t, kInvQ0Q1ModQ2, kQ2, kQinv2);
+    const uint64_t y = (uint64_t)kQ1 * x2 + x1;                 // < q1 q2
+    const uint64_t lo = (uint64_t)kQ0 * (uint32_t)y + x0;
+    const uint64_t hi = (uint64_t)kQ0 * (uint32_t)(y >> 32) + (lo >> 32);
+    c0 = (uint32_t)lo;
+    c1 = (uint32_t)hi;
+    c2 = (uint32_t)(hi >> 32);
+}
+
+// Carry maps: for a run of limbs, the carry out as a function of the carry
+// in c in {0,1,2,3}, packed two bits per entry.  Composition is associative,
+// so runs combine by a parallel scan.
+constexpr uint32_t kMapId = 0xE4u;  // c -> c
+
+__device__ __forceinline__ uint32_t map_at(uint32_t m, uint32_t c) { return (m >> (2 * c)) & 3u; }
+
+// (f o g)(c) = f(g(c))
+__device__ __forceinline__ uint32_t map_compose(uint32_t f, uint32_t g)
+{
+    uint32_t r = 0;
+#pragma unroll
+    for (uint32_t c = 0; c < 4; c++) r |= map_at(f, map_at(g, c)) << (2 * c);
+    return r;
+}
+
+// Exclusive scan of maps over the threads of the block, in thread order:
+// returns f_{t-1} o ... o f_0 for thread t, and the whole block's composition
+// through *total.  wsm holds 32 words.  Synchronises internally.
+__device__ uint32_t block_map_scan(uint32_t f, uint32_t *wsm, uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    uint32_t inc = f;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc = map_compose(inc, o);
+    }
+    __syncthreads();
+    if (lane == 31) wsm[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < nw ? wsm[lane] : kMapId;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w = map_compose(w, o);
+        }
+        wsm[lane] = w;
+    }
+    __syncthreads();
+    uint32_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) ex = kMapId;
+    const uint32_t before = wid > 0 ? wsm[wid - 1] : kMapId;
+    *total = wsm[nw - 1];
+    return map_compose(ex, before);
+}
+
+constexpr int kLimbsPerThread = 8;
+
+// Limb sums and carries for one tile.  cw0/cw1/cw2 hold the three words of
+// the coefficients j = -2 .. tile_len-1 of the tile at index j + 2 (the two
+// halo coefficients precede the tile; they are zero at the product's start).
+// Limb j of the tile is cw0[j] + cw1[j-1] + cw2[j-2] plus carries.  Writes
+// limbs j < out_count to out; returns the tile's carry map in *tile_map
+// (valid in every thread).  The tile's own carry-in is assumed 0.
+__device__ void tile_carry(const uint32_t *cw0, const uint32_t *cw1, const uint32_t *cw2,
+                           int tile_len, uint32_t *out, long out_count, uint32_t *wsm,
+                           uint32_t *tile_map)
+{
+    const int j0 = threadIdx.x * kLimbsPerThread;
+    uint32_t limb[kLimbsPerThread];
+    uint32_t carry = 0;
+    uint32_t f = kMapId;
+    if (j0 < tile_len) {
+#pragma unroll
+        for (int i = 0; i < kLimbsPerThread; i++) {
+            const int j = j0 + i;
+            uint64_t v = 0;
+            if (j < tile_len)
+                v = (uint64_t)cw0[j + 2] + cw1[j + 1] + cw2[j] + carry;
+            else
+                v = carry;
+            limb[i] = (uint32_t)v;
+            carry = (uint32_t)(v >> 32);
+        }
+        bool ones = true;
+#pragma unroll
+        for (int i = 1; i < kLimbsPerThread; i++) ones = ones && limb[i] == 0xffffffffu;
+        f = 0;
+#pragma unroll
+        for (uint32_t c = 0; c < 4; c++) {
+            const uint32_t o = carry + ((c > 0 && ones && limb[0] >= 0u - c) ? 1u : 0u);
+            f |= o << (2 * c);
+        }
+    }
+    uint32_t total;
+    const uint32_t ex = block_map_scan(f, wsm, &total);
+    *tile_map = total;
+    if (j0 < tile_len) {
+        uint32_t c = map_at(ex, 0);
+#pragma unroll
+        for (int i = 0; i < kLimbsPerThread; i++) {
+            const uint64_t v = (uint64_t)limb[i] + c;
+            limb[i] = (uint32_t)v;
+            c = (uint32_t)(v >> 32);
+        }
+#pragma unroll
+        for (int i = 0; i < kLimbsPerThread; i++)
+            if (j0 + i < tile_len && j0 + i < out_count) out[j0 + i] = limb[i];
+    }
+}
+
+constexpr int kTileThreads = 256;
+constexpr int kTile = kTileThreads * kLimbsPerThread;  // 2048 limbs
+
+struct CrtArgs {
+    const uint32_t *G;  // inverse-transformed residues [prime][product][L]
+    size_t gpstride;
+    int n;              // log2 L
+    uint32_t *out;      // product k at out + k * out_tstride
+    size_t out_tstride;
+    size_t out_len;     // limbs written per product (<= L)
+    uint8_t *tile_maps; // [product][tiles]
+};
+
+__global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
+{
+    __shared__ uint32_t cw[3][kTile + 2];
+    __shared__ uint32_t wsm[32];
+    const size_t tiles = ((size_t)1 << a.n) / kTile;
+    const size_t k = blockIdx.x / tiles;
+    const size_t t = blockIdx.x % tiles;
+    const long j0 = (long)(t * kTile);
+    const uint32_t *g0 = a.G + (k << a.n);
+    for (int i = threadIdx.x; i < kTile + 2; i += blockDim.x) {
+        const long j = j0 + i - 2;
+        uint32_t c0 = 0, c1 = 0, c2 = 0;
+        if (j >= 0) crt3(g0[j], g0[a.gpstride + j], g0[2 * a.gpstride + j], c0, c1, c2);
+        cw[0][i] = c0;
+        cw[1][i] = c1;
+        cw[2][i] = c2;
+    }
+    __syncthreads();
+    const long remaining = (long)a.out_len - j0;
+    uint32_t map;
+    tile_carry(cw[0], cw[1], cw[2], kTile, a.out + k * a.out_tstride + j0, remaining, wsm, &map);
+    if (threadIdx.x == 0) a.tile_maps[blockIdx.x] = (uint8_t)map;
+}
+
+// Carry into each tile: a scan of the tile maps of one product (one block).
+__global__ void __launch_bounds__(1024) carry_tile_scan(uint8_t *tile_maps, size_t tiles)
+{
+    __shared__ uint32_t wsm[32];
+    uint8_t *m = tile_maps + blockIdx.x * tiles;
+    uint32_t run = 0;  // carry into the current chunk
+    for (size_t base = 0; base < tiles; base += blockDim.x) {
+        const size_t i = base + threadIdx.x;
+        const uint32_t f = i < tiles ? m[i] : kMapId;
+        uint32_t total;
+        const uint32_t ex = block_map_scan(f, wsm, &total);
+        __syncthreads();
+        if (i < tiles) m[i] = (uint8_t)map_at(ex, run);  // now the tile's carry-in
+        run = map_at(total, run);
+        __syncthreads();
+    }
+}
+
+// Add each tile's carry-in to its first limbs (rarely more than one).
+__global__ void carry_fix(const uint8_t *tile_cin, size_t tiles_total, size_t tiles, int n,
+                          uint32_t *out, size_t out_tstride, size_t out_len)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tiles_total) return;
+    uint32_t c = tile_cin[t];
+    if (!c) return;
+    const size_t k = t / tiles, tt = t % tiles;
+    uint32_t *o = out + k * out_tstride;
+    size_t j = tt * kTile;
+    const size_t end = std::min(j + kTile, out_len);
+    for (; c && j < end; j++) {
+        const uint64_t v = (uint64_t)o[j] + c;
+        o[j] = (uint32_t)v;
+        c = (uint32_t)(v >> 32);
+    }
+}
+
+// ------------------------------------------ whole product in one block
+
+struct FusedArgs {
+    const uint32_t *A;
+    size_t a_tstride, a_len;
+    const uint32_t *B;  // null: square A
+    size_t b_tstride, b_len;
+    uint32_t *out;
+    size_t out_tstride, out_len;
+    int n;              // log2 L, L <= 4096
+    const uint2 *tw;
+    Scale scale;
+};
+
+constexpr int kFusedMaxLog = 12;
+constexpr int kFusedThreads = 512;
+
+// One product per block: three forward/pointwise/inverse rounds (one per
+// prime) in shared memory, then remaindering and carries over one tile.
+__global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    __shared__ uint32_t wsm[32];
+    // layout (words): residues R0 [0,L) R1 [L,2L) R2 [2L,3L); raw A shares
+    // R2's space (it is last read before R2 is written), raw B [3L,4L),
+    // transform pair XY [4L,6L).  After the three rounds the remaindered
+    // words (3 (L+2)) go to [3L, 6L+6).
+    const int L = 1 << a.n;
+    uint32_t *Rr[3] = {sm, sm + L, sm + 2 * L};
+    uint32_t *rawA = sm + 2 * L;
+    uint32_t *rawB = sm + 3 * L;
+    uint32_t *XY = sm + 4 * L;
+    const size_t k = blockIdx.x;
+    const uint32_t *ga = a.A + k * a.a_tstride;
+    const uint32_t *gb = a.B ? a.B + k * a.b_tstride : nullptr;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        rawA[i] = (size_t)i < a.a_len ? ga[i] : 0u;
+        rawB[i] = (gb && (size_t)i < a.b_len) ? gb[i] : 0u;
+    }
+    __syncthreads();
+    for (int p = 0; p < kNumPrimes; p++) {
+        const uint32_t q = c_q[p], qinv = c_qinv[p];
+        const uint2 *T = tw_table(a.tw, p, 0);
+        const uint2 *Ti = tw_table(a.tw, p, 1);
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            XY[2 * i] = reduce32(rawA[i], q);
+            XY[2 * i + 1] = reduce32(gb ? rawB[i] : rawA[i], q);
+        }
+        __syncthreads();
+        if (a.n > 0) smem_dif(XY, a.n, 1, T, q);
+        uint32_t *Z = Rr[p];
+        for (int i = threadIdx.x; i < L; i += blockDim.x)
+            Z[i] = mont_mul(mont_mul(XY[2 * i], XY[2 * i + 1], q, qinv), a.scale.c[p], q, qinv);
+        __syncthreads();
+        if (a.n > 0) smem_dit(Z, a.n, 0, Ti, q);
+    }
+    uint32_t *cw0 = sm + 3 * L, *cw1 = cw0 + (L + 2), *cw2 = cw1 + (L + 2);
+    for (int i = threadIdx.x; i < L + 2; i += blockDim.x) {
+        uint32_t c0 = 0, c1 = 0, c2 = 0;
+        if (i >= 2) crt3(Rr[0][i - 2], Rr[1][i - 2], Rr[2][i - 2], c0, c1, c2);
+        cw0[i] = c0;
+        cw1[i] = c1;
+        cw2[i] = c2;
+    }
+    __syncthreads();
+    uint32_t map;
+    tile_carry(cw0, cw1, cw2, L, a.out + k * a.out_tstride, (long)a.out_len, wsm, &map);
+}
+
+// ------------------------------------------------------------ host side
+
+struct NttPlan {
+    int n = 0;
+    int ncol = 0;
+    int rcol[3] = {0, 0, 0};
+    int rrow = 0;
+};
+
+static NttPlan make_plan(int n)
+{
+    NttPlan P;
+    P.n = n;
+    P.rrow = std::min(12, n - 4);
+    int rem = n - P.rrow;
+    P.ncol = (rem + 9) / 10;
+    for (int i = 0; i < P.ncol; i++) {
+        P.rcol[i] = rem / (P.ncol - i);
+        rem -= P.rcol[i];
+    }
+    std::sort(P.rcol, P.rcol + P.ncol, [](int x, int y) { return x > y; });
+    return P;
+}
+
+template <typename K>
+static void set_smem(K kernel, size_t bytes)
+{
+    if (bytes > 48 * 1024)
+        CAT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)bytes));
+}
+
+static constexpr int kColLogC = 4;
+static constexpr int kColThreads = 256;
+static constexpr int kRowThreads = 512;
+
+static void col_pass(Ctx &c, bool fwd, uint32_t *data, size_t pstride, size_t total, int m,
+                     int r, const uint32_t *src, size_t src_tstride, size_t src_len,
+                     cudaStream_t s)
+{
+    ColArgs a;
+    a.data = data;
+    a.pstride = pstride;
+    a.m = m;
+    a.r = r;
+    a.logc = kColLogC;
+    a.src = src;
+    a.src_tstride = src_tstride;
+    a.src_len = src_len;
+    a.tw = c.twiddles;
+    const size_t ctas = total >> (r + kColLogC);
+    const size_t smem = ((size_t)1 << (r + kColLogC)) * sizeof(uint32_t);
+    dim3 grid((unsigned)ctas, kNumPrimes);
+    // algorithmic bytes: every point of the three prime arrays read and
+    // written once (the first forward pass reads limbs instead)
+    double bytes = 24.0 * (double)total;
+    if (src) bytes = 12.0 * (double)total + 4.0 * (double)src_len * (double)(total >> m);
+    const int tok = prof_begin(c, fwd ? (src ? "ntt_col_fwd_first" : "ntt_col_fwd") : "ntt_col_inv", s);
+    if (fwd) {
+        set_smem(ntt_col_fwd, smem);
+        ntt_col_fwd<<<grid, kColThreads, smem, s>>>(a);
+    } else {
+        set_smem(ntt_col_inv, smem);
+        ntt_col_inv<<<grid, kColThreads, smem, s>>>(a);
+    }
+    CAT_LAUNCH(fwd ? "ntt_col_fwd" : "ntt_col_inv");
+    prof_end(c, tok, s, bytes);
+}
+
+// One operand source of a batched product.
+struct Operand {
+    const uint32_t *p;
+    size_t tstride;  // limbs between consecutive transforms (for batches)
+    size_t len;      // valid limbs per transform
+};
+
+// Batched products through the multi-pass transform, L = 2^n > 2^12.
+//  mode PAIR_ADJACENT: nprod products of transforms (2k, 2k+1) of `x`
+//                      (2 nprod transforms, tstride apart);
+//  mode PAIR_FIRST_TWO: one product of x and y;
+//  mode PAIR_SQUARE:   nprod squares of x's transforms.
+static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, Operand y,
+                              uint32_t *out, size_t out_tstride, size_t out_len,
+                              cudaStream_t s)
+{
+    const NttPlan P = make_plan(n);
+    const size_t L = (size_t)1 << n;
+    const size_t ntf = mode == PAIR_ADJACENT ? 2 * nprod : (mode == PAIR_SQUARE ? nprod : 2);
+    const size_t fp = ntf * L;
+    DevBuf<uint32_t> F(c, fp * kNumPrimes, s);
+    // forward column passes
+    if (mode == PAIR_FIRST_TWO) {
+        col_pass(c, true, F.get(), fp, L, n, P.rcol[0], x.p, 0, x.len, s);
+        col_pass(c, true, F.get() + L, fp, L, n, P.rcol[0], y.p, 0, y.len, s);
+    } else {
+        col_pass(c, true, F.get(), fp, fp, n, P.rcol[0], x.p, x.tstride, x.len, s);
+    }
+    int m = n - P.rcol[0];
+    for (int i = 1; i < P.ncol; i++) {
+        col_pass(c, true, F.get(), fp, fp, m, P.rcol[i], nullptr, 0, 0, s);
+        m -= P.rcol[i];
+    }
+    // fused row pass
+    const size_t gp = nprod * L;
+    DevBuf<uint32_t> G(c, gp * kNumPrimes, s);
+    RowArgs ra;
+    ra.F = F.get();
+    ra.fpstride = fp;
+    ra.G = G.get();
+    ra.gpstride = gp;
+    ra.n = n;
+    ra.r = P.rrow;
+    ra.mode = mode;
+    ra.tw = c.twiddles;
+    ra.scale = make_scale(n);
+    const size_t rsmem = ((size_t)3 << P.rrow) * sizeof(uint32_t);
+    set_smem(ntt_row_mul, rsmem);
+    dim3 rgrid((unsigned)(nprod << (n - P.rrow)), kNumPrimes);
+    int tok = prof_begin(c, "ntt_row_mul", s);
+    ntt_row_mul<<<rgrid, kRowThreads, rsmem, s>>>(ra);
+    CAT_LAUNCH("ntt_row_mul");
+    prof_end(c, tok, s, (mode == PAIR_SQUARE ? 24.0 : 36.0) * (double)gp);
+    F.reset();
+    // inverse column passes, reverse order
+    for (int i = P.ncol - 1; i >= 0; i--) {
+        int mi = n;
+        for (int j = 0; j < i; j++) mi -= P.rcol[j];
+        col_pass(c, false, G.get(), gp, gp, mi, P.rcol[i], nullptr, 0, 0, s);
+    }
+    // remaindering and carries
+    const size_t tiles = L / kTile;
+    DevBuf<uint8_t> maps(c, nprod * tiles, s);
+    CrtArgs ca;
+    ca.G = G.get();
+    ca.gpstride = gp;
+    ca.n = n;
+    ca.out = out;
+    ca.out_tstride = out_tstride;
+    ca.out_len = out_len;
+    ca.tile_maps = maps.get();
+    tok = prof_begin(c, "crt_carry_tiles", s);
+    crt_carry_tiles<<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
+    CAT_LAUNCH("crt_carry_tiles");
+    prof_end(c, tok, s, 12.0 * (double)gp + 4.0 * (double)nprod * (double)out_len);
+    tok = prof_begin(c, "carry_tile_scan", s);
+    carry_tile_scan<<<(unsigned)nprod, 1024, 0, s>>>(maps.get(), tiles);
+    CAT_LAUNCH("carry_tile_scan");
+    prof_end(c, tok, s, 2.0 * (double)(nprod * tiles));
+    const size_t tt = nprod * tiles;
+    tok = prof_begin(c, "carry_fix", s);
+    carry_fix<<<(unsigned)((tt + 255) / 256), 256, 0, s>>>(maps.get(), tt, tiles, n, out,
+                                                             out_tstride, out_len);
+    CAT_LAUNCH("carry_fix");
+    prof_end(c, tok, s, (double)tt);
+}
+
+static void ntt_mul_small(Ctx &c, int n, size_t nprod, Operand x, Operand y, bool square,
+                          uint32_t *out, size_t out_tstride, size_t out_len, cudaStream_t s)
+{
+    FusedArgs a;
+    a.A = x.p;
+    a.a_tstride = x.tstride;
+    a.a_len = x.len;
+    a.B = square ? nullptr : y.p;
+    a.b_tstride = y.tstride;
+    a.b_len = y.len;
+    a.out = out;
+    a.out_tstride = out_tstride;
+    a.out_len = out_len;
+    a.n = n;
+    a.tw = c.twiddles;
+    a.scale = make_scale(n);
+    const size_t L = (size_t)1 << n;
+    const size_t smem = (6 * L + 8) * sizeof(uint32_t);
+    set_smem(ntt_mul_fused, smem);
+    const int tok = prof_begin(c, "ntt_mul_fused", s);
+    ntt_mul_fused<<<(unsigned)nprod, kFusedThreads, smem, s>>>(a);
+    CAT_LAUNCH("ntt_mul_fused");
+    prof_end(c, tok, s, 4.0 * (double)nprod * (double)(x.len + (square ? 0 : y.len) + out_len));
+}
+
+static int ceil_log2(size_t x)
+{
+    int n = 0;
+    while (((size_t)1 << n) < x) n++;
+    return n;
+}
+
+// Level products of the fixed-slot product tree: nprod products of adjacent
+// slot-limb nodes of `level`, each written into a 2*slot-limb slot of out.
+void ntt_level(Ctx &c, const uint32_t *level, size_t slot, size_t nprod, uint32_t *out,
+               cudaStream_t s)
+{
+    const int n = ceil_log2(2 * slot);
+    Operand x{level, slot, slot};
+    if (n <= kFusedMaxLog) {
+        Operand a{level, 2 * slot, slot}, b{level + slot, 2 * slot, slot};
+        ntt_mul_small(c, n, nprod, a, b, false, out, 2 * slot, 2 * slot, s);
+    } else {
+        ntt_mul_multipass(c, n, PAIR_ADJACENT, nprod, x, x, out, 2 * slot, 2 * slot, s);
+    }
+}
+
+// out[0 .. na+nb) = a * b by the transform (na + nb <= 2^27).
+void ntt_mul(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
+             uint32_t *out, cudaStream_t s)
+{
+    const size_t len = na + nb;
+    const int n = ceil_log2(len);
+    if (n > kLogMaxNtt) fail(CAT_EINVAL, "operands too long for one transform");
+    const bool square = (a == b && na == nb);
+    Operand x{a, 0, na}, y{b, 0, nb};
+    if (n <= kFusedMaxLog) {
+        ntt_mul_small(c, n, 1, x, y, square, out, 0, len, s);
+    } else if (square) {
+        ntt_mul_multipass(c, n, PAIR_SQUARE, 1, x, x, out, 0, len, s);
+    } else {
+        ntt_mul_multipass(c, n, PAIR_FIRST_TWO, 1, x, y, out, 0, len, s);
+    }
+}
+
+}  // namespace cat

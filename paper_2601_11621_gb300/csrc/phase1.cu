@@ -1,0 +1,551 @@
+// phase1.cu -- Phase 1 of the method on the device (Sec. 3.1, Algorithm 1):
+// the primes up to the sieve limit by a segmented Sieve of Eratosthenes, the
+// exponent of each prime by Legendre's formula (Sec. 2), and the grouping of
+// the primes with e > 0 by exponent into CSR form.
+//
+// Sieve.  Seed primes up to sqrt(limit) come from one thread block.  The odd
+// numbers up to the limit are cut into segments of 2^18 (one bit each, 32 KiB
+// of shared memory per block).  Primes 3..31 are struck word by word from
+// precomputed bit patterns; primes 37..2047 are struck by whole warps (one
+// multiple per lane); larger seed primes by one thread each.  Each segment's
+// bitmap and prime count go to global memory; an exclusive scan of the
+// counts gives every segment its first output position.
+//
+// Exponents.  2n < 2^32, so every term floor(m / p^k) is a 32-bit division;
+// primes above sqrt(m) take one division per factorial.  c_p = v_p(n+1) is
+// the valuation of n+1 at p, which equals the exponent of p in the
+// trial-division factorisation of n+1 of Algorithm 1 step 2.
+//
+// Grouping.  (e, p) pairs are sorted stably by e (least-significant-digit
+// radix sort, pairs with e = 0 dropped in the first pass), so primes stay
+// ascending within each group; group starts are then collected.
+#include "cat_internal.cuh"
+
+#include <algorithm>
+#include <math.h>
+
+namespace cat {
+
+void exclusive_scan_u32(Ctx &c, uint32_t *data, size_t n, cudaStream_t s);
+
+constexpr int kSegBits = 1 << 18;           // odd numbers per segment
+constexpr int kSegWords = kSegBits / 32;    // 8192 words
+constexpr int kSieveThreads = 512;
+constexpr uint32_t kMediumPrime = 37;       // first prime struck by atomics
+constexpr uint32_t kLargePrime = 2048;      // thread-per-prime from here
+
+// ---------------------------------------------------------------- seeds
+
+// All primes <= root (root < 2^16) in ascending order, by one block.
+__global__ void __launch_bounds__(1024) seed_sieve(uint32_t root, uint32_t *seeds,
+                                                   uint32_t *nseeds)
+{
+    __shared__ uint32_t bm[2048];  // bit x set = x composite, x < 65536
+    __shared__ uint32_t pre[1024];
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x) bm[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) atomicOr(&bm[0], 3u);  // 0 and 1
+    for (uint32_t p = 2; p * p <= root; p++)
+        for (uint32_t j = p * p + threadIdx.x * p; j <= root; j += blockDim.x * p)
+            atomicOr(&bm[j >> 5], 1u << (j & 31));
+    __syncthreads();
+    // thread t owns numbers [64 t, 64 t + 64)
+    const uint32_t lo = threadIdx.x * 64;
+    uint32_t w0 = ~bm[2 * threadIdx.x], w1 = ~bm[2 * threadIdx.x + 1];
+    if (lo > root) { w0 = 0; w1 = 0; }
+    else if (lo + 64 > root + 1) {
+        const uint32_t keep = root + 1 - lo;  // 1..64 numbers kept
+        if (keep < 32) { w0 &= (1u << keep) - 1; w1 = 0; }
+        else if (keep < 64) { w1 &= (1u << (keep - 32)) - 1; }
+    }
+    const uint32_t cnt = __popc(w0) + __popc(w1);
+    pre[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint32_t v = threadIdx.x >= (unsigned)off ? pre[threadIdx.x - off] : 0;
+        __syncthreads();
+        pre[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t pos = pre[threadIdx.x] - cnt;
+    for (int b = 0; b < 32; b++)
+        if (w0 >> b & 1) seeds[pos++] = lo + b;
+    for (int b = 0; b < 32; b++)
+        if (w1 >> b & 1) seeds[pos++] = lo + 32 + b;
+    if (threadIdx.x == 1023) *nseeds = pre[1023];
+}
+
+// ------------------------------------------------------------ segments
+
+struct SieveArgs {
+    const uint32_t *seeds;  // ascending primes <= sqrt(limit)
+    uint32_t i_med, i_large, nseeds;  // index ranges: [0,i_med) small (3..31 are
+                                       // patterned), [i_med,i_large) medium, rest large
+    uint32_t imax;          // largest odd index i with 2i+1 <= limit
+    uint32_t *bits;         // out: per segment, bit set = prime
+    uint32_t *counts;       // out: primes per segment
+};
+
+__constant__ uint32_t c_small_primes[10] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
+
+__global__ void __launch_bounds__(kSieveThreads) sieve_segments(SieveArgs a)
+{
+    __shared__ uint32_t bm[kSegWords];
+    __shared__ uint32_t red[kSieveThreads / 32];
+    const uint32_t seg = blockIdx.x;
+    const uint32_t ibase = seg * (uint32_t)kSegBits;  // odd index of bit 0
+    // primes 3..31: bit b of word w is odd number x = 2(ibase + 32 w + b) + 1;
+    // p | x  <=>  ibase + 32 w + b = (p - 1)/2 (mod p)
+    for (int w = threadIdx.x; w < kSegWords; w += blockDim.x) {
+        const uint32_t i0 = ibase + 32u * w;
+        uint32_t m = 0;
+#pragma unroll
+        for (int k = 0; k < 10; k++) {
+            const uint32_t p = c_small_primes[k];
+            const uint32_t b0 = ((p - 1) / 2 + p - i0 % p) % p;
+            uint64_t pat = 0;
+            for (uint32_t b = b0; b < 32; b += p) pat |= 1ull << b;
+            m |= (uint32_t)pat;
+        }
+        bm[w] = m;
+    }
+    __syncthreads();
+    const uint64_t lo_num = 2ull * ibase + 1;  // smallest odd number here
+    // medium primes: one warp per prime, one multiple per lane
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (uint32_t j = a.i_med + wid; j < a.i_large; j += nw) {
+        const uint64_t p = a.seeds[j];
+        uint64_t x0 = (lo_num + p - 1) / p * p;
+        if (x0 < p * p) x0 = p * p;
+        if (!(x0 & 1)) x0 += p;
+        const uint64_t first = (x0 - 1) / 2 - ibase;
+        for (uint64_t i = first + (uint64_t)lane * p; i < (uint64_t)kSegBits; i += 32 * p)
+            atomicOr(&bm[i >> 5], 1u << (i & 31));
+    }
+    // large primes: one thread per prime
+    for (uint32_t j = a.i_large + threadIdx.x; j < a.nseeds; j += blockDim.x) {
+        const uint64_t p = a.seeds[j];
+        uint64_t x0 = (lo_num + p - 1) / p * p;
+        if (x0 < p * p) x0 = p * p;
+        if (!(x0 & 1)) x0 += p;
+        for (uint64_t i = (x0 - 1) / 2 - ibase; i < (uint64_t)kSegBits; i += p)
+            atomicOr(&bm[i >> 5], 1u << (i & 31));
+    }
+    __syncthreads();
+    if (seg == 0 && threadIdx.x == 0) {
+        uint32_t w0 = bm[0];
+        w0 |= 1u;  // 1 is not prime
+        for (int k = 0; k < 10; k++) {  // the pattern struck p itself
+            const uint32_t i = (c_small_primes[k] - 1) / 2;
+            w0 &= ~(1u << i);
+        }
+        bm[0] = w0;
+    }
+    __syncthreads();
+    uint32_t cnt = 0;
+    uint32_t *out = a.bits + (size_t)seg * kSegWords;
+    for (int w = threadIdx.x; w < kSegWords; w += blockDim.x) {
+        uint32_t v = ~bm[w];
+        const uint64_t i0 = (uint64_t)ibase + 32u * w;
+        if (i0 > a.imax) v = 0;
+        else if (i0 + 31 > a.imax) v &= (uint32_t)((2ull << (a.imax - i0)) - 1);
+        out[w] = v;
+        cnt += __popc(v);
+    }
+    for (int off = 16; off; off >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+    if (lane == 0) red[wid] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int k = 0; k < nw; k++) t += red[k];
+        a.counts[seg] = t;
+    }
+}
+
+// ----------------------------------------------------------- exponents
+
+// v_p(m!) = sum_k floor(m / p^k)  (Sec. 2)
+__device__ __forceinline__ uint32_t legendre32(uint32_t m, uint32_t p)
+{
+    uint32_t s = 0;
+    uint64_t pk = p;
+    while (pk <= m) {
+        s += m / (uint32_t)pk;
+        pk *= p;
+    }
+    return s;
+}
+
+__device__ __forceinline__ uint32_t valuation32(uint32_t x, uint32_t p)
+{
+    uint32_t v = 0;
+    while (x % p == 0) {
+        x /= p;
+        v++;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int64_t exponent_of(uint32_t p, uint32_t n, int kind)
+{
+    if (kind == CAT_FACTORIAL) return legendre32(n, p);
+    int64_t e = (int64_t)legendre32(2 * n, p) - 2 * (int64_t)legendre32(n, p);
+    if (kind == CAT_CATALAN) e -= valuation32(n + 1, p);
+    return e;
+}
+
+struct ExpandArgs {
+    const uint32_t *bits;
+    const uint32_t *seg_offsets;  // exclusive scan of the per-segment counts
+    uint32_t n;
+    int kind;
+    int has_two;                  // limit >= 2: item 0 is the prime 2
+    uint64_t *items;              // out: (e << 32) | p, all primes ascending
+    unsigned int *max_e;
+    unsigned int *negative;
+};
+
+// One block per segment: list its primes in order with their exponents.
+__global__ void __launch_bounds__(kSieveThreads) expand_exponents(ExpandArgs a)
+{
+    __shared__ uint32_t pre[kSieveThreads];
+    __shared__ uint32_t red[kSieveThreads / 32];
+    constexpr int kWordsPerThread = kSegWords / kSieveThreads;  // 16
+    const uint32_t seg = blockIdx.x;
+    const uint32_t *bits = a.bits + (size_t)seg * kSegWords + threadIdx.x * kWordsPerThread;
+    uint32_t w[kWordsPerThread];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int k = 0; k < kWordsPerThread; k++) {
+        w[k] = bits[k];
+        cnt += __popc(w[k]);
+    }
+    pre[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int off = 1; off < kSieveThreads; off <<= 1) {
+        const uint32_t v = threadIdx.x >= (unsigned)off ? pre[threadIdx.x - off] : 0;
+        __syncthreads();
+        pre[threadIdx.x] += v;
+        __syncthreads();
+    }
+    size_t pos = (size_t)a.seg_offsets[seg] + pre[threadIdx.x] - cnt + (a.has_two ? 1 : 0);
+    const uint32_t ibase = seg * (uint32_t)kSegBits + threadIdx.x * kWordsPerThread * 32;
+    uint32_t emax = 0, neg = 0;
+#pragma unroll
+    for (int k = 0; k < kWordsPerThread; k++) {
+        uint32_t v = w[k];
+        while (v) {
+            const int b = __ffs(v) - 1;
+            v &= v - 1;
+            const uint32_t p = 2 * (ibase + 32 * k + b) + 1;
+            const int64_t e = exponent_of(p, a.n, a.kind);
+            if (e < 0) neg = 1;
+            const uint32_t eu = e < 0 ? 0u : (uint32_t)e;
+            emax = max(emax, eu);
+            a.items[pos++] = ((uint64_t)eu << 32) | p;
+        }
+    }
+    if (seg == 0 && threadIdx.x == 0 && a.has_two) {
+        const int64_t e = exponent_of(2, a.n, a.kind);
+        if (e < 0) neg = 1;
+        const uint32_t eu = e < 0 ? 0u : (uint32_t)e;
+        emax = max(emax, eu);
+        a.items[0] = ((uint64_t)eu << 32) | 2u;
+    }
+    for (int off = 16; off; off >>= 1) {
+        emax = max(emax, __shfl_down_sync(0xffffffffu, emax, off));
+        neg |= __shfl_down_sync(0xffffffffu, neg, off);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = emax | (neg ? 0x80000000u : 0u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t m = 0, ng = 0;
+        for (int k = 0; k < kSieveThreads / 32; k++) {
+            m = max(m, red[k] & 0x7fffffffu);
+            ng |= red[k] >> 31;
+        }
+        atomicMax(a.max_e, m);
+        if (ng) atomicOr(a.negative, 1u);
+    }
+}
+
+// ------------------------------------------------------- radix grouping
+
+constexpr int kRsThreads = 256;
+constexpr int kRsItems = 16;                     // per thread
+constexpr int kRsTile = kRsThreads * kRsItems;   // 4096
+constexpr int kRsWarps = kRsThreads / 32;
+
+// item (warp w, iteration it, lane) of a tile is element
+// tile*4096 + w*512 + it*32 + lane: warp-major, so warp order = element order.
+__device__ __forceinline__ size_t rs_index(size_t tile, int w, int it, int lane)
+{
+    return tile * kRsTile + (size_t)w * (32 * kRsItems) + it * 32 + lane;
+}
+
+struct RsArgs {
+    const uint64_t *in;
+    uint64_t *out;
+    size_t count;
+    int shift, bits;    // digit = (e >> shift) & (2^bits - 1), e = item >> 32
+    int drop_zero;      // first pass: items with e == 0 are dropped
+    uint32_t *counts;   // [digit][tile]
+    size_t tiles;
+};
+
+__global__ void __launch_bounds__(kRsThreads) rs_histogram(RsArgs a)
+{
+    __shared__ uint32_t h[256];
+    const int nb = 1 << a.bits;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const size_t tile = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int it = 0; it < kRsItems; it++) {
+        const size_t i = rs_index(tile, w, it, lane);
+        if (i < a.count) {
+            const uint32_t e = (uint32_t)(a.in[i] >> 32);
+            if (!(a.drop_zero && e == 0)) atomicAdd(&h[(e >> a.shift) & (nb - 1)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) a.counts[(size_t)d * a.tiles + tile] = h[d];
+}
+
+__global__ void __launch_bounds__(kRsThreads) rs_scatter(RsArgs a)
+{
+    __shared__ uint32_t wh[kRsWarps][256];
+    const int nb = 1 << a.bits;
+    for (int i = threadIdx.x; i < kRsWarps * 256; i += blockDim.x) (&wh[0][0])[i] = 0;
+    __syncthreads();
+    const size_t tile = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t item[kRsItems];
+    uint32_t rank[kRsItems];
+    int digit[kRsItems];
+    for (int it = 0; it < kRsItems; it++) {
+        const size_t i = rs_index(tile, w, it, lane);
+        int d = -1;
+        uint64_t v = 0;
+        if (i < a.count) {
+            v = a.in[i];
+            const uint32_t e = (uint32_t)(v >> 32);
+            if (!(a.drop_zero && e == 0)) d = (int)((e >> a.shift) & (nb - 1));
+        }
+        item[it] = v;
+        digit[it] = d;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (d >= 0 && lane == leader) {
+            base = wh[w][d];
+            wh[w][d] = base + __popc(peers);
+        }
+        base = __shfl_sync(0xffffffffu, base, leader);
+        rank[it] = base + __popc(peers & ((1u << lane) - 1));
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive scan over warps per digit, plus the global digit offset
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) {
+        uint32_t run = a.counts[(size_t)d * a.tiles + tile];
+        for (int k = 0; k < kRsWarps; k++) {
+            const uint32_t c = wh[k][d];
+            wh[k][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int it = 0; it < kRsItems; it++)
+        if (digit[it] >= 0) a.out[wh[w][digit[it]] + rank[it]] = item[it];
+}
+
+// group starts: positions i with e_i != e_{i-1}, appended as (e, i)
+__global__ void group_starts(const uint64_t *items, size_t count, uint64_t *starts,
+                             unsigned int *nstarts, uint32_t *primes)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint64_t v = items[i];
+    primes[i] = (uint32_t)v;
+    const uint32_t e = (uint32_t)(v >> 32);
+    if (i == 0 || (uint32_t)(items[i - 1] >> 32) != e) {
+        const unsigned k = atomicAdd(nstarts, 1u);
+        starts[2 * k] = e;
+        starts[2 * k + 1] = i;
+    }
+}
+
+// ------------------------------------------------------------ host side
+
+static uint64_t isqrt64(uint64_t x)
+{
+    uint64_t r = (uint64_t)sqrtl((long double)x);
+    while (r > 0 && r * r > x) r--;
+    while ((r + 1) * (r + 1) <= x) r++;
+    return r;
+}
+
+void factor(Ctx &c, uint64_t n, int kind, cat_factorization *out, cudaStream_t s)
+{
+    if (n >= (1ull << 31)) fail(CAT_EINVAL, "n must be below 2^31");
+    if (kind < CAT_CATALAN || kind > CAT_FACTORIAL) fail(CAT_EINVAL, "unknown kind");
+    *out = cat_factorization{};
+    const uint64_t limit = kind == CAT_FACTORIAL ? n : 2 * n;
+    std::vector<uint64_t> h_exps, h_offs{0};
+    DevBuf<uint32_t> primes_out;
+    uint64_t sieved = 0, npos = 0;
+    if (limit >= 2) {
+        // seeds
+        const uint64_t root = isqrt64(limit);
+        DevBuf<uint32_t> seeds(c, 8192, s);
+        DevBuf<uint32_t> nseeds(c, 1, s);
+        seed_sieve<<<1, 1024, 0, s>>>((uint32_t)root, seeds.get(), nseeds.get());
+        CAT_LAUNCH("seed_sieve");
+        uint32_t ns = 0;
+        CAT_CUDA(cudaMemcpyAsync(&ns, nseeds.get(), 4, cudaMemcpyDeviceToHost, s));
+        CAT_CUDA(cudaStreamSynchronize(s));
+        std::vector<uint32_t> hs(ns);
+        if (ns)
+            CAT_CUDA(cudaMemcpyAsync(hs.data(), seeds.get(), 4 * ns, cudaMemcpyDeviceToHost, s));
+        CAT_CUDA(cudaStreamSynchronize(s));
+        // odd seeds only for the segment sieve
+        const uint32_t *odd = seeds.get() + (ns > 0 && hs[0] == 2 ? 1 : 0);
+        const uint32_t nodd = ns > 0 ? ns - 1 : 0;
+        uint32_t i_med = 0, i_large = 0;
+        for (uint32_t k = 0; k < nodd; k++) {
+            const uint32_t p = hs[k + 1];
+            if (p < kMediumPrime) i_med = k + 1;
+            if (p < kLargePrime) i_large = k + 1;
+        }
+        // segments over odd indices 0..imax (odd number 2i+1 <= limit)
+        const uint32_t imax = (uint32_t)((limit - 1) / 2);
+        const uint32_t nsegs = imax / kSegBits + 1;
+        DevBuf<uint32_t> bits(c, (size_t)nsegs * kSegWords, s);
+        DevBuf<uint32_t> counts(c, nsegs, s);
+        SieveArgs sa{odd, i_med, i_large, nodd, imax, bits.get(), counts.get()};
+        int tok = prof_begin(c, "sieve_segments", s);
+        sieve_segments<<<nsegs, kSieveThreads, 0, s>>>(sa);
+        CAT_LAUNCH("sieve_segments");
+        prof_end(c, tok, s, 4.0 * (double)nsegs * kSegWords);
+        uint32_t last_count = 0;
+        CAT_CUDA(cudaMemcpyAsync(&last_count, counts.get() + nsegs - 1, 4,
+                                 cudaMemcpyDeviceToHost, s));
+        exclusive_scan_u32(c, counts.get(), nsegs, s);
+        uint32_t last_off = 0;
+        CAT_CUDA(cudaMemcpyAsync(&last_off, counts.get() + nsegs - 1, 4,
+                                 cudaMemcpyDeviceToHost, s));
+        CAT_CUDA(cudaStreamSynchronize(s));
+        const uint64_t nodd_primes = (uint64_t)last_off + last_count;
+        sieved = nodd_primes + 1;  // plus the prime 2
+        // exponents
+        DevBuf<uint64_t> items(c, sieved, s);
+        DevBuf<unsigned int> flags(c, 2, s);
+        CAT_CUDA(cudaMemsetAsync(flags.get(), 0, 8, s));
+        ExpandArgs ea{bits.get(), counts.get(), (uint32_t)n, kind, 1, items.get(),
+                      flags.get(), flags.get() + 1};
+        tok = prof_begin(c, "expand_exponents", s);
+        expand_exponents<<<nsegs, kSieveThreads, 0, s>>>(ea);
+        CAT_LAUNCH("expand_exponents");
+        prof_end(c, tok, s, 4.0 * (double)nsegs * kSegWords + 8.0 * (double)sieved);
+        bits.reset();
+        counts.reset();
+        unsigned int hf[2];
+        CAT_CUDA(cudaMemcpyAsync(hf, flags.get(), 8, cudaMemcpyDeviceToHost, s));
+        CAT_CUDA(cudaStreamSynchronize(s));
+        if (hf[1]) fail(CAT_ENOTINTEGRAL, "a prime exponent is negative");
+        const uint32_t max_e = hf[0];
+        // stable radix sort by e, dropping e = 0
+        int ebits = 0;
+        while (ebits < 32 && (max_e >> ebits)) ebits++;
+        DevBuf<uint64_t> alt(c, sieved, s);
+        uint64_t *src = items.get(), *dst = alt.get();
+        size_t count = sieved;
+        for (int shift = 0, pass = 0; pass == 0 || shift < ebits; pass++) {
+            const int bitsd = std::max(1, std::min(8, ebits - shift));
+            const size_t tiles = (count + kRsTile - 1) / kRsTile;
+            if (tiles == 0) break;
+            const size_t nbins = (size_t)1 << bitsd;
+            DevBuf<uint32_t> cnt(c, nbins * tiles, s);
+            RsArgs ra{src, dst, count, shift, bitsd, pass == 0 ? 1 : 0, cnt.get(), tiles};
+            tok = prof_begin(c, "rs_histogram", s);
+            rs_histogram<<<(unsigned)tiles, kRsThreads, 0, s>>>(ra);
+            CAT_LAUNCH("rs_histogram");
+            prof_end(c, tok, s, 8.0 * (double)count);
+            uint32_t lastc = 0, lasto = 0;
+            CAT_CUDA(cudaMemcpyAsync(&lastc, cnt.get() + nbins * tiles - 1, 4,
+                                     cudaMemcpyDeviceToHost, s));
+            exclusive_scan_u32(c, cnt.get(), nbins * tiles, s);
+            CAT_CUDA(cudaMemcpyAsync(&lasto, cnt.get() + nbins * tiles - 1, 4,
+                                     cudaMemcpyDeviceToHost, s));
+            tok = prof_begin(c, "rs_scatter", s);
+            rs_scatter<<<(unsigned)tiles, kRsThreads, 0, s>>>(ra);
+            CAT_LAUNCH("rs_scatter");
+            prof_end(c, tok, s, 16.0 * (double)count);
+            CAT_CUDA(cudaStreamSynchronize(s));
+            count = (size_t)lasto + lastc;
+            std::swap(src, dst);
+            shift += bitsd;
+            if (ebits == 0) break;
+        }
+        npos = count;
+        if (npos > 0) {
+            primes_out = DevBuf<uint32_t>(c, npos, s);
+            DevBuf<uint64_t> starts(c, 2 * npos, s);
+            DevBuf<unsigned int> nst(c, 1, s);
+            CAT_CUDA(cudaMemsetAsync(nst.get(), 0, 4, s));
+            group_starts<<<(unsigned)((npos + 255) / 256), 256, 0, s>>>(
+                src, npos, starts.get(), nst.get(), primes_out.get());
+            CAT_LAUNCH("group_starts");
+            unsigned int ng = 0;
+            CAT_CUDA(cudaMemcpyAsync(&ng, nst.get(), 4, cudaMemcpyDeviceToHost, s));
+            CAT_CUDA(cudaStreamSynchronize(s));
+            std::vector<uint64_t> hst(2 * (size_t)ng);
+            CAT_CUDA(cudaMemcpyAsync(hst.data(), starts.get(), 16 * (size_t)ng,
+                                     cudaMemcpyDeviceToHost, s));
+            CAT_CUDA(cudaStreamSynchronize(s));
+            std::vector<std::pair<uint64_t, uint64_t>> g(ng);
+            for (size_t k = 0; k < ng; k++) g[k] = {hst[2 * k], hst[2 * k + 1]};
+            std::sort(g.begin(), g.end());
+            h_offs.clear();
+            for (auto &x : g) {
+                h_exps.push_back(x.first);
+                h_offs.push_back(x.second);
+            }
+            h_offs.push_back(npos);
+        }
+    }
+    const size_t ng = h_exps.size();
+    DevBuf<uint64_t> d_exps(c, ng + 1, s), d_offs(c, ng + 1, s);
+    if (!primes_out.get()) primes_out = DevBuf<uint32_t>(c, 1, s);
+    out->host_exps = new uint64_t[ng + 1];
+    out->host_offsets = new uint64_t[ng + 1];
+    for (size_t k = 0; k < ng; k++) out->host_exps[k] = h_exps[k];
+    out->host_exps[ng] = 0;
+    for (size_t k = 0; k <= ng; k++) out->host_offsets[k] = h_offs[k];
+    CAT_CUDA(cudaMemcpyAsync(d_exps.get(), out->host_exps, 8 * (ng + 1),
+                             cudaMemcpyHostToDevice, s));
+    CAT_CUDA(cudaMemcpyAsync(d_offs.get(), out->host_offsets, 8 * (ng + 1),
+                             cudaMemcpyHostToDevice, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    out->num_groups = ng;
+    out->num_primes = npos;
+    out->primes_sieved = sieved;
+    out->exps = d_exps.release();
+    out->offsets = d_offs.release();
+    out->primes = primes_out.release();
+}
+
+void factor_free(Ctx &c, cat_factorization *f)
+{
+    if (!f) return;
+    dev_free(c, f->exps, 8 * (f->num_groups + 1), nullptr);
+    dev_free(c, f->offsets, 8 * (f->num_groups + 1), nullptr);
+    dev_free(c, f->primes, 4 * (f->num_primes ? f->num_primes : 1), nullptr);
+    delete[] f->host_exps;
+    delete[] f->host_offsets;
+    *f = cat_factorization{};
+}
+
+}  // namespace cat

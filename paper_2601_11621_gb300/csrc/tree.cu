@@ -1,0 +1,161 @@
+// tree.cu -- Phase 2 of the method (Sec. 3.2, Algorithm 2): the balanced
+// product tree, binary powering and the final product, as level-synchronous
+// batched multiplications on the device.
+//
+// Product tree.  The leaves (32-bit primes) are combined eight at a time into
+// 8-limb nodes; every further level multiplies adjacent nodes (2i, 2i+1) of a
+// fixed slot size S into slots of 2S limbs (a product of 2^k values below 2^32
+// always fits 2^k limbs), with an odd last node carried up unchanged.  All
+// products of one level are one batched launch: schoolbook (Comba) kernels
+// for small slots, a one-block transform for products up to 2^12 limbs, and
+// the multi-pass transform above.  Nodes of a level hold equally many primes,
+// which is what keeps the tree balanced.
+#include "cat_internal.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace cat {
+
+// comba.cu
+void leaf_level(Ctx &c, const uint32_t *values, size_t count, uint32_t *out, size_t nodes,
+                cudaStream_t s);
+bool comba_level(Ctx &c, const uint32_t *in, size_t slot, size_t nprod, uint32_t *out,
+                 cudaStream_t s);
+// ntt.cu
+void ntt_level(Ctx &c, const uint32_t *level, size_t slot, size_t nprod, uint32_t *out,
+               cudaStream_t s);
+void ntt_mul(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
+             uint32_t *out, cudaStream_t s);
+
+constexpr size_t kLeafSlot = 8;
+constexpr size_t kMaxProductLimbs = (size_t)1 << kLogMaxNtt;
+
+static Big make_one(Ctx &c, cudaStream_t s)
+{
+    Big r;
+    r.buf = DevBuf<uint32_t>(c, 1, s);
+    static const uint32_t one = 1;
+    CAT_CUDA(cudaMemcpyAsync(r.buf.get(), &one, 4, cudaMemcpyHostToDevice, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    r.n = 1;
+    return r;
+}
+
+// Length of x[0..n) after dropping zero top limbs, reading only the top few
+// limbs when they decide it.
+static size_t trim(Ctx &c, const uint32_t *x, size_t n, cudaStream_t s)
+{
+    if (n == 0) return 0;
+    const size_t k = std::min<size_t>(n, 4);
+    uint32_t h[4];
+    CAT_CUDA(cudaMemcpyAsync(h, x + n - k, 4 * k, cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    for (size_t i = k; i-- > 0;)
+        if (h[i]) return n - k + i + 1;
+    return normalized_length(c, x, n - k, s);
+}
+
+void mul_into(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
+              uint32_t *out, cudaStream_t s)
+{
+    if (na == 0 || nb == 0) {
+        if (na + nb) CAT_CUDA(cudaMemsetAsync(out, 0, 4 * (na + nb), s));
+        return;
+    }
+    if (na + nb > kMaxProductLimbs)
+        fail(CAT_EINVAL, "product longer than 2^27 limbs is not supported");
+    ntt_mul(c, a, na, b, nb, out, s);
+}
+
+Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s)
+{
+    if (count == 0) return make_one(c, s);
+    size_t slot = kLeafSlot;
+    size_t nodes = (count + kLeafSlot - 1) / kLeafSlot;
+    DevBuf<uint32_t> cur(c, nodes * slot, s);
+    leaf_level(c, values, count, cur.get(), nodes, s);
+    while (nodes > 1) {
+        const size_t nprod = nodes / 2, odd = nodes & 1, nn = nprod + odd, ns = 2 * slot;
+        DevBuf<uint32_t> nxt(c, nn * ns, s);
+        if (!comba_level(c, cur.get(), slot, nprod, nxt.get(), s))
+            ntt_level(c, cur.get(), slot, nprod, nxt.get(), s);
+        if (odd) {
+            CAT_CUDA(cudaMemcpyAsync(nxt.get() + nprod * ns, cur.get() + (nodes - 1) * slot,
+                                     4 * slot, cudaMemcpyDeviceToDevice, s));
+            CAT_CUDA(cudaMemsetAsync(nxt.get() + nprod * ns + slot, 0, 4 * slot, s));
+        }
+        cur = std::move(nxt);
+        nodes = nn;
+        slot = ns;
+    }
+    Big r;
+    r.n = normalized_length(c, cur.get(), slot, s);
+    r.buf = std::move(cur);
+    return r;
+}
+
+static Big copy_big(Ctx &c, const uint32_t *a, size_t n, cudaStream_t s)
+{
+    Big r;
+    r.buf = DevBuf<uint32_t>(c, n ? n : 1, s);
+    if (n) CAT_CUDA(cudaMemcpyAsync(r.buf.get(), a, 4 * n, cudaMemcpyDeviceToDevice, s));
+    r.n = n;
+    return r;
+}
+
+static Big mul_big(Ctx &c, const Big &x, const Big &y, cudaStream_t s)
+{
+    Big r;
+    const size_t n = x.n + y.n;
+    r.buf = DevBuf<uint32_t>(c, n ? n : 1, s);
+    mul_into(c, x.buf.get(), x.n, y.buf.get(), y.n, r.buf.get(), s);
+    r.n = trim(c, r.buf.get(), n, s);
+    return r;
+}
+
+// a^e, left-to-right binary ("fast pow" of Algorithm 2).  Squarings reuse
+// one forward transform.
+Big power(Ctx &c, const uint32_t *a, size_t na, uint64_t e, cudaStream_t s)
+{
+    na = normalized_length(c, a, na, s);
+    if (e == 0) return make_one(c, s);
+    if (na == 0) return copy_big(c, a, 0, s);
+    Big base = copy_big(c, a, na, s);
+    Big r = copy_big(c, a, na, s);
+    int top = 63;
+    while (!((e >> top) & 1)) top--;
+    for (int bit = top - 1; bit >= 0; bit--) {
+        r = mul_big(c, r, r, s);
+        if ((e >> bit) & 1) r = mul_big(c, r, base, s);
+    }
+    return r;
+}
+
+// Algorithm 2: Q_e by the tree, P_e = Q_e^e, then the P_e combined by
+// repeatedly multiplying the two shortest (equal-length operands meet
+// first, so intermediates stay as short as possible).
+Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s)
+{
+    std::vector<Big> P;
+    for (uint64_t g = 0; g < f->num_groups; g++) {
+        const uint64_t off = f->host_offsets[g], cnt = f->host_offsets[g + 1] - off;
+        Big Q = tree_product(c, f->primes + off, cnt, s);
+        if (f->host_exps[g] == 1)
+            P.push_back(std::move(Q));
+        else
+            P.push_back(power(c, Q.buf.get(), Q.n, f->host_exps[g], s));
+    }
+    if (P.empty()) return make_one(c, s);
+    while (P.size() > 1) {
+        std::sort(P.begin(), P.end(), [](const Big &x, const Big &y) { return x.n > y.n; });
+        Big x = std::move(P.back());
+        P.pop_back();
+        Big y = std::move(P.back());
+        P.pop_back();
+        P.push_back(mul_big(c, x, y, s));
+    }
+    return std::move(P[0]);
+}
+
+}  // namespace cat

@@ -18,3 +18,22 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def cat_lib():
+    """Builds (if stale) and loads libcatalan.so."""
+    from paper_2601_11621_gb300 import build, capi
+    build.build()
+    return capi
+
+
+@pytest.fixture(scope="session")
+def ctx(cat_lib):
+    """A libcatalan context on cuda:0 (GPU tests only)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = cat_lib.Context(0)
+    yield c
+    c.close()

@@ -356,3 +356,11 @@ def test_paper_n_plus_1_and_seed_range(orc):
     n = 2050572903
     assert math.isqrt(2 * n) == 64040
     assert orc.prime_count(64040) == 6418
+
+
+def test_sieve_range_is_a_slice_of_the_sieve(orc):
+    full = orc.sieve((1 << 24) + 100)
+    for lo, hi in [(0, 100), (2, 2), (90, 97), (1_000_000, 1_000_100),
+                   ((1 << 24) - 50, (1 << 24) + 50), (2_999_000, 3_000_000)]:
+        want = full[(full >= lo) & (full <= hi)]
+        assert (orc.sieve_range(lo, hi) == want).all(), (lo, hi)
