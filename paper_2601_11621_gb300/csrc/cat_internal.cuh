@@ -156,6 +156,7 @@ struct Ctx {
     std::string last_error;
     uint2 *twiddles = nullptr;  // [prime][dir][kTwPerDir] (Montgomery w, w q^-1)
     int num_sms = 0;
+    size_t comba_max_slot = 128;  // tree levels with slots up to this use schoolbook
     bool profiling = false;
     std::vector<ProfEntry> prof;
     std::vector<ProfPending> pending;

@@ -4,6 +4,7 @@
 
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include <string>
 #include <vector>
@@ -198,6 +199,7 @@ void ctx_init(Ctx &c, int device, size_t budget)
     c.device = device;
     c.budget = budget;
     CAT_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device));
+    if (const char *e = getenv("CAT_COMBA_MAX_SLOT")) c.comba_max_slot = strtoull(e, nullptr, 10);
     pool_for(device);
     build_twiddles(c);
 }

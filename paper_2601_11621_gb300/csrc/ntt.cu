@@ -77,215 +77,6 @@ __device__ __forceinline__ uint2 tw_get(const uint2 *T, uint32_t E, uint32_t q, 
     return make_uint2(w, w * qinv);
 }
 
-// --------------------------------------------- shared-memory sub-transforms
-
-// In-place DIF on 2^logc interleaved columns of length 2^r, element (row, col)
-// at s[(row << logc) + col].  Stage with half-span h = 2^hl pairs rows
-// (i, i + h) and multiplies the difference by w_{2h}^(i mod h); w_{2h}^j is
-// entry j << (12 - hl) of the table's high part (requires 2h <= 2^13).
-// Caller synchronises before; returns synchronised.
-__device__ void smem_dif(uint32_t *s, int r, int logc, const uint2 *T, uint32_t q)
-{
-    const int C = 1 << logc;
-    const int nb = (1 << (r - 1)) << logc;
-    for (int hl = r - 1; hl >= 0; --hl) {
-        const int h = 1 << hl;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            const int col = b & (C - 1);
-            const int jj = b >> logc;
-            const int j = jj & (h - 1);
-            const int row = ((jj >> hl) << (hl + 1)) | j;
-            uint32_t *px = s + (row << logc) + col;
-            uint32_t *py = px + (h << logc);
-            const uint32_t x = *px, y = *py;
-            const uint2 w = __ldg(&T[kTwLo + (j << (12 - hl))]);
-            *px = add_mod(x, y, q);
-            *py = mont_mul_pre(sub_mod(x, y, q), w.x, w.y, q);
-        }
-        __syncthreads();
-    }
-}
-
-// In-place DIT inverse of smem_dif (stages in reverse order, inverse roots,
-// no 1/2 factors).  Caller synchronises before; returns synchronised.
-__device__ void smem_dit(uint32_t *s, int r, int logc, const uint2 *Ti, uint32_t q)
-{
-    const int C = 1 << logc;
-    const int nb = (1 << (r - 1)) << logc;
-    for (int hl = 0; hl < r; ++hl) {
-        const int h = 1 << hl;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            const int col = b & (C - 1);
-            const int jj = b >> logc;
-            const int j = jj & (h - 1);
-            const int row = ((jj >> hl) << (hl + 1)) | j;
-            uint32_t *px = s + (row << logc) + col;
-            uint32_t *py = px + (h << logc);
-            const uint32_t x = *px;
-            const uint2 w = __ldg(&Ti[kTwLo + (j << (12 - hl))]);
-            const uint32_t t = mont_mul_pre(*py, w.x, w.y, q);
-            *px = add_mod(x, t, q);
-            *py = sub_mod(x, t, q);
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------- column passes
-
-struct ColArgs {
-    uint32_t *data;        // prime p's array at data + p * pstride
-    size_t pstride;
-    int m;                 // block size 2^m (the sub-problem this pass splits)
-    int r;                 // rows 2^r (sub-transform length of this pass)
-    int logc;              // columns per thread block 2^logc
-    const uint32_t *src;   // first forward pass: limb source (else null)
-    size_t src_tstride;    // limbs between consecutive transforms' sources
-    size_t src_len;        // valid limbs per transform (rest are zero)
-    const uint2 *tw;
-};
-
-// Forward column pass: sub-transform over rows (stride S = 2^(m-r)) for
-// 2^logc consecutive columns of one block, then element (row, col) is
-// multiplied by w_M^(col * bitrev(row)).
-__global__ void ntt_col_fwd(ColArgs a)
-{
-    extern __shared__ uint32_t sm[];
-    const int p = blockIdx.y;
-    const uint32_t q = c_q[p], qinv = c_qinv[p];
-    const int R = 1 << a.r, C = 1 << a.logc;
-    const int slog = a.m - a.r;
-    const size_t S = (size_t)1 << slog;
-    const size_t groups = S >> a.logc;
-    const size_t blk = blockIdx.x / groups;
-    const size_t col0 = (blockIdx.x % groups) << a.logc;
-    uint32_t *base = a.data + p * a.pstride + (blk << a.m);
-    const int total = R * C;
-    if (a.src) {
-        const uint32_t *src = a.src + blk * a.src_tstride;
-        for (int v = threadIdx.x; v < total; v += blockDim.x) {
-            const size_t idx = (size_t)(v >> a.logc) * S + col0 + (v & (C - 1));
-            sm[v] = idx < a.src_len ? reduce32(src[idx], q) : 0u;
-        }
-    } else {
-        for (int v = threadIdx.x; v < total; v += blockDim.x) {
-            const size_t idx = (size_t)(v >> a.logc) * S + col0 + (v & (C - 1));
-            sm[v] = base[idx];
-        }
-    }
-    __syncthreads();
-    const uint2 *T = tw_table(a.tw, p, 0);
-    smem_dif(sm, a.r, a.logc, T, q);
-    for (int v = threadIdx.x; v < total; v += blockDim.x) {
-        const int row = v >> a.logc;
-        const uint32_t gcol = (uint32_t)(col0 + (v & (C - 1)));
-        const uint32_t k1 = bitrev((uint32_t)row, a.r);
-        uint32_t x = sm[v];
-        const uint32_t E = (gcol * k1) << (kLogMaxNtt - a.m);
-        if (E) {
-            const uint2 w = tw_get(T, E, q, qinv);
-            x = mont_mul_pre(x, w.x, w.y, q);
-        }
-        base[(size_t)row * S + gcol] = x;
-    }
-}
-
-// Inverse column pass: undo the twiddle, then the DIT sub-transform.
-__global__ void ntt_col_inv(ColArgs a)
-{
-    extern __shared__ uint32_t sm[];
-    const int p = blockIdx.y;
-    const uint32_t q = c_q[p], qinv = c_qinv[p];
-    const int R = 1 << a.r, C = 1 << a.logc;
-    const int slog = a.m - a.r;
-    const size_t S = (size_t)1 << slog;
-    const size_t groups = S >> a.logc;
-    const size_t blk = blockIdx.x / groups;
-    const size_t col0 = (blockIdx.x % groups) << a.logc;
-    uint32_t *base = a.data + p * a.pstride + (blk << a.m);
-    const int total = R * C;
-    const uint2 *Ti = tw_table(a.tw, p, 1);
-    for (int v = threadIdx.x; v < total; v += blockDim.x) {
-        const int row = v >> a.logc;
-        const uint32_t gcol = (uint32_t)(col0 + (v & (C - 1)));
-        const uint32_t k1 = bitrev((uint32_t)row, a.r);
-        uint32_t x = base[(size_t)row * S + gcol];
-        const uint32_t E = (gcol * k1) << (kLogMaxNtt - a.m);
-        if (E) {
-            const uint2 w = tw_get(Ti, E, q, qinv);
-            x = mont_mul_pre(x, w.x, w.y, q);
-        }
-        sm[v] = x;
-    }
-    __syncthreads();
-    smem_dit(sm, a.r, a.logc, Ti, q);
-    for (int v = threadIdx.x; v < total; v += blockDim.x) {
-        const size_t idx = (size_t)(v >> a.logc) * S + col0 + (v & (C - 1));
-        base[idx] = sm[v];
-    }
-}
-
-// ------------------------------------------------------------ row pass
-
-enum { PAIR_ADJACENT = 0, PAIR_SQUARE = 1, PAIR_FIRST_TWO = 2 };
-
-struct RowArgs {
-    const uint32_t *F;  // forward data after the column passes
-    size_t fpstride;
-    uint32_t *G;        // products (transform domain, then inverse rows)
-    size_t gpstride;
-    int n;              // log2 L
-    int r;              // row length 2^r
-    int mode;           // which transforms product k multiplies
-    const uint2 *tw;
-    Scale scale;
-};
-
-// Last forward pass of both operands, pointwise product and first inverse
-// pass, on one contiguous row of 2^r points of product k.
-__global__ void ntt_row_mul(RowArgs a)
-{
-    extern __shared__ uint32_t sm[];
-    const int p = blockIdx.y;
-    const uint32_t q = c_q[p], qinv = c_qinv[p];
-    const int R = 1 << a.r;
-    const size_t rows = (size_t)1 << (a.n - a.r);
-    const size_t k = blockIdx.x / rows;
-    const size_t row = blockIdx.x % rows;
-    size_t ta, tb;
-    if (a.mode == PAIR_ADJACENT) { ta = 2 * k; tb = 2 * k + 1; }
-    else if (a.mode == PAIR_SQUARE) { ta = k; tb = k; }
-    else { ta = 0; tb = 1; }
-    const uint32_t *fa = a.F + p * a.fpstride + (ta << a.n) + row * R;
-    const uint32_t *fb = a.F + p * a.fpstride + (tb << a.n) + row * R;
-    const uint2 *T = tw_table(a.tw, p, 0);
-    const uint2 *Ti = tw_table(a.tw, p, 1);
-    uint32_t *Z = sm + 2 * R;
-    const uint32_t sc = a.scale.c[p];
-    if (a.mode == PAIR_SQUARE) {
-        for (int i = threadIdx.x; i < R; i += blockDim.x) sm[i] = fa[i];
-        __syncthreads();
-        smem_dif(sm, a.r, 0, T, q);
-        for (int i = threadIdx.x; i < R; i += blockDim.x) {
-            const uint32_t x = sm[i];
-            Z[i] = mont_mul(mont_mul(x, x, q, qinv), sc, q, qinv);
-        }
-    } else {
-        for (int i = threadIdx.x; i < R; i += blockDim.x) {
-            sm[2 * i] = fa[i];
-            sm[2 * i + 1] = fb[i];
-        }
-        __syncthreads();
-        smem_dif(sm, a.r, 1, T, q);
-        for (int i = threadIdx.x; i < R; i += blockDim.x)
-            Z[i] = mont_mul(mont_mul(sm[2 * i], sm[2 * i + 1], q, qinv), sc, q, qinv);
-    }
-    __syncthreads();
-    smem_dit(Z, a.r, 0, Ti, q);
-    uint32_t *g = a.G + p * a.gpstride + (k << a.n) + row * R;
-    for (int i = threadIdx.x; i < R; i += blockDim.x) g[i] = Z[i];
-}
-
 // ----------------------------------------------- remaindering and carries
 
 // Garner: the coefficient c < q0 q1 q2 with c = r_i mod q_i, as three words.
@@ -483,6 +274,282 @@ __global__ void carry_fix(const uint8_t *tile_cin, size_t tiles_total, size_t ti
     }
 }
 
+// -------------------------------------------- register-round sub-transforms
+//
+// A 2^LR-point sub-transform runs in "rounds" of up to four radix-2 stages.
+// In a round covering stage bits [b, b + e), a thread loads the 2^e elements
+// base + k 2^b (k < 2^e) of one group into registers, runs the e stages
+// there, and writes them back; one barrier separates rounds.  Data sit in
+// shared memory as C interleaved columns, element (row, col) at
+// s[row * C + col].  The stage with half-span 2^st (st = s - b within the
+// round) multiplies by w_{2^(s+1)}^(i mod 2^s), i = base + k 2^b, which is
+// entry (i mod 2^s) << (12 - s) of the table's high part (2^(s+1) <= 2^13).
+
+__host__ __device__ constexpr int rounds_of(int lr) { return (lr + 3) / 4; }
+__host__ __device__ constexpr int round_size(int lr, int rd)
+{
+    return lr / rounds_of(lr) + (rd < lr % rounds_of(lr) ? 1 : 0);
+}
+__host__ __device__ constexpr int round_base(int lr, int rd)  // stages below round rd (DIT order)
+{
+    int b = 0;
+    for (int j = 0; j < rd; j++) b += round_size(lr, j);
+    return b;
+}
+
+__device__ __forceinline__ void bf_dif(uint32_t &x, uint32_t &y, uint2 w, uint32_t q)
+{
+    const uint32_t a = x, b = y;
+    x = add_mod(a, b, q);
+    y = mont_mul_pre(sub_mod(a, b, q), w.x, w.y, q);
+}
+
+__device__ __forceinline__ void bf_dit(uint32_t &x, uint32_t &y, uint2 w, uint32_t q)
+{
+    const uint32_t t = mont_mul_pre(y, w.x, w.y, q);
+    const uint32_t a = x;
+    x = add_mod(a, t, q);
+    y = sub_mod(a, t, q);
+}
+
+// One round of a DIF (forward) or DIT (inverse) sub-transform.
+template <int LR, int C, int B, int E, bool FWD>
+__device__ __forceinline__ void transform_round(uint32_t *s, const uint2 *T, uint32_t q)
+{
+    constexpr int R = 1 << LR;
+    constexpr int NG = C * (R >> E);
+    for (int g = threadIdx.x; g < NG; g += blockDim.x) {
+        const int c = g & (C - 1);
+        const int gg = g / C;
+        const int glow = gg & ((1 << B) - 1);
+        const int base = ((gg >> B) << (B + E)) | glow;
+        uint32_t x[1 << E];
+#pragma unroll
+        for (int k = 0; k < (1 << E); k++) x[k] = s[(base + (k << B)) * C + c];
+        if (FWD) {
+#pragma unroll
+            for (int st = E - 1; st >= 0; st--) {
+#pragma unroll
+                for (int k = 0; k < (1 << E); k++) {
+                    if (k & (1 << st)) continue;
+                    const int p = glow + ((k & ((1 << st) - 1)) << B);
+                    const uint2 w = __ldg(&T[kTwLo + (p << (12 - B - st))]);
+                    bf_dif(x[k], x[k + (1 << st)], w, q);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int st = 0; st < E; st++) {
+#pragma unroll
+                for (int k = 0; k < (1 << E); k++) {
+                    if (k & (1 << st)) continue;
+                    const int p = glow + ((k & ((1 << st) - 1)) << B);
+                    const uint2 w = __ldg(&T[kTwLo + (p << (12 - B - st))]);
+                    bf_dit(x[k], x[k + (1 << st)], w, q);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < (1 << E); k++) s[(base + (k << B)) * C + c] = x[k];
+    }
+    __syncthreads();
+}
+
+// Forward DIF: rounds from the top stage bits down.  Caller synchronises
+// before; returns synchronised.
+template <int LR, int C>
+__device__ __forceinline__ void dif_block(uint32_t *s, const uint2 *T, uint32_t q)
+{
+    constexpr int NR = rounds_of(LR);
+    if constexpr (NR >= 1) {
+        constexpr int E0 = round_size(LR, 0);
+        transform_round<LR, C, LR - E0, E0, true>(s, T, q);
+    }
+    if constexpr (NR >= 2) {
+        constexpr int E0 = round_size(LR, 0), E1 = round_size(LR, 1);
+        transform_round<LR, C, LR - E0 - E1, E1, true>(s, T, q);
+    }
+    if constexpr (NR >= 3) {
+        constexpr int E0 = round_size(LR, 0), E1 = round_size(LR, 1), E2 = round_size(LR, 2);
+        transform_round<LR, C, LR - E0 - E1 - E2, E2, true>(s, T, q);
+    }
+    if constexpr (NR >= 4) {
+        constexpr int E3 = round_size(LR, 3);
+        transform_round<LR, C, 0, E3, true>(s, T, q);
+    }
+}
+
+// Inverse DIT: rounds from the bottom stage bits up (inverse roots).
+template <int LR, int C>
+__device__ __forceinline__ void dit_block(uint32_t *s, const uint2 *Ti, uint32_t q)
+{
+    constexpr int NR = rounds_of(LR);
+    if constexpr (NR >= 1) transform_round<LR, C, 0, round_size(LR, 0), false>(s, Ti, q);
+    if constexpr (NR >= 2)
+        transform_round<LR, C, round_base(LR, 1), round_size(LR, 1), false>(s, Ti, q);
+    if constexpr (NR >= 3)
+        transform_round<LR, C, round_base(LR, 2), round_size(LR, 2), false>(s, Ti, q);
+    if constexpr (NR >= 4)
+        transform_round<LR, C, round_base(LR, 3), round_size(LR, 3), false>(s, Ti, q);
+}
+
+// ---------------------------------------------------------- column passes
+
+constexpr int kColLogC = 4;     // 16 consecutive columns per thread block
+constexpr int kColC = 1 << kColLogC;
+constexpr int kColThreads = 256;
+constexpr int kColMaxLog = 10;  // rows per column pass: up to 2^10 (64 KiB)
+
+struct ColArgs {
+    uint32_t *data;        // prime p's array at data + p * pstride
+    size_t pstride;
+    int m;                 // block size 2^m (the sub-problem this pass splits)
+    const uint32_t *src;   // first forward pass: limb source (else null)
+    size_t src_tstride;    // limbs between consecutive transforms' sources
+    size_t src_len;        // valid limbs per transform (rest are zero)
+    const uint2 *tw;
+};
+
+// Forward column pass: a 2^LR-point DIF down each of 16 consecutive columns of
+// one block (row stride S = 2^(m-LR)), then element (row, col) times
+// w_M^(col * bitrev(row)).
+template <int LR>
+__global__ void __launch_bounds__(kColThreads) ntt_col_fwd(ColArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    constexpr int R = 1 << LR;
+    constexpr int total = R * kColC;
+    const int p = blockIdx.y;
+    const uint32_t q = c_q[p], qinv = c_qinv[p];
+    const int slog = a.m - LR;
+    const size_t S = (size_t)1 << slog;
+    const size_t groups = S >> kColLogC;
+    const size_t blk = blockIdx.x / groups;
+    const size_t col0 = (blockIdx.x % groups) << kColLogC;
+    uint32_t *base = a.data + p * a.pstride + (blk << a.m);
+    if (a.src) {
+        const uint32_t *src = a.src + blk * a.src_tstride;
+        for (int v = threadIdx.x; v < total; v += kColThreads) {
+            const size_t idx = (size_t)(v >> kColLogC) * S + col0 + (v & (kColC - 1));
+            sm[v] = idx < a.src_len ? reduce32(src[idx], q) : 0u;
+        }
+    } else {
+        for (int v = threadIdx.x; v < total; v += kColThreads)
+            sm[v] = base[(size_t)(v >> kColLogC) * S + col0 + (v & (kColC - 1))];
+    }
+    __syncthreads();
+    const uint2 *T = tw_table(a.tw, p, 0);
+    dif_block<LR, kColC>(sm, T, q);
+    for (int v = threadIdx.x; v < total; v += kColThreads) {
+        const int row = v >> kColLogC;
+        const uint32_t gcol = (uint32_t)(col0 + (v & (kColC - 1)));
+        const uint32_t E = (gcol * bitrev((uint32_t)row, LR)) << (kLogMaxNtt - a.m);
+        uint32_t x = sm[v];
+        if (E) {
+            const uint2 w = tw_get(T, E, q, qinv);
+            x = mont_mul_pre(x, w.x, w.y, q);
+        }
+        base[(size_t)row * S + gcol] = x;
+    }
+}
+
+// Inverse column pass: undo the twiddle, then the DIT down each column.
+template <int LR>
+__global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    constexpr int R = 1 << LR;
+    constexpr int total = R * kColC;
+    const int p = blockIdx.y;
+    const uint32_t q = c_q[p], qinv = c_qinv[p];
+    const int slog = a.m - LR;
+    const size_t S = (size_t)1 << slog;
+    const size_t groups = S >> kColLogC;
+    const size_t blk = blockIdx.x / groups;
+    const size_t col0 = (blockIdx.x % groups) << kColLogC;
+    uint32_t *base = a.data + p * a.pstride + (blk << a.m);
+    const uint2 *Ti = tw_table(a.tw, p, 1);
+    for (int v = threadIdx.x; v < total; v += kColThreads) {
+        const int row = v >> kColLogC;
+        const uint32_t gcol = (uint32_t)(col0 + (v & (kColC - 1)));
+        const uint32_t E = (gcol * bitrev((uint32_t)row, LR)) << (kLogMaxNtt - a.m);
+        uint32_t x = base[(size_t)row * S + gcol];
+        if (E) {
+            const uint2 w = tw_get(Ti, E, q, qinv);
+            x = mont_mul_pre(x, w.x, w.y, q);
+        }
+        sm[v] = x;
+    }
+    __syncthreads();
+    dit_block<LR, kColC>(sm, Ti, q);
+    for (int v = threadIdx.x; v < total; v += kColThreads)
+        base[(size_t)(v >> kColLogC) * S + col0 + (v & (kColC - 1))] = sm[v];
+}
+
+// ------------------------------------------------------------ row pass
+
+enum { PAIR_ADJACENT = 0, PAIR_SQUARE = 1, PAIR_FIRST_TWO = 2 };
+
+constexpr int kRowThreads = 256;
+constexpr int kRowMaxLog = 12;
+
+struct RowArgs {
+    const uint32_t *F;  // forward data after the column passes
+    size_t fpstride;
+    uint32_t *G;        // products (transform domain, then inverse rows)
+    size_t gpstride;
+    int n;              // log2 L
+    int mode;           // which transforms product k multiplies
+    const uint2 *tw;
+    Scale scale;
+};
+
+// Last forward pass of both operands, pointwise product and first inverse
+// pass, on one contiguous row of 2^LR points of product k.
+template <int LR>
+__global__ void __launch_bounds__(kRowThreads) ntt_row_mul(RowArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    constexpr int R = 1 << LR;
+    const int p = blockIdx.y;
+    const uint32_t q = c_q[p], qinv = c_qinv[p];
+    const size_t rows = (size_t)1 << (a.n - LR);
+    const size_t k = blockIdx.x / rows;
+    const size_t row = blockIdx.x % rows;
+    size_t ta, tb;
+    if (a.mode == PAIR_ADJACENT) { ta = 2 * k; tb = 2 * k + 1; }
+    else if (a.mode == PAIR_SQUARE) { ta = k; tb = k; }
+    else { ta = 0; tb = 1; }
+    const uint32_t *fa = a.F + p * a.fpstride + (ta << a.n) + row * R;
+    const uint32_t *fb = a.F + p * a.fpstride + (tb << a.n) + row * R;
+    const uint2 *T = tw_table(a.tw, p, 0);
+    const uint2 *Ti = tw_table(a.tw, p, 1);
+    uint32_t *Z = sm + 2 * R;
+    const uint32_t sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
+    if (a.mode == PAIR_SQUARE) {
+        for (int i = threadIdx.x; i < R; i += kRowThreads) Z[i] = fa[i];
+        __syncthreads();
+        dif_block<LR, 1>(Z, T, q);
+        for (int i = threadIdx.x; i < R; i += kRowThreads) {
+            const uint32_t x = Z[i];
+            Z[i] = mont_mul(mont_mul(x, x, q, qinv), sc, q, qinv);
+        }
+    } else {
+        for (int i = threadIdx.x; i < R; i += kRowThreads) {
+            sm[2 * i] = fa[i];
+            sm[2 * i + 1] = fb[i];
+        }
+        __syncthreads();
+        dif_block<LR, 2>(sm, T, q);
+        for (int i = threadIdx.x; i < R; i += kRowThreads)
+            Z[i] = mont_mul(mont_mul(sm[2 * i], sm[2 * i + 1], q, qinv), sc, q, qinv);
+    }
+    __syncthreads();
+    dit_block<LR, 1>(Z, Ti, q);
+    uint32_t *g = a.G + p * a.gpstride + (k << a.n) + row * R;
+    for (int i = threadIdx.x; i < R; i += kRowThreads) g[i] = Z[i];
+}
+
 // ------------------------------------------ whole product in one block
 
 struct FusedArgs {
@@ -492,7 +559,6 @@ struct FusedArgs {
     size_t b_tstride, b_len;
     uint32_t *out;
     size_t out_tstride, out_len;
-    int n;              // log2 L, L <= 4096
     const uint2 *tw;
     Scale scale;
 };
@@ -502,15 +568,16 @@ constexpr int kFusedThreads = 512;
 
 // One product per block: three forward/pointwise/inverse rounds (one per
 // prime) in shared memory, then remaindering and carries over one tile.
+// Layout (words): residues R0 [0,L) R1 [L,2L) R2 [2L,3L); raw A shares R2's
+// space (it is last read before R2 is written), raw B [3L,4L), transform pair
+// XY [4L,6L).  After the three rounds the remaindered words (3 (L+2)) go to
+// [3L, 6L+6).
+template <int LR>
 __global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
 {
     extern __shared__ uint32_t sm[];
     __shared__ uint32_t wsm[32];
-    // layout (words): residues R0 [0,L) R1 [L,2L) R2 [2L,3L); raw A shares
-    // R2's space (it is last read before R2 is written), raw B [3L,4L),
-    // transform pair XY [4L,6L).  After the three rounds the remaindered
-    // words (3 (L+2)) go to [3L, 6L+6).
-    const int L = 1 << a.n;
+    constexpr int L = 1 << LR;
     uint32_t *Rr[3] = {sm, sm + L, sm + 2 * L};
     uint32_t *rawA = sm + 2 * L;
     uint32_t *rawB = sm + 3 * L;
@@ -523,21 +590,23 @@ __global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
         rawB[i] = (gb && (size_t)i < a.b_len) ? gb[i] : 0u;
     }
     __syncthreads();
+#pragma unroll 1
     for (int p = 0; p < kNumPrimes; p++) {
         const uint32_t q = c_q[p], qinv = c_qinv[p];
         const uint2 *T = tw_table(a.tw, p, 0);
         const uint2 *Ti = tw_table(a.tw, p, 1);
+        const uint32_t sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
         for (int i = threadIdx.x; i < L; i += blockDim.x) {
             XY[2 * i] = reduce32(rawA[i], q);
             XY[2 * i + 1] = reduce32(gb ? rawB[i] : rawA[i], q);
         }
         __syncthreads();
-        if (a.n > 0) smem_dif(XY, a.n, 1, T, q);
+        dif_block<LR, 2>(XY, T, q);
         uint32_t *Z = Rr[p];
         for (int i = threadIdx.x; i < L; i += blockDim.x)
-            Z[i] = mont_mul(mont_mul(XY[2 * i], XY[2 * i + 1], q, qinv), a.scale.c[p], q, qinv);
+            Z[i] = mont_mul(mont_mul(XY[2 * i], XY[2 * i + 1], q, qinv), sc, q, qinv);
         __syncthreads();
-        if (a.n > 0) smem_dit(Z, a.n, 0, Ti, q);
+        dit_block<LR, 1>(Z, Ti, q);
     }
     uint32_t *cw0 = sm + 3 * L, *cw1 = cw0 + (L + 2), *cw2 = cw1 + (L + 2);
     for (int i = threadIdx.x; i < L + 2; i += blockDim.x) {
@@ -561,13 +630,15 @@ struct NttPlan {
     int rrow = 0;
 };
 
+// Row pass of up to 2^12 points (at least 2^4 so column passes keep 16
+// columns), column passes of at most 2^10 rows, split as evenly as possible.
 static NttPlan make_plan(int n)
 {
     NttPlan P;
     P.n = n;
-    P.rrow = std::min(12, n - 4);
+    P.rrow = std::min(kRowMaxLog, n - kColLogC);
     int rem = n - P.rrow;
-    P.ncol = (rem + 9) / 10;
+    P.ncol = (rem + kColMaxLog - 1) / kColMaxLog;
     for (int i = 0; i < P.ncol; i++) {
         P.rcol[i] = rem / (P.ncol - i);
         rem -= P.rcol[i];
@@ -584,9 +655,18 @@ static void set_smem(K kernel, size_t bytes)
                                       (int)bytes));
 }
 
-static constexpr int kColLogC = 4;
-static constexpr int kColThreads = 256;
-static constexpr int kRowThreads = 512;
+template <int LR>
+static void launch_col(bool fwd, dim3 grid, cudaStream_t s, const ColArgs &a)
+{
+    const size_t smem = ((size_t)1 << (LR + kColLogC)) * sizeof(uint32_t);
+    if (fwd) {
+        set_smem(ntt_col_fwd<LR>, smem);
+        ntt_col_fwd<LR><<<grid, kColThreads, smem, s>>>(a);
+    } else {
+        set_smem(ntt_col_inv<LR>, smem);
+        ntt_col_inv<LR><<<grid, kColThreads, smem, s>>>(a);
+    }
+}
 
 static void col_pass(Ctx &c, bool fwd, uint32_t *data, size_t pstride, size_t total, int m,
                      int r, const uint32_t *src, size_t src_tstride, size_t src_len,
@@ -596,29 +676,40 @@ static void col_pass(Ctx &c, bool fwd, uint32_t *data, size_t pstride, size_t to
     a.data = data;
     a.pstride = pstride;
     a.m = m;
-    a.r = r;
-    a.logc = kColLogC;
     a.src = src;
     a.src_tstride = src_tstride;
     a.src_len = src_len;
     a.tw = c.twiddles;
     const size_t ctas = total >> (r + kColLogC);
-    const size_t smem = ((size_t)1 << (r + kColLogC)) * sizeof(uint32_t);
     dim3 grid((unsigned)ctas, kNumPrimes);
     // algorithmic bytes: every point of the three prime arrays read and
     // written once (the first forward pass reads limbs instead)
     double bytes = 24.0 * (double)total;
     if (src) bytes = 12.0 * (double)total + 4.0 * (double)src_len * (double)(total >> m);
     const int tok = prof_begin(c, fwd ? (src ? "ntt_col_fwd_first" : "ntt_col_fwd") : "ntt_col_inv", s);
-    if (fwd) {
-        set_smem(ntt_col_fwd, smem);
-        ntt_col_fwd<<<grid, kColThreads, smem, s>>>(a);
-    } else {
-        set_smem(ntt_col_inv, smem);
-        ntt_col_inv<<<grid, kColThreads, smem, s>>>(a);
+    switch (r) {
+    case 1: launch_col<1>(fwd, grid, s, a); break;
+    case 2: launch_col<2>(fwd, grid, s, a); break;
+    case 3: launch_col<3>(fwd, grid, s, a); break;
+    case 4: launch_col<4>(fwd, grid, s, a); break;
+    case 5: launch_col<5>(fwd, grid, s, a); break;
+    case 6: launch_col<6>(fwd, grid, s, a); break;
+    case 7: launch_col<7>(fwd, grid, s, a); break;
+    case 8: launch_col<8>(fwd, grid, s, a); break;
+    case 9: launch_col<9>(fwd, grid, s, a); break;
+    case 10: launch_col<10>(fwd, grid, s, a); break;
+    default: fail(CAT_EINVAL, "column pass size out of range");
     }
     CAT_LAUNCH(fwd ? "ntt_col_fwd" : "ntt_col_inv");
     prof_end(c, tok, s, bytes);
+}
+
+template <int LR>
+static void launch_row(dim3 grid, cudaStream_t s, const RowArgs &a)
+{
+    const size_t smem = ((size_t)3 << LR) * sizeof(uint32_t);
+    set_smem(ntt_row_mul<LR>, smem);
+    ntt_row_mul<LR><<<grid, kRowThreads, smem, s>>>(a);
 }
 
 // One operand source of a batched product.
@@ -663,15 +754,18 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     ra.G = G.get();
     ra.gpstride = gp;
     ra.n = n;
-    ra.r = P.rrow;
     ra.mode = mode;
     ra.tw = c.twiddles;
     ra.scale = make_scale(n);
-    const size_t rsmem = ((size_t)3 << P.rrow) * sizeof(uint32_t);
-    set_smem(ntt_row_mul, rsmem);
     dim3 rgrid((unsigned)(nprod << (n - P.rrow)), kNumPrimes);
     int tok = prof_begin(c, "ntt_row_mul", s);
-    ntt_row_mul<<<rgrid, kRowThreads, rsmem, s>>>(ra);
+    switch (P.rrow) {
+    case 9: launch_row<9>(rgrid, s, ra); break;
+    case 10: launch_row<10>(rgrid, s, ra); break;
+    case 11: launch_row<11>(rgrid, s, ra); break;
+    case 12: launch_row<12>(rgrid, s, ra); break;
+    default: fail(CAT_EINVAL, "row pass size out of range");
+    }
     CAT_LAUNCH("ntt_row_mul");
     prof_end(c, tok, s, (mode == PAIR_SQUARE ? 24.0 : 36.0) * (double)gp);
     F.reset();
@@ -708,6 +802,14 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     prof_end(c, tok, s, (double)tt);
 }
 
+template <int LR>
+static void launch_fused(unsigned grid, cudaStream_t s, const FusedArgs &a)
+{
+    const size_t smem = (6 * ((size_t)1 << LR) + 8) * sizeof(uint32_t);
+    set_smem(ntt_mul_fused<LR>, smem);
+    ntt_mul_fused<LR><<<grid, kFusedThreads, smem, s>>>(a);
+}
+
 static void ntt_mul_small(Ctx &c, int n, size_t nprod, Operand x, Operand y, bool square,
                           uint32_t *out, size_t out_tstride, size_t out_len, cudaStream_t s)
 {
@@ -721,14 +823,25 @@ static void ntt_mul_small(Ctx &c, int n, size_t nprod, Operand x, Operand y, boo
     a.out = out;
     a.out_tstride = out_tstride;
     a.out_len = out_len;
-    a.n = n;
     a.tw = c.twiddles;
     a.scale = make_scale(n);
-    const size_t L = (size_t)1 << n;
-    const size_t smem = (6 * L + 8) * sizeof(uint32_t);
-    set_smem(ntt_mul_fused, smem);
+    const unsigned grid = (unsigned)nprod;
     const int tok = prof_begin(c, "ntt_mul_fused", s);
-    ntt_mul_fused<<<(unsigned)nprod, kFusedThreads, smem, s>>>(a);
+    switch (n) {
+    case 1: launch_fused<1>(grid, s, a); break;
+    case 2: launch_fused<2>(grid, s, a); break;
+    case 3: launch_fused<3>(grid, s, a); break;
+    case 4: launch_fused<4>(grid, s, a); break;
+    case 5: launch_fused<5>(grid, s, a); break;
+    case 6: launch_fused<6>(grid, s, a); break;
+    case 7: launch_fused<7>(grid, s, a); break;
+    case 8: launch_fused<8>(grid, s, a); break;
+    case 9: launch_fused<9>(grid, s, a); break;
+    case 10: launch_fused<10>(grid, s, a); break;
+    case 11: launch_fused<11>(grid, s, a); break;
+    case 12: launch_fused<12>(grid, s, a); break;
+    default: fail(CAT_EINVAL, "one-block transform size out of range");
+    }
     CAT_LAUNCH("ntt_mul_fused");
     prof_end(c, tok, s, 4.0 * (double)nprod * (double)(x.len + (square ? 0 : y.len) + out_len));
 }
@@ -760,7 +873,7 @@ void ntt_mul(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
              uint32_t *out, cudaStream_t s)
 {
     const size_t len = na + nb;
-    const int n = ceil_log2(len);
+    const int n = std::max(1, ceil_log2(len));
     if (n > kLogMaxNtt) fail(CAT_EINVAL, "operands too long for one transform");
     const bool square = (a == b && na == nb);
     Operand x{a, 0, na}, y{b, 0, nb};

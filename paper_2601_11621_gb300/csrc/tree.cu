@@ -78,7 +78,7 @@ Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s)
     while (nodes > 1) {
         const size_t nprod = nodes / 2, odd = nodes & 1, nn = nprod + odd, ns = 2 * slot;
         DevBuf<uint32_t> nxt(c, nn * ns, s);
-        if (!comba_level(c, cur.get(), slot, nprod, nxt.get(), s))
+        if (slot > c.comba_max_slot || !comba_level(c, cur.get(), slot, nprod, nxt.get(), s))
             ntt_level(c, cur.get(), slot, nprod, nxt.get(), s);
         if (odd) {
             CAT_CUDA(cudaMemcpyAsync(nxt.get() + nprod * ns, cur.get() + (nodes - 1) * slot,

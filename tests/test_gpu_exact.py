@@ -144,9 +144,9 @@ def test_paper_scale(ctx, cat_lib, orc):
     nbytes = (bits + 7) // 8
     assert nbytes == int(t["result_file_bytes"])
     le = got.astype("<u4").tobytes()[:nbytes]
-    sha_le = hashlib.sha256(le).hexdigest()
-    sha_be = hashlib.sha256(le[::-1]).hexdigest()
-    print("paper-scale SHA-256 LE", sha_le, "BE", sha_be)
+    header = bytes.fromhex(t["sha256_header_hex"])
+    sha = hashlib.sha256(header + le).hexdigest()
+    print("paper-scale SHA-256 (header + LE magnitude)", sha)
     # digits: floor(log10 C) + 1 from the top limbs (the fraction 0.981 is far
     # from an integer, so double precision decides it)
     l10 = _leading_digits(got, bits)
@@ -157,4 +157,5 @@ def test_paper_scale(ctx, cat_lib, orc):
         want = list(ex.map(lambda q: orc.exact_mod(orc.CATALAN, n, q), qs))
         have = list(ex.map(lambda q: orc.limbs_mod(got, q), qs))
     assert have == want
-    assert t["sha256"] in (sha_le, sha_be)
+    # Table 1's SHA-256 of the paper's own result file
+    assert sha == t["sha256"]
