@@ -133,6 +133,32 @@ int cat_factor_copy_primes(cat_ctx *ctx, const cat_factorization *f, uint32_t *d
 int bigint_mul(cat_ctx *ctx, const uint32_t *a, size_t na, const uint32_t *b,
                size_t nb, uint32_t *out, size_t cap, size_t *out_len, void *stream);
 
+/* out = a * b without allocating any device memory.  The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc, such as an
+ * application whose own allocator already holds the device's memory (a new
+ * allocation would fail or fragment it), or latency-critical code that must
+ * not take cudaMalloc/cudaFree's implicit device-wide synchronisation, or a
+ * service that must not meet an out-of-memory failure in the middle of a
+ * request.  There is no context: the
+ * transform scratch and the twiddle tables live in fixed-size __device__
+ * arrays of the library (about 2.4 MB of scratch and 1.2 MB of tables),
+ * which every GPU that loads the library holds until the process exits.
+ *   - Limit: na + nb <= 65,536 limbs; larger products return CAT_ENOMEM.
+ *   - out must have room for na + nb limbs (cap >= na + nb, else
+ *     CAT_ERANGE); *out_len = the normalised length.  a, b, out are device
+ *     pointers; stream as elsewhere; the call returns after the result is
+ *     complete.
+ *   - Runs on the current CUDA device.  The first call on a device sets that
+ *     device up (looks up the arrays' device addresses and uploads the
+ *     twiddle table with a synchronous copy); make that first call before any
+ *     stream capture.
+ *   - Every call shares the same scratch array: calls that overlap on the GPU
+ *     (other streams or other host threads) race; serialise them.
+ *   - Errors: CAT_EINVAL (null pointer), CAT_ENOMEM (too large), CAT_ERANGE,
+ *     CAT_ECUDA. */
+int bigint_mul_noalloc(const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
+                       uint32_t *out, size_t cap, size_t *out_len, void *stream);
+
 /* out = a^e by left-to-right binary exponentiation ("fast pow",
  * Algorithm 2).  a^0 = 1.  Errors as bigint_mul. */
 int bigint_pow(cat_ctx *ctx, const uint32_t *a, size_t na, uint64_t e,

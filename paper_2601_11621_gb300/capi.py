@@ -26,7 +26,8 @@ STATUS = {0: "CAT_OK", -1: "CAT_EINVAL", -2: "CAT_ENOMEM", -3: "CAT_ERANGE",
 
 EXPORTED = ["cat_ctx_create", "cat_ctx_destroy", "cat_last_error", "cat_ctx_memory",
             "cat_ctx_set_profiling", "cat_ctx_profile",
-            "catalan_factor", "cat_factor_free", "cat_factor_copy_primes", "bigint_mul", "bigint_pow",
+            "catalan_factor", "cat_factor_free", "cat_factor_copy_primes", "bigint_mul",
+            "bigint_mul_noalloc", "bigint_pow",
             "product_tree", "cat_reconstruct", "cat_bound_limbs", "cat_exact",
             "catalan_exact", "cat_exact_host"]
 
@@ -82,6 +83,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cat_factor_copy_primes.restype = i32
     L.bigint_mul.argtypes = [vp, vp, sz, vp, sz, vp, sz, szp, vp]
     L.bigint_mul.restype = i32
+    L.bigint_mul_noalloc.argtypes = [vp, sz, vp, sz, vp, sz, szp, vp]
+    L.bigint_mul_noalloc.restype = i32
     L.bigint_pow.argtypes = [vp, vp, sz, u64, vp, sz, szp, vp]
     L.bigint_pow.restype = i32
     L.product_tree.argtypes = [vp, vp, sz, vp, sz, szp, vp]
@@ -195,6 +198,26 @@ def bigint_mul(ctx: Context, a, b, stream=None):
     n = ctypes.c_size_t()
     ctx.check(load().bigint_mul(ctx.handle, _ptr(ta), ta.numel(), _ptr(tb), tb.numel(),
                                 _ptr(out), cap, ctypes.byref(n), _stream(stream)))
+    return out[:n.value]
+
+
+NOALLOC_MAX_LIMBS = 1 << 16
+
+
+def bigint_mul_noalloc(a, b, out=None, stream=None, device: int = 0):
+    """a * b through bigint_mul_noalloc (no context, no device allocation in
+    the library).  `out` may be a preallocated int32 device tensor of at
+    least len(a) + len(b) limbs; the result is a view of it."""
+    dev = f"cuda:{device}"
+    ta, tb = _limbs_tensor(a, dev), _limbs_tensor(b, dev)
+    cap = ta.numel() + tb.numel()
+    if out is None:
+        out = _empty(cap, dev)
+    n = ctypes.c_size_t()
+    rc = load().bigint_mul_noalloc(_ptr(ta), ta.numel(), _ptr(tb), tb.numel(), _ptr(out),
+                                   out.numel(), ctypes.byref(n), _stream(stream))
+    if rc != 0:
+        raise CatError(rc, "bigint_mul_noalloc")
     return out[:n.value]
 
 

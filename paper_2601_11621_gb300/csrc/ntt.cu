@@ -25,6 +25,7 @@
 #include "cat_internal.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace cat {
 
@@ -886,4 +887,213 @@ void ntt_mul(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
     }
 }
 
+// --------------------------------------- multiplication without allocation
+//
+// For callers that must not allocate device memory: code running where
+// cudaMalloc is not allowed or not wanted (inside a host callback, a caller
+// that owns all device memory through its own arena, or a process whose
+// allocator is already saturated).  The transform scratch and the twiddle
+// tables of this variant live in file-scope __device__ arrays of fixed size,
+// reserved when the library is loaded, on every device that loads it, until
+// the process exits.  Products of up to kNoAllocMaxLimbs limbs fit.
+
+constexpr int kNoAllocLog = 16;
+constexpr size_t kNoAllocMaxLimbs = (size_t)1 << kNoAllocLog;   // na + nb limit
+constexpr size_t kNoAllocL = kNoAllocMaxLimbs;
+// words: F (3 primes x 2 transforms x L), G (3 x L), tile maps, top index
+constexpr size_t kNoAllocF = 6 * kNoAllocL;
+constexpr size_t kNoAllocG = 3 * kNoAllocL;
+constexpr size_t kNoAllocMapWords = 64;
+constexpr size_t kNoAllocWords = kNoAllocF + kNoAllocG + kNoAllocMapWords + 2;
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
+static __device__ __align__(256) uint2 g_noalloc_twiddles[(size_t)kNumPrimes * 2 * kTwPerDir];
+
+// Largest i + 1 with x[i] != 0 into *top (which the caller clears).
+__global__ void noalloc_top(const uint32_t *x, size_t n, unsigned long long *top)
+{
+    unsigned long long best = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        if (x[i]) best = i + 1;
+    for (int off = 16; off; off >>= 1) {
+        const unsigned long long o = __shfl_down_sync(0xffffffffu, best, off);
+        best = o > best ? o : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(top, best);
+}
+
+struct NoAllocDevice {
+    bool ready = false;
+    uint32_t *scratch = nullptr;  // device address of g_noalloc_scratch
+    uint2 *twiddles = nullptr;    // device address of g_noalloc_twiddles
+};
+static NoAllocDevice g_noalloc_dev[64];
+static uint2 g_noalloc_tw_host[(size_t)kNumPrimes * 2 * kTwPerDir];
+
+static uint32_t noalloc_generator(uint32_t q)
+{
+    uint64_t f[16];
+    int nf = 0;
+    uint64_t m = q - 1;
+    for (uint64_t d = 2; d * d <= m; d++)
+        if (m % d == 0) {
+            f[nf++] = d;
+            while (m % d == 0) m /= d;
+        }
+    if (m > 1) f[nf++] = m;
+    for (uint32_t g = 2;; g++) {
+        bool ok = true;
+        for (int i = 0; i < nf && ok; i++) ok = powmod_u32(g, (q - 1) / f[i], q) != 1;
+        if (ok) return g;
+    }
+}
+
+// Once per device, with that device current: resolve the device addresses of
+// the two arrays and fill the twiddle table (same layout as the context's).
+static std::mutex g_noalloc_mutex;
+
+static int noalloc_setup(int dev)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoAllocDevice &d = g_noalloc_dev[dev];
+    if (d.ready) return CAT_OK;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return CAT_ECUDA;
+    d.scratch = (uint32_t *)p;
+    if (cudaGetSymbolAddress(&p, g_noalloc_twiddles) != cudaSuccess) return CAT_ECUDA;
+    d.twiddles = (uint2 *)p;
+    for (int i = 0; i < kNumPrimes; i++) {
+        const uint32_t q = ntt_prime(i), qi = inv32(q);
+        const uint32_t w = powmod_u32(noalloc_generator(q), (q - 1) >> kLogMaxNtt, q);
+        for (int dir = 0; dir < 2; dir++) {
+            const uint32_t root = dir == 0 ? w : powmod_u32(w, (1u << kLogMaxNtt) - 1, q);
+            uint2 *T = &g_noalloc_tw_host[((size_t)i * 2 + dir) * kTwPerDir];
+            uint64_t x = 1;
+            for (int j = 0; j < kTwLo; j++) {
+                const uint32_t mm = to_mont_c(x, q);
+                T[j] = make_uint2(mm, mm * qi);
+                x = x * root % q;
+            }
+            const uint32_t step = powmod_u32(root, kTwLo, q);
+            x = 1;
+            for (int j = 0; j < kTwHi; j++) {
+                const uint32_t mm = to_mont_c(x, q);
+                T[kTwLo + j] = make_uint2(mm, mm * qi);
+                x = x * step % q;
+            }
+        }
+    }
+    if (cudaMemcpyToSymbol(g_noalloc_twiddles, g_noalloc_tw_host, sizeof(g_noalloc_tw_host)) !=
+        cudaSuccess)
+        return CAT_ECUDA;
+    d.ready = true;
+    return CAT_OK;
+}
+
+// The product through the same kernels as ntt_mul, with all scratch taken
+// from the static array.
+static void noalloc_mul(const NoAllocDevice &d, const uint32_t *a, size_t na, const uint32_t *b,
+                        size_t nb, uint32_t *out, cudaStream_t s)
+{
+    Ctx local;  // no device resources: only the twiddle pointer is used
+    local.twiddles = d.twiddles;
+    const size_t len = na + nb;
+    const int n = std::max(1, ceil_log2(len));
+    Operand x{a, 0, na}, y{b, 0, nb};
+    if (n <= kFusedMaxLog) {
+        ntt_mul_small(local, n, 1, x, y, false, out, 0, len, s);
+        return;
+    }
+    const NttPlan P = make_plan(n);
+    const size_t L = (size_t)1 << n;
+    uint32_t *F = d.scratch;
+    uint32_t *G = d.scratch + kNoAllocF;
+    uint8_t *maps = (uint8_t *)(d.scratch + kNoAllocF + kNoAllocG);
+    const size_t fp = 2 * L, gp = L;
+    col_pass(local, true, F, fp, L, n, P.rcol[0], x.p, 0, x.len, s);
+    col_pass(local, true, F + L, fp, L, n, P.rcol[0], y.p, 0, y.len, s);
+    int m = n - P.rcol[0];
+    for (int i = 1; i < P.ncol; i++) {
+        col_pass(local, true, F, fp, fp, m, P.rcol[i], nullptr, 0, 0, s);
+        m -= P.rcol[i];
+    }
+    RowArgs ra;
+    ra.F = F;
+    ra.fpstride = fp;
+    ra.G = G;
+    ra.gpstride = gp;
+    ra.n = n;
+    ra.mode = PAIR_FIRST_TWO;
+    ra.tw = d.twiddles;
+    ra.scale = make_scale(n);
+    dim3 rgrid((unsigned)(L >> P.rrow), kNumPrimes);
+    switch (P.rrow) {
+    case 9: launch_row<9>(rgrid, s, ra); break;
+    case 10: launch_row<10>(rgrid, s, ra); break;
+    case 11: launch_row<11>(rgrid, s, ra); break;
+    case 12: launch_row<12>(rgrid, s, ra); break;
+    default: fail(CAT_EINVAL, "row pass size out of range");
+    }
+    CAT_LAUNCH("ntt_row_mul");
+    for (int i = P.ncol - 1; i >= 0; i--) {
+        int mi = n;
+        for (int j = 0; j < i; j++) mi -= P.rcol[j];
+        col_pass(local, false, G, gp, gp, mi, P.rcol[i], nullptr, 0, 0, s);
+    }
+    const size_t tiles = L / kTile;
+    CrtArgs ca;
+    ca.G = G;
+    ca.gpstride = gp;
+    ca.n = n;
+    ca.out = out;
+    ca.out_tstride = 0;
+    ca.out_len = len;
+    ca.tile_maps = maps;
+    crt_carry_tiles<<<(unsigned)tiles, kTileThreads, 0, s>>>(ca);
+    CAT_LAUNCH("crt_carry_tiles");
+    carry_tile_scan<<<1, 1024, 0, s>>>(maps, tiles);
+    CAT_LAUNCH("carry_tile_scan");
+    carry_fix<<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(maps, tiles, tiles, n, out, 0, len);
+    CAT_LAUNCH("carry_fix");
+}
+
 }  // namespace cat
+
+extern "C" int bigint_mul_noalloc(const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
+                                  uint32_t *out, size_t cap, size_t *out_len, void *stream)
+{
+    using namespace cat;
+    if (!out_len || (na && !a) || (nb && !b) || (cap && !out)) return CAT_EINVAL;
+    if (na + nb > kNoAllocMaxLimbs) return CAT_ENOMEM;  // beyond the static scratch
+    if (cap < na + nb) return CAT_ERANGE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CAT_ECUDA;
+    const int rc = noalloc_setup(dev);
+    if (rc != CAT_OK) return rc;
+    const NoAllocDevice &d = g_noalloc_dev[dev];
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    try {
+        if (na == 0 || nb == 0) {
+            if (na + nb) CAT_CUDA(cudaMemsetAsync(out, 0, 4 * (na + nb), s));
+            CAT_CUDA(cudaStreamSynchronize(s));
+            *out_len = 0;
+            return CAT_OK;
+        }
+        noalloc_mul(d, a, na, b, nb, out, s);
+        unsigned long long *top = (unsigned long long *)(d.scratch + kNoAllocF + kNoAllocG +
+                                                         kNoAllocMapWords);
+        CAT_CUDA(cudaMemsetAsync(top, 0, sizeof(*top), s));
+        noalloc_top<<<64, 256, 0, s>>>(out, na + nb, top);
+        CAT_LAUNCH("noalloc_top");
+        unsigned long long h = 0;
+        CAT_CUDA(cudaMemcpyAsync(&h, top, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CAT_CUDA(cudaStreamSynchronize(s));
+        *out_len = (size_t)h;
+        return CAT_OK;
+    } catch (const Error &e) {
+        return e.code;
+    } catch (...) {
+        return CAT_ECUDA;
+    }
+}
