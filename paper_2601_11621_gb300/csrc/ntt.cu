@@ -275,281 +275,7 @@ __global__ void carry_fix(const uint8_t *tile_cin, size_t tiles_total, size_t ti
     }
 }
 
-// -------------------------------------------- register-round sub-transforms
-//
-// A 2^LR-point sub-transform runs in "rounds" of up to four radix-2 stages.
-// In a round covering stage bits [b, b + e), a thread loads the 2^e elements
-// base + k 2^b (k < 2^e) of one group into registers, runs the e stages
-// there, and writes them back; one barrier separates rounds.  Data sit in
-// shared memory as C interleaved columns, element (row, col) at
-// s[row * C + col].  The stage with half-span 2^st (st = s - b within the
-// round) multiplies by w_{2^(s+1)}^(i mod 2^s), i = base + k 2^b, which is
-// entry (i mod 2^s) << (12 - s) of the table's high part (2^(s+1) <= 2^13).
-
-__host__ __device__ constexpr int rounds_of(int lr) { return (lr + 3) / 4; }
-__host__ __device__ constexpr int round_size(int lr, int rd)
-{
-    return lr / rounds_of(lr) + (rd < lr % rounds_of(lr) ? 1 : 0);
-}
-__host__ __device__ constexpr int round_base(int lr, int rd)  // stages below round rd (DIT order)
-{
-    int b = 0;
-    for (int j = 0; j < rd; j++) b += round_size(lr, j);
-    return b;
-}
-
-__device__ __forceinline__ void bf_dif(uint32_t &x, uint32_t &y, uint2 w, uint32_t q)
-{
-    const uint32_t a = x, b = y;
-    x = add_mod(a, b, q);
-    y = mont_mul_pre(sub_mod(a, b, q), w.x, w.y, q);
-}
-
-__device__ __forceinline__ void bf_dit(uint32_t &x, uint32_t &y, uint2 w, uint32_t q)
-{
-    const uint32_t t = mont_mul_pre(y, w.x, w.y, q);
-    const uint32_t a = x;
-    x = add_mod(a, t, q);
-    y = sub_mod(a, t, q);
-}
-
-// One round of a DIF (forward) or DIT (inverse) sub-transform.
-template <int LR, int C, int B, int E, bool FWD>
-__device__ __forceinline__ void transform_round(uint32_t *s, const uint2 *T, uint32_t q)
-{
-    constexpr int R = 1 << LR;
-    constexpr int NG = C * (R >> E);
-    for (int g = threadIdx.x; g < NG; g += blockDim.x) {
-        const int c = g & (C - 1);
-        const int gg = g / C;
-        const int glow = gg & ((1 << B) - 1);
-        const int base = ((gg >> B) << (B + E)) | glow;
-        uint32_t x[1 << E];
-#pragma unroll
-        for (int k = 0; k < (1 << E); k++) x[k] = s[(base + (k << B)) * C + c];
-        if (FWD) {
-#pragma unroll
-            for (int st = E - 1; st >= 0; st--) {
-#pragma unroll
-                for (int k = 0; k < (1 << E); k++) {
-                    if (k & (1 << st)) continue;
-                    const int p = glow + ((k & ((1 << st) - 1)) << B);
-                    const uint2 w = __ldg(&T[kTwLo + (p << (12 - B - st))]);
-                    bf_dif(x[k], x[k + (1 << st)], w, q);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int st = 0; st < E; st++) {
-#pragma unroll
-                for (int k = 0; k < (1 << E); k++) {
-                    if (k & (1 << st)) continue;
-                    const int p = glow + ((k & ((1 << st) - 1)) << B);
-                    const uint2 w = __ldg(&T[kTwLo + (p << (12 - B - st))]);
-                    bf_dit(x[k], x[k + (1 << st)], w, q);
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < (1 << E); k++) s[(base + (k << B)) * C + c] = x[k];
-    }
-    __syncthreads();
-}
-
-// Forward DIF: rounds from the top stage bits down.  Caller synchronises
-// before; returns synchronised.
-template <int LR, int C>
-__device__ __forceinline__ void dif_block(uint32_t *s, const uint2 *T, uint32_t q)
-{
-    constexpr int NR = rounds_of(LR);
-    if constexpr (NR >= 1) {
-        constexpr int E0 = round_size(LR, 0);
-        transform_round<LR, C, LR - E0, E0, true>(s, T, q);
-    }
-    if constexpr (NR >= 2) {
-        constexpr int E0 = round_size(LR, 0), E1 = round_size(LR, 1);
-        transform_round<LR, C, LR - E0 - E1, E1, true>(s, T, q);
-    }
-    if constexpr (NR >= 3) {
-        constexpr int E0 = round_size(LR, 0), E1 = round_size(LR, 1), E2 = round_size(LR, 2);
-        transform_round<LR, C, LR - E0 - E1 - E2, E2, true>(s, T, q);
-    }
-    if constexpr (NR >= 4) {
-        constexpr int E3 = round_size(LR, 3);
-        transform_round<LR, C, 0, E3, true>(s, T, q);
-    }
-}
-
-// Inverse DIT: rounds from the bottom stage bits up (inverse roots).
-template <int LR, int C>
-__device__ __forceinline__ void dit_block(uint32_t *s, const uint2 *Ti, uint32_t q)
-{
-    constexpr int NR = rounds_of(LR);
-    if constexpr (NR >= 1) transform_round<LR, C, 0, round_size(LR, 0), false>(s, Ti, q);
-    if constexpr (NR >= 2)
-        transform_round<LR, C, round_base(LR, 1), round_size(LR, 1), false>(s, Ti, q);
-    if constexpr (NR >= 3)
-        transform_round<LR, C, round_base(LR, 2), round_size(LR, 2), false>(s, Ti, q);
-    if constexpr (NR >= 4)
-        transform_round<LR, C, round_base(LR, 3), round_size(LR, 3), false>(s, Ti, q);
-}
-
-// ---------------------------------------------------------- column passes
-
-constexpr int kColLogC = 4;     // 16 consecutive columns per thread block
-constexpr int kColC = 1 << kColLogC;
-constexpr int kColThreads = 256;
-constexpr int kColMaxLog = 10;  // rows per column pass: up to 2^10 (64 KiB)
-
-struct ColArgs {
-    uint32_t *data;        // prime p's array at data + p * pstride
-    size_t pstride;
-    int m;                 // block size 2^m (the sub-problem this pass splits)
-    const uint32_t *src;   // first forward pass: limb source (else null)
-    size_t src_tstride;    // limbs between consecutive transforms' sources
-    size_t src_len;        // valid limbs per transform (rest are zero)
-    const uint2 *tw;
-};
-
-// Forward column pass: a 2^LR-point DIF down each of 16 consecutive columns of
-// one block (row stride S = 2^(m-LR)), then element (row, col) times
-// w_M^(col * bitrev(row)).
-template <int LR>
-__global__ void __launch_bounds__(kColThreads) ntt_col_fwd(ColArgs a)
-{
-    extern __shared__ uint32_t sm[];
-    constexpr int R = 1 << LR;
-    constexpr int total = R * kColC;
-    const int p = blockIdx.y;
-    const uint32_t q = c_q[p], qinv = c_qinv[p];
-    const int slog = a.m - LR;
-    const size_t S = (size_t)1 << slog;
-    const size_t groups = S >> kColLogC;
-    const size_t blk = blockIdx.x / groups;
-    const size_t col0 = (blockIdx.x % groups) << kColLogC;
-    uint32_t *base = a.data + p * a.pstride + (blk << a.m);
-    if (a.src) {
-        const uint32_t *src = a.src + blk * a.src_tstride;
-        for (int v = threadIdx.x; v < total; v += kColThreads) {
-            const size_t idx = (size_t)(v >> kColLogC) * S + col0 + (v & (kColC - 1));
-            sm[v] = idx < a.src_len ? reduce32(src[idx], q) : 0u;
-        }
-    } else {
-        for (int v = threadIdx.x; v < total; v += kColThreads)
-            sm[v] = base[(size_t)(v >> kColLogC) * S + col0 + (v & (kColC - 1))];
-    }
-    __syncthreads();
-    const uint2 *T = tw_table(a.tw, p, 0);
-    dif_block<LR, kColC>(sm, T, q);
-    for (int v = threadIdx.x; v < total; v += kColThreads) {
-        const int row = v >> kColLogC;
-        const uint32_t gcol = (uint32_t)(col0 + (v & (kColC - 1)));
-        const uint32_t E = (gcol * bitrev((uint32_t)row, LR)) << (kLogMaxNtt - a.m);
-        uint32_t x = sm[v];
-        if (E) {
-            const uint2 w = tw_get(T, E, q, qinv);
-            x = mont_mul_pre(x, w.x, w.y, q);
-        }
-        base[(size_t)row * S + gcol] = x;
-    }
-}
-
-// Inverse column pass: undo the twiddle, then the DIT down each column.
-template <int LR>
-__global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
-{
-    extern __shared__ uint32_t sm[];
-    constexpr int R = 1 << LR;
-    constexpr int total = R * kColC;
-    const int p = blockIdx.y;
-    const uint32_t q = c_q[p], qinv = c_qinv[p];
-    const int slog = a.m - LR;
-    const size_t S = (size_t)1 << slog;
-    const size_t groups = S >> kColLogC;
-    const size_t blk = blockIdx.x / groups;
-    const size_t col0 = (blockIdx.x % groups) << kColLogC;
-    uint32_t *base = a.data + p * a.pstride + (blk << a.m);
-    const uint2 *Ti = tw_table(a.tw, p, 1);
-    for (int v = threadIdx.x; v < total; v += kColThreads) {
-        const int row = v >> kColLogC;
-        const uint32_t gcol = (uint32_t)(col0 + (v & (kColC - 1)));
-        const uint32_t E = (gcol * bitrev((uint32_t)row, LR)) << (kLogMaxNtt - a.m);
-        uint32_t x = base[(size_t)row * S + gcol];
-        if (E) {
-            const uint2 w = tw_get(Ti, E, q, qinv);
-            x = mont_mul_pre(x, w.x, w.y, q);
-        }
-        sm[v] = x;
-    }
-    __syncthreads();
-    dit_block<LR, kColC>(sm, Ti, q);
-    for (int v = threadIdx.x; v < total; v += kColThreads)
-        base[(size_t)(v >> kColLogC) * S + col0 + (v & (kColC - 1))] = sm[v];
-}
-
-// ------------------------------------------------------------ row pass
-
-enum { PAIR_ADJACENT = 0, PAIR_SQUARE = 1, PAIR_FIRST_TWO = 2 };
-
-constexpr int kRowThreads = 256;
-constexpr int kRowMaxLog = 12;
-
-struct RowArgs {
-    const uint32_t *F;  // forward data after the column passes
-    size_t fpstride;
-    uint32_t *G;        // products (transform domain, then inverse rows)
-    size_t gpstride;
-    int n;              // log2 L
-    int mode;           // which transforms product k multiplies
-    const uint2 *tw;
-    Scale scale;
-};
-
-// Last forward pass of both operands, pointwise product and first inverse
-// pass, on one contiguous row of 2^LR points of product k.
-template <int LR>
-__global__ void __launch_bounds__(kRowThreads) ntt_row_mul(RowArgs a)
-{
-    extern __shared__ uint32_t sm[];
-    constexpr int R = 1 << LR;
-    const int p = blockIdx.y;
-    const uint32_t q = c_q[p], qinv = c_qinv[p];
-    const size_t rows = (size_t)1 << (a.n - LR);
-    const size_t k = blockIdx.x / rows;
-    const size_t row = blockIdx.x % rows;
-    size_t ta, tb;
-    if (a.mode == PAIR_ADJACENT) { ta = 2 * k; tb = 2 * k + 1; }
-    else if (a.mode == PAIR_SQUARE) { ta = k; tb = k; }
-    else { ta = 0; tb = 1; }
-    const uint32_t *fa = a.F + p * a.fpstride + (ta << a.n) + row * R;
-    const uint32_t *fb = a.F + p * a.fpstride + (tb << a.n) + row * R;
-    const uint2 *T = tw_table(a.tw, p, 0);
-    const uint2 *Ti = tw_table(a.tw, p, 1);
-    uint32_t *Z = sm + 2 * R;
-    const uint32_t sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
-    if (a.mode == PAIR_SQUARE) {
-        for (int i = threadIdx.x; i < R; i += kRowThreads) Z[i] = fa[i];
-        __syncthreads();
-        dif_block<LR, 1>(Z, T, q);
-        for (int i = threadIdx.x; i < R; i += kRowThreads) {
-            const uint32_t x = Z[i];
-            Z[i] = mont_mul(mont_mul(x, x, q, qinv), sc, q, qinv);
-        }
-    } else {
-        for (int i = threadIdx.x; i < R; i += kRowThreads) {
-            sm[2 * i] = fa[i];
-            sm[2 * i + 1] = fb[i];
-        }
-        __syncthreads();
-        dif_block<LR, 2>(sm, T, q);
-        for (int i = threadIdx.x; i < R; i += kRowThreads)
-            Z[i] = mont_mul(mont_mul(sm[2 * i], sm[2 * i + 1], q, qinv), sc, q, qinv);
-    }
-    __syncthreads();
-    dit_block<LR, 1>(Z, Ti, q);
-    uint32_t *g = a.G + p * a.gpstride + (k << a.n) + row * R;
-    for (int i = threadIdx.x; i < R; i += kRowThreads) g[i] = Z[i];
-}
+#include "ntt_kernels.cuh"
 
 // ------------------------------------------ whole product in one block
 
@@ -582,7 +308,8 @@ __global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
     uint32_t *Rr[3] = {sm, sm + L, sm + 2 * L};
     uint32_t *rawA = sm + 2 * L;
     uint32_t *rawB = sm + 3 * L;
-    uint32_t *XY = sm + 4 * L;
+    uint32_t *X = sm + 4 * L;  // X [4L,5L), Y [5L,6L): two arrays for the dual rounds
+    uint32_t *Y = X + L;
     const size_t k = blockIdx.x;
     const uint32_t *ga = a.A + k * a.a_tstride;
     const uint32_t *gb = a.B ? a.B + k * a.b_tstride : nullptr;
@@ -598,21 +325,25 @@ __global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
         const uint2 *Ti = tw_table(a.tw, p, 1);
         const uint32_t sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
         for (int i = threadIdx.x; i < L; i += blockDim.x) {
-            XY[2 * i] = reduce32(rawA[i], q);
-            XY[2 * i + 1] = reduce32(gb ? rawB[i] : rawA[i], q);
+            X[swz(i)] = reduce32(rawA[i], q);
+            Y[swz(i)] = reduce32(gb ? rawB[i] : rawA[i], q);
         }
         __syncthreads();
-        dif_block<LR, 2>(XY, T, q);
+        dif_smem<LR, 2>(X, T, q);
         uint32_t *Z = Rr[p];
+        // elementwise in the swizzled space: Z, X, Y share the permutation
         for (int i = threadIdx.x; i < L; i += blockDim.x)
-            Z[i] = mont_mul(mont_mul(XY[2 * i], XY[2 * i + 1], q, qinv), sc, q, qinv);
+            Z[i] = mont_mul(mont_mul(X[i], Y[i], q, qinv), sc, q, qinv);
         __syncthreads();
-        dit_block<LR, 1>(Z, Ti, q);
+        dit_smem<LR, 1>(Z, Ti, q);
     }
     uint32_t *cw0 = sm + 3 * L, *cw1 = cw0 + (L + 2), *cw2 = cw1 + (L + 2);
     for (int i = threadIdx.x; i < L + 2; i += blockDim.x) {
         uint32_t c0 = 0, c1 = 0, c2 = 0;
-        if (i >= 2) crt3(Rr[0][i - 2], Rr[1][i - 2], Rr[2][i - 2], c0, c1, c2);
+        if (i >= 2) {
+            const int j = swz(i - 2);
+            crt3(Rr[0][j], Rr[1][j], Rr[2][j], c0, c1, c2);
+        }
         cw0[i] = c0;
         cw1[i] = c1;
         cw2[i] = c2;
@@ -637,7 +368,7 @@ static NttPlan make_plan(int n)
 {
     NttPlan P;
     P.n = n;
-    P.rrow = std::min(kRowMaxLog, n - kColLogC);
+    P.rrow = std::min(kRowMaxLog, n - kColMinLog);
     int rem = n - P.rrow;
     P.ncol = (rem + kColMaxLog - 1) / kColMaxLog;
     for (int i = 0; i < P.ncol; i++) {
@@ -659,7 +390,7 @@ static void set_smem(K kernel, size_t bytes)
 template <int LR>
 static void launch_col(bool fwd, dim3 grid, cudaStream_t s, const ColArgs &a)
 {
-    const size_t smem = ((size_t)1 << (LR + kColLogC)) * sizeof(uint32_t);
+    const size_t smem = ((size_t)1 << (LR + col_log_c(LR))) * sizeof(uint32_t);
     if (fwd) {
         set_smem(ntt_col_fwd<LR>, smem);
         ntt_col_fwd<LR><<<grid, kColThreads, smem, s>>>(a);
@@ -681,7 +412,7 @@ static void col_pass(Ctx &c, bool fwd, uint32_t *data, size_t pstride, size_t to
     a.src_tstride = src_tstride;
     a.src_len = src_len;
     a.tw = c.twiddles;
-    const size_t ctas = total >> (r + kColLogC);
+    const size_t ctas = total >> (r + col_log_c(r));
     dim3 grid((unsigned)ctas, kNumPrimes);
     // algorithmic bytes: every point of the three prime arrays read and
     // written once (the first forward pass reads limbs instead)
@@ -708,9 +439,15 @@ static void col_pass(Ctx &c, bool fwd, uint32_t *data, size_t pstride, size_t to
 template <int LR>
 static void launch_row(dim3 grid, cudaStream_t s, const RowArgs &a)
 {
-    const size_t smem = ((size_t)3 << LR) * sizeof(uint32_t);
-    set_smem(ntt_row_mul<LR>, smem);
-    ntt_row_mul<LR><<<grid, kRowThreads, smem, s>>>(a);
+    if (a.mode == PAIR_SQUARE) {
+        const size_t smem = ((size_t)1 << kRowMaxLog) * sizeof(uint32_t);
+        set_smem(ntt_row_mul<LR, true>, smem);
+        ntt_row_mul<LR, true><<<grid, kRowThreads, smem, s>>>(a);
+    } else {
+        const size_t smem = ((size_t)2 << kRowMaxLog) * sizeof(uint32_t);
+        set_smem(ntt_row_mul<LR, false>, smem);
+        ntt_row_mul<LR, false><<<grid, kRowThreads, smem, s>>>(a);
+    }
 }
 
 // One operand source of a batched product.
@@ -758,7 +495,7 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     ra.mode = mode;
     ra.tw = c.twiddles;
     ra.scale = make_scale(n);
-    dim3 rgrid((unsigned)(nprod << (n - P.rrow)), kNumPrimes);
+    dim3 rgrid((unsigned)(nprod << (n - kRowMaxLog)), kNumPrimes);
     int tok = prof_begin(c, "ntt_row_mul", s);
     switch (P.rrow) {
     case 9: launch_row<9>(rgrid, s, ra); break;
@@ -808,7 +545,8 @@ static void launch_fused(unsigned grid, cudaStream_t s, const FusedArgs &a)
 {
     const size_t smem = (6 * ((size_t)1 << LR) + 8) * sizeof(uint32_t);
     set_smem(ntt_mul_fused<LR>, smem);
-    ntt_mul_fused<LR><<<grid, kFusedThreads, smem, s>>>(a);
+    const int threads = std::min(kFusedThreads, std::max(64, (1 << LR) / 8));
+    ntt_mul_fused<LR><<<grid, threads, smem, s>>>(a);
 }
 
 static void ntt_mul_small(Ctx &c, int n, size_t nprod, Operand x, Operand y, bool square,
@@ -1027,7 +765,7 @@ static void noalloc_mul(const NoAllocDevice &d, const uint32_t *a, size_t na, co
     ra.mode = PAIR_FIRST_TWO;
     ra.tw = d.twiddles;
     ra.scale = make_scale(n);
-    dim3 rgrid((unsigned)(L >> P.rrow), kNumPrimes);
+    dim3 rgrid((unsigned)(L >> kRowMaxLog), kNumPrimes);
     switch (P.rrow) {
     case 9: launch_row<9>(rgrid, s, ra); break;
     case 10: launch_row<10>(rgrid, s, ra); break;

@@ -1,0 +1,467 @@
+// ntt_kernels.cuh -- the sub-transform engine and the pass kernels of the
+// multi-pass NTT (included once by ntt.cu, after the constants, twiddle
+// helpers and the remaindering code).
+//
+// A 2^LR-point sub-transform runs in "rounds" of up to four radix-2 stages.
+// In a round covering stage bits [B, B + E), a thread holds the 2^E elements
+// base + k 2^B (k < 2^E) of one group in registers and runs the E stages
+// there.  The forward (DIF) rounds go from the top bits down, the inverse
+// (DIT) rounds mirror them from the bottom up.  A pass kernel reads its first
+// round straight from global memory and writes its last round straight to
+// global memory; rounds in between exchange through shared memory (one
+// barrier per round).  Stage s (half-span 2^s) multiplies by
+// w_{2^(s+1)}^(i mod 2^s), entry (i mod 2^s) << (12 - s) of the table's high
+// part (2^(s+1) <= 2^13).
+#pragma once
+
+__host__ __device__ constexpr int rounds_of(int lr) { return (lr + 3) / 4; }
+
+// size of DIF round rd (counted from the top stage bits)
+__host__ __device__ constexpr int round_size(int lr, int rd)
+{
+    return lr / rounds_of(lr) + (rd < lr % rounds_of(lr) ? 1 : 0);
+}
+
+// lowest stage bit of DIF round rd
+__host__ __device__ constexpr int dif_base(int lr, int rd)
+{
+    int b = lr;
+    for (int j = 0; j <= rd; j++) b -= round_size(lr, j);
+    return b;
+}
+
+// DIT round rd (counted from the bottom) mirrors DIF round NR-1-rd
+__host__ __device__ constexpr int dit_size(int lr, int rd)
+{
+    return round_size(lr, rounds_of(lr) - 1 - rd);
+}
+
+__host__ __device__ constexpr int dit_base(int lr, int rd)
+{
+    int b = 0;
+    for (int j = 0; j < rd; j++) b += dit_size(lr, j);
+    return b;
+}
+
+// Shared-memory address swizzle: flips the bank bits by the row-of-32 index,
+// which makes every round's access pattern free of bank conflicts.
+__device__ __forceinline__ int swz(int a) { return a ^ ((a >> 5) & 31); }
+
+__device__ __forceinline__ void bf_dif(uint32_t &x, uint32_t &y, uint2 w, uint32_t q)
+{
+    const uint32_t a = x, b = y;
+    x = add_mod(a, b, q);
+    y = mont_mul_pre(sub_mod(a, b, q), w.x, w.y, q);
+}
+
+__device__ __forceinline__ void bf_dit(uint32_t &x, uint32_t &y, uint2 w, uint32_t q)
+{
+    const uint32_t t = mont_mul_pre(y, w.x, w.y, q);
+    const uint32_t a = x;
+    x = add_mod(a, t, q);
+    y = sub_mod(a, t, q);
+}
+
+template <int E, int B, int NA>
+__device__ __forceinline__ void dif_stages(uint32_t (&x)[NA][1 << E], int glow, const uint2 *T,
+                                           uint32_t q)
+{
+#pragma unroll
+    for (int st = E - 1; st >= 0; st--) {
+#pragma unroll
+        for (int k = 0; k < (1 << E); k++) {
+            if (k & (1 << st)) continue;
+            const int p = glow + ((k & ((1 << st) - 1)) << B);
+            const uint2 w = __ldg(&T[kTwLo + (p << (12 - B - st))]);
+#pragma unroll
+            for (int a = 0; a < NA; a++) bf_dif(x[a][k], x[a][k + (1 << st)], w, q);
+        }
+    }
+}
+
+template <int E, int B, int NA>
+__device__ __forceinline__ void dit_stages(uint32_t (&x)[NA][1 << E], int glow, const uint2 *Ti,
+                                           uint32_t q)
+{
+#pragma unroll
+    for (int st = 0; st < E; st++) {
+#pragma unroll
+        for (int k = 0; k < (1 << E); k++) {
+            if (k & (1 << st)) continue;
+            const int p = glow + ((k & ((1 << st) - 1)) << B);
+            const uint2 w = __ldg(&Ti[kTwLo + (p << (12 - B - st))]);
+#pragma unroll
+            for (int a = 0; a < NA; a++) bf_dit(x[a][k], x[a][k + (1 << st)], w, q);
+        }
+    }
+}
+
+// One round over C independent sub-transforms ("columns") of 2^LR points:
+// every group of this thread is loaded by `in`, transformed, and stored by
+// `out`.  COLFAST: consecutive threads take consecutive columns (strided
+// columns in global memory); otherwise consecutive threads take consecutive
+// groups of one column (contiguous rows in global memory).  No barrier.
+template <int LR, int C, int B, int E, bool FWD, int NA, bool COLFAST, class IN, class OUT>
+__device__ __forceinline__ void round_io(const IN &in, const OUT &out, const uint2 *T, uint32_t q)
+{
+    constexpr int NGC = (1 << LR) >> E;  // groups per column
+    constexpr int NG = C * NGC;
+    for (int g = threadIdx.x; g < NG; g += blockDim.x) {
+        const int c = COLFAST ? (g & (C - 1)) : (g / NGC);
+        const int gg = COLFAST ? (g / C) : (g & (NGC - 1));
+        const int glow = gg & ((1 << B) - 1);
+        const int base = ((gg >> B) << (B + E)) | glow;
+        uint32_t x[NA][1 << E];
+        in.template load<E, B, NA>(x, base, c);
+        if (FWD)
+            dif_stages<E, B, NA>(x, glow, T, q);
+        else
+            dit_stages<E, B, NA>(x, glow, T, q);
+        out.template store<E, B, NA>(x, base, c);
+    }
+}
+
+// NA arrays of 2^LR x C words each, back to back, swizzled.  COLFAST: the
+// columns interleave (point i of column c at i C + c); otherwise each column
+// is contiguous (at c 2^LR + i).
+template <int LR, int C, bool COLFAST>
+struct SmemIO {
+    uint32_t *s;
+    __device__ __forceinline__ static int at(int i, int c)
+    {
+        return COLFAST ? swz(i * C + c) : c * (1 << LR) + swz(i);
+    }
+    template <int E, int B, int NA>
+    __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
+    {
+#pragma unroll
+        for (int a = 0; a < NA; a++)
+#pragma unroll
+            for (int k = 0; k < (1 << E); k++)
+                x[a][k] = s[a * ((1 << LR) * C) + at(base + (k << B), c)];
+    }
+    template <int E, int B, int NA>
+    __device__ __forceinline__ void store(uint32_t (&x)[NA][1 << E], int base, int c) const
+    {
+#pragma unroll
+        for (int a = 0; a < NA; a++)
+#pragma unroll
+            for (int k = 0; k < (1 << E); k++)
+                s[a * ((1 << LR) * C) + at(base + (k << B), c)] = x[a][k];
+    }
+};
+
+// All-shared-memory transforms (used by the one-block multiply).  Caller
+// synchronises before; these return synchronised.
+template <int LR, int NA>
+__device__ __forceinline__ void dif_smem(uint32_t *s, const uint2 *T, uint32_t q)
+{
+    constexpr int NR = rounds_of(LR);
+    SmemIO<LR, 1, true> S{s};
+    round_io<LR, 1, dif_base(LR, 0), round_size(LR, 0), true, NA, true>(S, S, T, q);
+    __syncthreads();
+    if constexpr (NR >= 2) {
+        round_io<LR, 1, dif_base(LR, 1), round_size(LR, 1), true, NA, true>(S, S, T, q);
+        __syncthreads();
+    }
+    if constexpr (NR >= 3) {
+        round_io<LR, 1, dif_base(LR, 2), round_size(LR, 2), true, NA, true>(S, S, T, q);
+        __syncthreads();
+    }
+}
+
+template <int LR, int NA>
+__device__ __forceinline__ void dit_smem(uint32_t *s, const uint2 *Ti, uint32_t q)
+{
+    constexpr int NR = rounds_of(LR);
+    SmemIO<LR, 1, true> S{s};
+    round_io<LR, 1, dit_base(LR, 0), dit_size(LR, 0), false, NA, true>(S, S, Ti, q);
+    __syncthreads();
+    if constexpr (NR >= 2) {
+        round_io<LR, 1, dit_base(LR, 1), dit_size(LR, 1), false, NA, true>(S, S, Ti, q);
+        __syncthreads();
+    }
+    if constexpr (NR >= 3) {
+        round_io<LR, 1, dit_base(LR, 2), dit_size(LR, 2), false, NA, true>(S, S, Ti, q);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------- column passes
+
+// A column pass block holds C columns of 2^LR rows: 16 columns at 2^10 rows
+// (64 KiB), otherwise 2^(13-LR) columns (8192 points, 32 KiB), so that
+// every thread has a group to work on even for short columns.
+__host__ __device__ constexpr int col_log_c(int lr) { return lr >= 10 ? 4 : 13 - lr; }
+constexpr int kColThreads = 512;
+constexpr int kColMinLog = 4;   // columns of at least 2^4 rows
+constexpr int kColMaxLog = 10;  // and at most 2^10
+
+struct ColArgs {
+    uint32_t *data;        // prime p's array at data + p * pstride
+    size_t pstride;
+    int m;                 // block size 2^m (the sub-problem this pass splits)
+    const uint32_t *src;   // first forward pass: limb source (else null)
+    size_t src_tstride;    // limbs between consecutive transforms' sources
+    size_t src_len;        // valid limbs per transform (rest are zero)
+    const uint2 *tw;
+};
+
+// Column tile in global memory: element (row, c) at p[row * S + col0 + c].
+// With `src`, elements come from limbs instead (zero past src_len, reduced).
+struct ColIn {
+    const uint32_t *p;
+    const uint32_t *src;
+    size_t S, col0, src_len;
+    uint32_t q;
+    template <int E, int B, int NA>
+    __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
+    {
+#pragma unroll
+        for (int k = 0; k < (1 << E); k++) {
+            const size_t idx = (size_t)(base + (k << B)) * S + col0 + c;
+            if (src)
+                x[0][k] = idx < src_len ? reduce32(src[idx], q) : 0u;
+            else
+                x[0][k] = p[idx];
+        }
+    }
+};
+
+// Forward pass output: element (row, col) times w_M^(col * bitrev(row)).
+template <int LR>
+struct ColOutTw {
+    uint32_t *p;
+    size_t S, col0;
+    const uint2 *T;
+    uint32_t q, qinv;
+    int shift;  // 27 - m
+    template <int E, int B, int NA>
+    __device__ __forceinline__ void store(uint32_t (&x)[NA][1 << E], int base, int c) const
+    {
+        const uint32_t gcol = (uint32_t)(col0 + c);
+#pragma unroll
+        for (int k = 0; k < (1 << E); k++) {
+            const int row = base + (k << B);
+            const uint32_t e = (gcol * bitrev((uint32_t)row, LR)) << shift;
+            uint32_t v = x[0][k];
+            if (e) {
+                const uint2 w = tw_get(T, e, q, qinv);
+                v = mont_mul_pre(v, w.x, w.y, q);
+            }
+            p[(size_t)row * S + gcol] = v;
+        }
+    }
+};
+
+// Inverse pass input: element (row, col) times w_M^-(col * bitrev(row)).
+template <int LR>
+struct ColInTw {
+    const uint32_t *p;
+    size_t S, col0;
+    const uint2 *Ti;
+    uint32_t q, qinv;
+    int shift;
+    template <int E, int B, int NA>
+    __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
+    {
+        const uint32_t gcol = (uint32_t)(col0 + c);
+#pragma unroll
+        for (int k = 0; k < (1 << E); k++) {
+            const int row = base + (k << B);
+            uint32_t v = p[(size_t)row * S + gcol];
+            const uint32_t e = (gcol * bitrev((uint32_t)row, LR)) << shift;
+            if (e) {
+                const uint2 w = tw_get(Ti, e, q, qinv);
+                v = mont_mul_pre(v, w.x, w.y, q);
+            }
+            x[0][k] = v;
+        }
+    }
+};
+
+struct ColOut {
+    uint32_t *p;
+    size_t S, col0;
+    template <int E, int B, int NA>
+    __device__ __forceinline__ void store(uint32_t (&x)[NA][1 << E], int base, int c) const
+    {
+#pragma unroll
+        for (int k = 0; k < (1 << E); k++) p[(size_t)(base + (k << B)) * S + col0 + c] = x[0][k];
+    }
+};
+
+// Forward column pass: a 2^LR-point DIF down each of C consecutive columns of
+// one block (row stride S = 2^(m-LR)), then the twiddle w_M^(col * bitrev(row)).
+template <int LR>
+__global__ void __launch_bounds__(kColThreads) ntt_col_fwd(ColArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    constexpr int LC = col_log_c(LR), C = 1 << LC;
+    constexpr int NR = rounds_of(LR);
+    const int p = blockIdx.y;
+    const uint32_t q = c_q[p], qinv = c_qinv[p];
+    const size_t S = (size_t)1 << (a.m - LR);
+    const size_t groups = S >> LC;
+    const size_t blk = blockIdx.x / groups;
+    const size_t col0 = (blockIdx.x % groups) << LC;
+    uint32_t *base = a.data + p * a.pstride + (blk << a.m);
+    const uint2 *T = tw_table(a.tw, p, 0);
+    const ColIn in{base, a.src ? a.src + blk * a.src_tstride : nullptr, S, col0, a.src_len, q};
+    const ColOutTw<LR> out{base, S, col0, T, q, qinv, kLogMaxNtt - a.m};
+    if constexpr (NR == 1) {
+        round_io<LR, C, 0, LR, true, 1, true>(in, out, T, q);
+    } else {
+        const SmemIO<LR, C, true> sio{sm};
+        round_io<LR, C, dif_base(LR, 0), round_size(LR, 0), true, 1, true>(in, sio, T, q);
+        __syncthreads();
+        if constexpr (NR == 3) {
+            round_io<LR, C, dif_base(LR, 1), round_size(LR, 1), true, 1, true>(sio, sio, T, q);
+            __syncthreads();
+        }
+        round_io<LR, C, 0, round_size(LR, NR - 1), true, 1, true>(sio, out, T, q);
+    }
+}
+
+// Inverse column pass: undo the twiddle, then the DIT down each column.
+template <int LR>
+__global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    constexpr int LC = col_log_c(LR), C = 1 << LC;
+    constexpr int NR = rounds_of(LR);
+    const int p = blockIdx.y;
+    const uint32_t q = c_q[p], qinv = c_qinv[p];
+    const size_t S = (size_t)1 << (a.m - LR);
+    const size_t groups = S >> LC;
+    const size_t blk = blockIdx.x / groups;
+    const size_t col0 = (blockIdx.x % groups) << LC;
+    uint32_t *base = a.data + p * a.pstride + (blk << a.m);
+    const uint2 *Ti = tw_table(a.tw, p, 1);
+    const ColInTw<LR> in{base, S, col0, Ti, q, qinv, kLogMaxNtt - a.m};
+    const ColOut out{base, S, col0};
+    if constexpr (NR == 1) {
+        round_io<LR, C, 0, LR, false, 1, true>(in, out, Ti, q);
+    } else {
+        const SmemIO<LR, C, true> sio{sm};
+        round_io<LR, C, 0, dit_size(LR, 0), false, 1, true>(in, sio, Ti, q);
+        __syncthreads();
+        if constexpr (NR == 3) {
+            round_io<LR, C, dit_base(LR, 1), dit_size(LR, 1), false, 1, true>(sio, sio, Ti, q);
+            __syncthreads();
+        }
+        round_io<LR, C, dit_base(LR, NR - 1), dit_size(LR, NR - 1), false, 1, true>(sio, out,
+                                                                                     Ti, q);
+    }
+}
+
+// ------------------------------------------------------------ row pass
+
+enum { PAIR_ADJACENT = 0, PAIR_SQUARE = 1, PAIR_FIRST_TWO = 2 };
+
+constexpr int kRowThreads = 256;
+constexpr int kRowMaxLog = 12;
+// rows of 2^LR points per block: 4096 points per block in all
+__host__ __device__ constexpr int row_log_rows(int lr) { return kRowMaxLog - lr; }
+
+struct RowArgs {
+    const uint32_t *F;  // forward data after the column passes
+    size_t fpstride;
+    uint32_t *G;        // products (transform domain, then inverse rows)
+    size_t gpstride;
+    int n;              // log2 L
+    int mode;           // which transforms product k multiplies
+    const uint2 *tw;
+    Scale scale;
+};
+
+// Consecutive rows in global memory (operands a, b): point i of row c at
+// c 2^LR + i from the block's first row.
+template <int LR>
+struct RowIn {
+    const uint32_t *pa, *pb;
+    template <int E, int B, int NA>
+    __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
+    {
+#pragma unroll
+        for (int k = 0; k < (1 << E); k++) {
+            x[0][k] = pa[(c << LR) + base + (k << B)];
+            if (NA > 1) x[NA - 1][k] = pb[(c << LR) + base + (k << B)];
+        }
+    }
+};
+
+template <int LR>
+struct RowOut {
+    uint32_t *p;
+    template <int E, int B, int NA>
+    __device__ __forceinline__ void store(uint32_t (&x)[NA][1 << E], int base, int c) const
+    {
+#pragma unroll
+        for (int k = 0; k < (1 << E); k++) p[(c << LR) + base + (k << B)] = x[0][k];
+    }
+};
+
+// Last forward pass of both operands (or one, squaring), pointwise product
+// and first inverse pass, on 2^(12-LR) consecutive rows of 2^LR points of
+// product k.  The last forward round, the product and the first inverse round
+// share one register round (their stage bits coincide).
+template <int LR, bool SQ>
+__global__ void __launch_bounds__(kRowThreads) ntt_row_mul(RowArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    constexpr int NR = rounds_of(LR);
+    constexpr int NA = SQ ? 1 : 2;
+    constexpr int EL = round_size(LR, NR - 1);
+    constexpr int RB = row_log_rows(LR), C = 1 << RB;
+    static_assert(EL == dit_size(LR, 0), "mirrored rounds");
+    const int p = blockIdx.y;
+    const uint32_t q = c_q[p], qinv = c_qinv[p];
+    const size_t blocks = (size_t)1 << (a.n - LR - RB);  // row blocks per product
+    const size_t k = blockIdx.x / blocks;
+    const size_t off = (blockIdx.x % blocks) << (LR + RB);
+    size_t ta, tb;
+    if (a.mode == PAIR_ADJACENT) { ta = 2 * k; tb = 2 * k + 1; }
+    else if (a.mode == PAIR_SQUARE) { ta = k; tb = k; }
+    else { ta = 0; tb = 1; }
+    const uint32_t *fa = a.F + p * a.fpstride + (ta << a.n) + off;
+    const uint32_t *fb = a.F + p * a.fpstride + (tb << a.n) + off;
+    const uint2 *T = tw_table(a.tw, p, 0);
+    const uint2 *Ti = tw_table(a.tw, p, 1);
+    const uint32_t sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
+    const SmemIO<LR, C, false> sio{sm};
+    // forward rounds but the last
+    round_io<LR, C, dif_base(LR, 0), round_size(LR, 0), true, NA, false>(RowIn<LR>{fa, fb}, sio,
+                                                                          T, q);
+    __syncthreads();
+    if constexpr (NR == 3) {
+        round_io<LR, C, dif_base(LR, 1), round_size(LR, 1), true, NA, false>(sio, sio, T, q);
+        __syncthreads();
+    }
+    // last forward round + pointwise product + first inverse round
+    constexpr int NGC = (1 << LR) >> EL;
+    for (int g = threadIdx.x; g < C * NGC; g += blockDim.x) {
+        const int c = g / NGC;
+        const int base = (g & (NGC - 1)) << EL;
+        uint32_t x[NA][1 << EL];
+        sio.template load<EL, 0, NA>(x, base, c);
+        dif_stages<EL, 0, NA>(x, 0, T, q);
+        uint32_t z[1][1 << EL];
+#pragma unroll
+        for (int j = 0; j < (1 << EL); j++)
+            z[0][j] = mont_mul(mont_mul(x[0][j], x[NA - 1][j], q, qinv), sc, q, qinv);
+        dit_stages<EL, 0, 1>(z, 0, Ti, q);
+        sio.template store<EL, 0, 1>(z, base, c);
+    }
+    __syncthreads();
+    uint32_t *g = a.G + p * a.gpstride + (k << a.n) + off;
+    if constexpr (NR == 2) {
+        round_io<LR, C, dit_base(LR, 1), dit_size(LR, 1), false, 1, false>(sio, RowOut<LR>{g}, Ti,
+                                                                            q);
+    } else {
+        round_io<LR, C, dit_base(LR, 1), dit_size(LR, 1), false, 1, false>(sio, sio, Ti, q);
+        __syncthreads();
+        round_io<LR, C, dit_base(LR, 2), dit_size(LR, 2), false, 1, false>(sio, RowOut<LR>{g}, Ti,
+                                                                            q);
+    }
+}
