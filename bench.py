@@ -31,7 +31,9 @@ sys.path.insert(0, ROOT)
 
 PAPER_N = 2_050_572_903
 METRIC = "sec per exact C(n) at n=2.05e9"
-DOMINANT_CANDIDATES = None  # any kernel may be dominant; picked by device time
+# Integer issue peak of one GB300: 152 SMs x 4 schedulers x 32 lanes, one
+# instruction per scheduler per clock, at the 2,070 MHz maximum SM clock.
+ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
 
 def read_peaks():
@@ -252,18 +254,29 @@ def main():
     dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     roof = None
     if dom:
-        name, (cnt, kms, kbytes) = dom
-        achieved = kbytes / (kms / 1000.0) / 1e9 if kms > 0 else 0.0
-        roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "peak_source": peak_kind, "traffic": None,
-                "launches": cnt, "avg_launch_ms": round(kms / cnt, 4),
-                "algorithmic_bytes_per_launch": kbytes / cnt,
-                "share_of_step": round(kms / ms, 4) if ms > 0 else None}
+        name, (cnt, kms, kbytes, kops) = dom
+        secs = kms / 1000.0
+        gbs = kbytes / secs / 1e9 if secs > 0 else 0.0
+        tops = kops / secs / 1e12 if secs > 0 else 0.0
+        common = {"kernel": name, "launches": cnt, "avg_launch_ms": round(kms / cnt, 4),
+                  "algorithmic_bytes_per_launch": kbytes / cnt,
+                  "algorithmic_ops_per_launch": kops / cnt,
+                  "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
+                  "share_of_step": round(kms / ms, 4) if ms > 0 else None}
+        if kops > 0 and tops / ALU_PEAK_TOPS > gbs / peak:
+            # compute-bound: 32-bit integer instruction issue (see ALU_PEAK_TOPS)
+            roof = {"bound": "alu", "achieved": round(tops, 3), "peak": ALU_PEAK_TOPS,
+                    "unit": "Tops/s", "frac": round(tops / ALU_PEAK_TOPS, 4),
+                    "peak_source": "derived: 152 SMs x 128 lanes x 2.07 GHz",
+                    "traffic": None, **common}
+        else:
+            roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(gbs / peak, 4), "peak_source": peak_kind, "traffic": None,
+                    **common}
     if args.profile_json and rank == 0:
         with open(args.profile_json, "w") as f:
-            json.dump({k: {"launches": v[0], "ms": v[1], "bytes": v[2]} for k, v in prof.items()},
-                      f, indent=1)
+            json.dump({k: {"launches": v[0], "ms": v[1], "bytes": v[2], "ops": v[3]}
+                       for k, v in prof.items()}, f, indent=1)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

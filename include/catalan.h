@@ -85,11 +85,13 @@ int cat_ctx_memory(const cat_ctx *ctx, size_t *in_use, size_t *peak);
 int cat_ctx_set_profiling(cat_ctx *ctx, int on);
 
 /* Totals for the i-th kernel name seen since profiling was switched on:
- * launches, summed device milliseconds and summed algorithmic bytes (the
- * bytes the launch must read and write at minimum).  *name is owned by ctx.
+ * launches, summed device milliseconds, summed algorithmic bytes (the bytes
+ * the launch must read and write at minimum) and summed algorithmic 32-bit
+ * integer operations (the instruction count of the minimal sequence for the
+ * arithmetic the launch performs; 0 where not counted).  *name is owned by ctx.
  * Returns CAT_ERANGE when i is past the last entry. */
 int cat_ctx_profile(const cat_ctx *ctx, size_t i, const char **name, uint64_t *launches,
-                    double *ms, double *bytes);
+                    double *ms, double *bytes, double *ops);
 
 /* ------------------------------------------------------------------ Phase 1
  * Grouped prime factorisation of the quantity (Sec. 3.1, Algorithm 1):
@@ -141,7 +143,7 @@ int bigint_mul(cat_ctx *ctx, const uint32_t *a, size_t na, const uint32_t *b,
  * service that must not meet an out-of-memory failure in the middle of a
  * request.  There is no context: the
  * transform scratch and the twiddle tables live in fixed-size __device__
- * arrays of the library (about 2.4 MB of scratch and 1.2 MB of tables),
+ * arrays of the library (about 2.4 MB of scratch and 0.5 MB of tables),
  * which every GPU that loads the library holds until the process exits.
  *   - Limit: na + nb <= 65,536 limbs; larger products return CAT_ENOMEM.
  *   - out must have room for na + nb limbs (cap >= na + nb, else

@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cat_ctx_profile.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_char_p),
                                   ctypes.POINTER(ctypes.c_uint64),
                                   ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double)]
     L.cat_ctx_profile.restype = i32
     L.catalan_factor.argtypes = [vp, u64, i32, ctypes.POINTER(Factorization), vp]
@@ -140,17 +141,17 @@ class Context:
         self.check(load().cat_ctx_set_profiling(self.handle, 1 if on else 0))
 
     def profile(self) -> dict:
-        """{kernel name: (launches, total ms, total algorithmic bytes)}."""
+        """{kernel name: (launches, total ms, total algorithmic bytes, total ops)}."""
         out = {}
         i = 0
         while True:
             name = ctypes.c_char_p()
-            n, ms, b = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
+            n, ms, b, o = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
             rc = load().cat_ctx_profile(self.handle, i, ctypes.byref(name), ctypes.byref(n),
-                                        ctypes.byref(ms), ctypes.byref(b))
+                                        ctypes.byref(ms), ctypes.byref(b), ctypes.byref(o))
             if rc != 0:
                 break
-            out[name.value.decode()] = (n.value, ms.value, b.value)
+            out[name.value.decode()] = (n.value, ms.value, b.value, o.value)
             i += 1
         return out
 

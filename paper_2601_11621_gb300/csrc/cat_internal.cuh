@@ -36,10 +36,15 @@ void check_cuda(cudaError_t e, const char *what);
 
 constexpr int kNumPrimes = 3;
 constexpr int kLogMaxNtt = 27;  // largest transform: 2^27 points
-constexpr int kTwLoBits = 14;   // twiddle table split: exponent = hi*2^14 + lo
-constexpr int kTwLo = 1 << kTwLoBits;
-constexpr int kTwHi = 1 << (kLogMaxNtt - kTwLoBits);
-constexpr int kTwPerDir = kTwLo + kTwHi;  // uint2 entries per (prime, direction)
+// Twiddle tables per (prime, direction), w the primitive 2^27-th root of
+// unity (or its inverse), entries (Montgomery form, that times q^-1 mod 2^32):
+//   [0, 2^13)               w^(j 2^14): the roots of order <= 2^13 used by
+//                           the butterfly stages of a sub-transform;
+//   three tables of 512     w^j, w^(512 j), w^(2^18 j): any w^E, E < 2^27,
+//                           as a product of three small-table entries.
+constexpr int kTwStage = 1 << 13;
+constexpr int kTwSmall = 512;
+constexpr int kTwPerDir = kTwStage + 3 * kTwSmall;  // uint2 entries per (prime, direction)
 
 __host__ __device__ constexpr uint32_t ntt_prime(int i)
 {
@@ -140,12 +145,14 @@ struct ProfEntry {
     uint64_t launches = 0;
     double ms = 0;
     double bytes = 0;
+    double ops = 0;  // algorithmic 32-bit integer operations
 };
 
 struct ProfPending {
     int idx;
     cudaEvent_t a, b;
     double bytes;
+    double ops;
 };
 
 struct Ctx {
@@ -167,8 +174,11 @@ struct Ctx {
 // profiling is off); prof_end records the stop event and the launch's
 // algorithmic bytes.  prof_resolve turns finished pairs into totals.
 int prof_begin(Ctx &c, const char *name, cudaStream_t s);
-void prof_end(Ctx &c, int token, cudaStream_t s, double bytes);
+void prof_end(Ctx &c, int token, cudaStream_t s, double bytes, double ops = 0);
 void prof_resolve(Ctx &c);
+
+// Fills h[kNumPrimes * 2 * kTwPerDir] with the twiddle tables (host side).
+void twiddle_tables_host(uint2 *h);
 
 // Device allocation from the context's stream-ordered pool (cudaMallocAsync on
 // the device's default memory pool, whose release threshold is raised at

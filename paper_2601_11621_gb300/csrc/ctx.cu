@@ -98,20 +98,21 @@ int prof_begin(Ctx &c, const char *name, cudaStream_t s)
     for (size_t i = 0; i < c.prof.size(); i++)
         if (c.prof[i].name == name) { idx = (int)i; break; }
     if (idx < 0) {
-        c.prof.push_back(ProfEntry{name, 0, 0.0, 0.0});
+        c.prof.push_back(ProfEntry{name, 0, 0.0, 0.0, 0.0});
         idx = (int)c.prof.size() - 1;
     }
-    ProfPending p{idx, take_event(c), take_event(c), 0.0};
+    ProfPending p{idx, take_event(c), take_event(c), 0.0, 0.0};
     CAT_CUDA(cudaEventRecord(p.a, s));
     c.pending.push_back(p);
     return (int)c.pending.size() - 1;
 }
 
-void prof_end(Ctx &c, int token, cudaStream_t s, double bytes)
+void prof_end(Ctx &c, int token, cudaStream_t s, double bytes, double ops)
 {
     if (token < 0) return;
     ProfPending &p = c.pending[token];
     p.bytes = bytes;
+    p.ops = ops;
     CAT_CUDA(cudaEventRecord(p.b, s));
 }
 
@@ -125,6 +126,7 @@ void prof_resolve(Ctx &c)
             e.launches++;
             e.ms += ms;
             e.bytes += p.bytes;
+            e.ops += p.ops;
         }
         c.event_pool.push_back(p.a);
         c.event_pool.push_back(p.b);
@@ -154,37 +156,43 @@ static uint32_t find_generator(uint32_t q)
     }
 }
 
-// Table layout per (prime i, direction d): entries [0, 2^14) hold w^j and
-// entries [2^14, 2^14 + 2^13) hold w^(j 2^14), where w is the primitive
-// 2^27-th root of unity (d = 0) or its inverse (d = 1).  Each entry is
-// (Montgomery form of the power, that value times q^-1 mod 2^32).
-static void build_twiddles(Ctx &c)
+// Powers 1, s, s^2, ... (count of them) of `step` into T, as (Montgomery
+// form, that times q^-1 mod 2^32).
+static void fill_powers(uint2 *T, int count, uint32_t step, uint32_t q)
 {
-    std::vector<uint2> h((size_t)kNumPrimes * 2 * kTwPerDir);
+    const uint32_t qi = inv32(q);
+    uint64_t x = 1;
+    for (int j = 0; j < count; j++) {
+        const uint32_t m = to_mont_c(x, q);
+        T[j] = make_uint2(m, m * qi);
+        x = x * step % q;
+    }
+}
+
+// Table layout per (prime i, direction d), w the primitive 2^27-th root of
+// unity (d = 0) or its inverse (d = 1): see kTwStage / kTwSmall.
+void twiddle_tables_host(uint2 *h)
+{
     for (int i = 0; i < kNumPrimes; i++) {
-        uint32_t q = ntt_prime(i), qi = inv32(q);
-        uint32_t g = find_generator(q);
-        uint32_t w = powmod_u32(g, (q - 1) >> kLogMaxNtt, q);
+        const uint32_t q = ntt_prime(i);
+        const uint32_t w = powmod_u32(find_generator(q), (q - 1) >> kLogMaxNtt, q);
         if (powmod_u32(w, 1u << (kLogMaxNtt - 1), q) != q - 1)
             fail(CAT_ECUDA, "twiddle root check failed");
         for (int d = 0; d < 2; d++) {
-            uint32_t root = d == 0 ? w : powmod_u32(w, (1u << kLogMaxNtt) - 1, q);
-            uint2 *T = &h[((size_t)i * 2 + d) * kTwPerDir];
-            uint64_t x = 1;
-            for (int j = 0; j < kTwLo; j++) {
-                uint32_t m = to_mont_c(x, q);
-                T[j] = make_uint2(m, m * qi);
-                x = x * root % q;
-            }
-            uint32_t step = powmod_u32(root, kTwLo, q);
-            x = 1;
-            for (int j = 0; j < kTwHi; j++) {
-                uint32_t m = to_mont_c(x, q);
-                T[kTwLo + j] = make_uint2(m, m * qi);
-                x = x * step % q;
-            }
+            const uint32_t root = d == 0 ? w : powmod_u32(w, (1u << kLogMaxNtt) - 1, q);
+            uint2 *T = h + ((size_t)i * 2 + d) * kTwPerDir;
+            fill_powers(T, kTwStage, powmod_u32(root, 1u << 14, q), q);
+            fill_powers(T + kTwStage, kTwSmall, root, q);
+            fill_powers(T + kTwStage + kTwSmall, kTwSmall, powmod_u32(root, 1u << 9, q), q);
+            fill_powers(T + kTwStage + 2 * kTwSmall, kTwSmall, powmod_u32(root, 1u << 18, q), q);
         }
     }
+}
+
+static void build_twiddles(Ctx &c)
+{
+    std::vector<uint2> h((size_t)kNumPrimes * 2 * kTwPerDir);
+    twiddle_tables_host(h.data());
     CAT_CUDA(cudaMalloc(&c.twiddles, h.size() * sizeof(uint2)));
     CAT_CUDA(cudaMemcpy(c.twiddles, h.data(), h.size() * sizeof(uint2),
                         cudaMemcpyHostToDevice));

@@ -69,13 +69,17 @@ __device__ __forceinline__ const uint2 *tw_table(const uint2 *tw, int p, int dir
     return tw + ((size_t)p * 2 + dir) * kTwPerDir;
 }
 
-// w^E for E in [0, 2^27), w the primitive 2^27-th root of the table.
-__device__ __forceinline__ uint2 tw_get(const uint2 *T, uint32_t E, uint32_t q, uint32_t qinv)
+// x * w^E for E in [0, 2^27), w the primitive 2^27-th root of the table:
+// three products with entries of the three 512-entry tables (which stay in
+// L1), w^E = w^(E mod 512) * w^(512 ((E >> 9) mod 512)) * w^(2^18 (E >> 18)).
+__device__ __forceinline__ uint32_t tw_apply(uint32_t x, const uint2 *T, uint32_t E, uint32_t q)
 {
-    uint2 lo = __ldg(&T[E & (kTwLo - 1)]);
-    uint2 hi = __ldg(&T[kTwLo + (E >> kTwLoBits)]);
-    uint32_t w = mont_mul_pre(lo.x, hi.x, hi.y, q);
-    return make_uint2(w, w * qinv);
+    const uint2 a = __ldg(&T[kTwStage + (E & (kTwSmall - 1))]);
+    const uint2 b = __ldg(&T[kTwStage + kTwSmall + ((E >> 9) & (kTwSmall - 1))]);
+    const uint2 c = __ldg(&T[kTwStage + 2 * kTwSmall + (E >> 18)]);
+    x = mont_mul_pre(x, a.x, a.y, q);
+    x = mont_mul_pre(x, b.x, b.y, q);
+    return mont_mul_pre(x, c.x, c.y, q);
 }
 
 // ----------------------------------------------- remaindering and carries
@@ -433,7 +437,9 @@ static void col_pass(Ctx &c, bool fwd, uint32_t *data, size_t pstride, size_t to
     default: fail(CAT_EINVAL, "column pass size out of range");
     }
     CAT_LAUNCH(fwd ? "ntt_col_fwd" : "ntt_col_inv");
-    prof_end(c, tok, s, bytes);
+    // algorithmic ops: r/2 butterflies of 12 ops per point and one twiddle
+    // product (11 ops) per point, three primes
+    prof_end(c, tok, s, bytes, 3.0 * (double)total * (6.0 * r + 11.0));
 }
 
 template <int LR>
@@ -505,7 +511,8 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     default: fail(CAT_EINVAL, "row pass size out of range");
     }
     CAT_LAUNCH("ntt_row_mul");
-    prof_end(c, tok, s, (mode == PAIR_SQUARE ? 24.0 : 36.0) * (double)gp);
+    prof_end(c, tok, s, (mode == PAIR_SQUARE ? 24.0 : 36.0) * (double)gp,
+             3.0 * (double)gp * ((mode == PAIR_SQUARE ? 12.0 : 18.0) * P.rrow + 12.0));
     F.reset();
     // inverse column passes, reverse order
     for (int i = P.ncol - 1; i >= 0; i--) {
@@ -527,7 +534,8 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     tok = prof_begin(c, "crt_carry_tiles", s);
     crt_carry_tiles<<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
     CAT_LAUNCH("crt_carry_tiles");
-    prof_end(c, tok, s, 12.0 * (double)gp + 4.0 * (double)nprod * (double)out_len);
+    prof_end(c, tok, s, 12.0 * (double)gp + 4.0 * (double)nprod * (double)out_len,
+             40.0 * (double)gp);
     tok = prof_begin(c, "carry_tile_scan", s);
     carry_tile_scan<<<(unsigned)nprod, 1024, 0, s>>>(maps.get(), tiles);
     CAT_LAUNCH("carry_tile_scan");
@@ -582,7 +590,9 @@ static void ntt_mul_small(Ctx &c, int n, size_t nprod, Operand x, Operand y, boo
     default: fail(CAT_EINVAL, "one-block transform size out of range");
     }
     CAT_LAUNCH("ntt_mul_fused");
-    prof_end(c, tok, s, 4.0 * (double)nprod * (double)(x.len + (square ? 0 : y.len) + out_len));
+    const double Lf = (double)(1u << n);
+    prof_end(c, tok, s, 4.0 * (double)nprod * (double)(x.len + (square ? 0 : y.len) + out_len),
+             (double)nprod * ((square ? 36.0 : 54.0) * Lf * n + 36.0 * Lf + 40.0 * Lf));
 }
 
 static int ceil_log2(size_t x)
@@ -669,24 +679,6 @@ struct NoAllocDevice {
 static NoAllocDevice g_noalloc_dev[64];
 static uint2 g_noalloc_tw_host[(size_t)kNumPrimes * 2 * kTwPerDir];
 
-static uint32_t noalloc_generator(uint32_t q)
-{
-    uint64_t f[16];
-    int nf = 0;
-    uint64_t m = q - 1;
-    for (uint64_t d = 2; d * d <= m; d++)
-        if (m % d == 0) {
-            f[nf++] = d;
-            while (m % d == 0) m /= d;
-        }
-    if (m > 1) f[nf++] = m;
-    for (uint32_t g = 2;; g++) {
-        bool ok = true;
-        for (int i = 0; i < nf && ok; i++) ok = powmod_u32(g, (q - 1) / f[i], q) != 1;
-        if (ok) return g;
-    }
-}
-
 // Once per device, with that device current: resolve the device addresses of
 // the two arrays and fill the twiddle table (same layout as the context's).
 static std::mutex g_noalloc_mutex;
@@ -701,26 +693,10 @@ static int noalloc_setup(int dev)
     d.scratch = (uint32_t *)p;
     if (cudaGetSymbolAddress(&p, g_noalloc_twiddles) != cudaSuccess) return CAT_ECUDA;
     d.twiddles = (uint2 *)p;
-    for (int i = 0; i < kNumPrimes; i++) {
-        const uint32_t q = ntt_prime(i), qi = inv32(q);
-        const uint32_t w = powmod_u32(noalloc_generator(q), (q - 1) >> kLogMaxNtt, q);
-        for (int dir = 0; dir < 2; dir++) {
-            const uint32_t root = dir == 0 ? w : powmod_u32(w, (1u << kLogMaxNtt) - 1, q);
-            uint2 *T = &g_noalloc_tw_host[((size_t)i * 2 + dir) * kTwPerDir];
-            uint64_t x = 1;
-            for (int j = 0; j < kTwLo; j++) {
-                const uint32_t mm = to_mont_c(x, q);
-                T[j] = make_uint2(mm, mm * qi);
-                x = x * root % q;
-            }
-            const uint32_t step = powmod_u32(root, kTwLo, q);
-            x = 1;
-            for (int j = 0; j < kTwHi; j++) {
-                const uint32_t mm = to_mont_c(x, q);
-                T[kTwLo + j] = make_uint2(mm, mm * qi);
-                x = x * step % q;
-            }
-        }
+    try {
+        twiddle_tables_host(g_noalloc_tw_host);
+    } catch (...) {
+        return CAT_ECUDA;
     }
     if (cudaMemcpyToSymbol(g_noalloc_twiddles, g_noalloc_tw_host, sizeof(g_noalloc_tw_host)) !=
         cudaSuccess)

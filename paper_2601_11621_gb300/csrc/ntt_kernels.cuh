@@ -62,6 +62,16 @@ __device__ __forceinline__ void bf_dit(uint32_t &x, uint32_t &y, uint2 w, uint32
     y = sub_mod(a, t, q);
 }
 
+// butterfly with twiddle 1 (same in both directions)
+__device__ __forceinline__ void bf_unit(uint32_t &x, uint32_t &y, uint32_t q)
+{
+    const uint32_t a = x, b = y;
+    x = add_mod(a, b, q);
+    y = sub_mod(a, b, q);
+}
+
+// In a round with B = 0 the twiddle index is a compile-time constant, and the
+// butterflies with (k mod 2^st) = 0 have twiddle w^0 = 1: no multiply.
 template <int E, int B, int NA>
 __device__ __forceinline__ void dif_stages(uint32_t (&x)[NA][1 << E], int glow, const uint2 *T,
                                            uint32_t q)
@@ -71,8 +81,13 @@ __device__ __forceinline__ void dif_stages(uint32_t (&x)[NA][1 << E], int glow, 
 #pragma unroll
         for (int k = 0; k < (1 << E); k++) {
             if (k & (1 << st)) continue;
+            if (B == 0 && (k & ((1 << st) - 1)) == 0) {
+#pragma unroll
+                for (int a = 0; a < NA; a++) bf_unit(x[a][k], x[a][k + (1 << st)], q);
+                continue;
+            }
             const int p = glow + ((k & ((1 << st) - 1)) << B);
-            const uint2 w = __ldg(&T[kTwLo + (p << (12 - B - st))]);
+            const uint2 w = __ldg(&T[p << (12 - B - st)]);
 #pragma unroll
             for (int a = 0; a < NA; a++) bf_dif(x[a][k], x[a][k + (1 << st)], w, q);
         }
@@ -88,8 +103,13 @@ __device__ __forceinline__ void dit_stages(uint32_t (&x)[NA][1 << E], int glow, 
 #pragma unroll
         for (int k = 0; k < (1 << E); k++) {
             if (k & (1 << st)) continue;
+            if (B == 0 && (k & ((1 << st) - 1)) == 0) {
+#pragma unroll
+                for (int a = 0; a < NA; a++) bf_unit(x[a][k], x[a][k + (1 << st)], q);
+                continue;
+            }
             const int p = glow + ((k & ((1 << st) - 1)) << B);
-            const uint2 w = __ldg(&Ti[kTwLo + (p << (12 - B - st))]);
+            const uint2 w = __ldg(&Ti[p << (12 - B - st)]);
 #pragma unroll
             for (int a = 0; a < NA; a++) bf_dit(x[a][k], x[a][k + (1 << st)], w, q);
         }
@@ -245,10 +265,7 @@ struct ColOutTw {
             const int row = base + (k << B);
             const uint32_t e = (gcol * bitrev((uint32_t)row, LR)) << shift;
             uint32_t v = x[0][k];
-            if (e) {
-                const uint2 w = tw_get(T, e, q, qinv);
-                v = mont_mul_pre(v, w.x, w.y, q);
-            }
+            if (e) v = tw_apply(v, T, e, q);
             p[(size_t)row * S + gcol] = v;
         }
     }
@@ -271,10 +288,7 @@ struct ColInTw {
             const int row = base + (k << B);
             uint32_t v = p[(size_t)row * S + gcol];
             const uint32_t e = (gcol * bitrev((uint32_t)row, LR)) << shift;
-            if (e) {
-                const uint2 w = tw_get(Ti, e, q, qinv);
-                v = mont_mul_pre(v, w.x, w.y, q);
-            }
+            if (e) v = tw_apply(v, Ti, e, q);
             x[0][k] = v;
         }
     }
