@@ -198,6 +198,31 @@ int catalan_exact(cat_ctx *ctx, uint64_t n, uint32_t *out, size_t cap,
 int cat_exact_host(cat_ctx *ctx, int kind, uint64_t n, uint32_t *host_out,
                    size_t cap, size_t *out_len, void *stream);
 
+/* ------------------------------------------------------------------ batches
+ * One request of a batch: the quantity `kind` at n. */
+typedef struct {
+    int kind;
+    uint64_t n;
+} cat_request;
+
+/* Limbs a batch needs in total: the sum of cat_bound_limbs over the
+ * requests.  Errors: CAT_EINVAL. */
+int cat_batch_bound(const cat_request *reqs, size_t count, size_t *total);
+
+/* The exact quantities of `count` requests computed together: Phase 1 once
+ * for the batch (one sieve up to the largest limit, exponents for every
+ * request) and Phase 2 as one segmented product tree whose every level, for
+ * all requests at once, is a single batched multiplication (each request's
+ * product runs over its primes with multiplicity e_p, which equals
+ * prod_e Q_e^e of Algorithm 2).  Results go back to back into the device
+ * buffer out (cap limbs, at least cat_batch_bound): request r at
+ * offsets[r] (host array, written by the call; the prefix sums of
+ * cat_bound_limbs), normalised length lengths[r] (host array).
+ * Errors: CAT_EINVAL, CAT_ERANGE (cap too small; lengths[0] = the total
+ * needed), CAT_ENOMEM, CAT_ENOTINTEGRAL, CAT_ECUDA. */
+int cat_exact_batch(cat_ctx *ctx, const cat_request *reqs, size_t count, uint32_t *out,
+                    size_t cap, uint64_t *offsets, uint64_t *lengths, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

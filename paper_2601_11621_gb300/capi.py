@@ -29,7 +29,7 @@ EXPORTED = ["cat_ctx_create", "cat_ctx_destroy", "cat_last_error", "cat_ctx_memo
             "catalan_factor", "cat_factor_free", "cat_factor_copy_primes", "bigint_mul",
             "bigint_mul_noalloc", "bigint_pow",
             "product_tree", "cat_reconstruct", "cat_bound_limbs", "cat_exact",
-            "catalan_exact", "cat_exact_host"]
+            "catalan_exact", "cat_exact_host", "cat_batch_bound", "cat_exact_batch"]
 
 
 class CatError(RuntimeError):
@@ -45,6 +45,10 @@ class Factorization(ctypes.Structure):
                 ("primes", ctypes.c_void_p),
                 ("host_exps", ctypes.POINTER(ctypes.c_uint64)),
                 ("host_offsets", ctypes.POINTER(ctypes.c_uint64))]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_uint64)]
 
 
 _lib = None
@@ -100,6 +104,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.catalan_exact.restype = i32
     L.cat_exact_host.argtypes = [vp, i32, u64, vp, sz, szp, vp]
     L.cat_exact_host.restype = i32
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    L.cat_batch_bound.argtypes = [ctypes.POINTER(Request), sz, szp]
+    L.cat_batch_bound.restype = i32
+    L.cat_exact_batch.argtypes = [vp, ctypes.POINTER(Request), sz, vp, sz, u64p, u64p, vp]
+    L.cat_exact_batch.restype = i32
     _lib = L
     return L
 
@@ -318,6 +327,40 @@ def cat_exact_host(ctx: Context, kind: int, n: int, out: np.ndarray | None = Non
                                     out.ctypes.data_as(ctypes.c_void_p), out.size,
                                     ctypes.byref(m), _stream(stream)))
     return out[:m.value]
+
+
+def _requests(reqs):
+    arr = (Request * max(1, len(reqs)))()
+    for i, (kind, n) in enumerate(reqs):
+        arr[i].kind = int(kind)
+        arr[i].n = int(n)
+    return arr
+
+
+def cat_batch_bound(reqs) -> int:
+    """Total limbs a batch of (kind, n) requests needs."""
+    total = ctypes.c_size_t()
+    rc = load().cat_batch_bound(_requests(reqs), len(reqs), ctypes.byref(total))
+    if rc != 0:
+        raise CatError(rc, "cat_batch_bound")
+    return total.value
+
+
+def cat_exact_batch(ctx: Context, reqs, out=None, stream=None):
+    """All (kind, n) requests computed together.  Returns (out, offsets,
+    lengths): request r's limbs are out[offsets[r] : offsets[r] + lengths[r]]
+    (out an int32 device tensor of uint32 limbs)."""
+    count = len(reqs)
+    cap = cat_batch_bound(reqs)
+    if out is None:
+        out = _empty(cap, f"cuda:{ctx.device}")
+    offs = np.zeros(max(1, count), dtype=np.uint64)
+    lens = np.zeros(max(1, count), dtype=np.uint64)
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    ctx.check(load().cat_exact_batch(ctx.handle, _requests(reqs), count, _ptr(out), out.numel(),
+                                     offs.ctypes.data_as(u64p), lens.ctypes.data_as(u64p),
+                                     _stream(stream)))
+    return out, offs[:count], lens[:count]
 
 
 def to_numpy(t) -> np.ndarray:

@@ -1,0 +1,359 @@
+// batch.cu -- many exact quantities computed together (uneven n, mixed kinds).
+//
+// Phase 1 (Sec. 3.1) once for the whole batch: one sieve up to the largest
+// limit, then one thread per (request, prime) computes e_p (Sec. 2) and the
+// primes of request r are written out e_p times each, request after request.
+// Phase 2 (Sec. 3.2) as one segmented, level-synchronous product tree: every
+// level of every request's tree is multiplied by the same batched launches
+// (schoolbook, one-block transform or multi-pass transform, by slot size).
+// A segment with an odd node count at some level gets a node of value 1
+// appended, so adjacent pairs never straddle two requests.  The product over
+// a request's primes, each repeated e_p times, is prod_e Q_e^e: the powers
+// P_e = Q_e^e of Algorithm 2 are formed inside the tree rather than by
+// separate square-and-multiply chains, which keeps the whole batch in a
+// handful of launches per level.
+#include "cat_internal.cuh"
+#include "legendre.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace cat {
+
+DevBuf<uint32_t> sieve_primes(Ctx &c, uint64_t limit, uint64_t *count, cudaStream_t s);
+void exclusive_scan_u32(Ctx &c, uint32_t *data, size_t n, cudaStream_t s);
+bool comba_level(Ctx &c, const uint32_t *in, size_t slot, size_t nprod, uint32_t *out,
+                 cudaStream_t s);
+void ntt_level(Ctx &c, const uint32_t *level, size_t slot, size_t nprod, uint32_t *out,
+               cudaStream_t s);
+
+namespace {
+
+constexpr int kBatchLeafSlot = 8;
+
+// index r with pre[r] <= t < pre[r+1] (pre ascending, pre[0] = 0)
+__device__ __forceinline__ int find_segment(const uint64_t *pre, int count, uint64_t t)
+{
+    int lo = 0, hi = count;  // pre[lo] <= t < pre[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// pi(limit_r) for each request: binary search in the ascending prime list
+__global__ void count_primes_le(const uint32_t *primes, uint64_t np, const uint64_t *limits,
+                                int count, uint64_t *out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= count) return;
+    uint64_t lo = 0, hi = np;  // first index with primes[i] > limit
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if ((uint64_t)primes[mid] <= limits[r]) lo = mid + 1; else hi = mid;
+    }
+    out[r] = lo;
+}
+
+struct ReqDev {
+    uint32_t n;
+    int kind;
+};
+
+// e_p for flat index t = (request r, prime index t - pre[r]); counts into e
+__global__ void batch_exponents(const uint32_t *primes, const uint64_t *pre, int count,
+                                const ReqDev *reqs, uint32_t *e, unsigned int *negative)
+{
+    const uint64_t total = pre[count];
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int r = find_segment(pre, count, t);
+    const int64_t v = exponent_of(primes[t - pre[r]], reqs[r].n, reqs[r].kind);
+    if (v < 0) atomicOr(negative, 1u);
+    e[t] = v < 0 ? 0u : (uint32_t)v;
+}
+
+// after the scan: pos[t] = first leaf slot of flat index t; write p e times
+__global__ void batch_leaves(const uint32_t *primes, const uint64_t *pre, int count,
+                             const ReqDev *reqs, const uint32_t *pos, uint32_t *leaves)
+{
+    const uint64_t total = pre[count];
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int r = find_segment(pre, count, t);
+    const uint32_t p = primes[t - pre[r]];
+    const int64_t v = exponent_of(p, reqs[r].n, reqs[r].kind);
+    uint32_t at = pos[t];
+    for (int64_t k = 0; k < v; k++) leaves[at++] = p;
+}
+
+// leaf segment start of every request (flat index pre[r] -> its position)
+__global__ void batch_seg_starts(const uint64_t *pre, int count, const uint32_t *pos,
+                                 uint32_t total_leaves, uint64_t *seg)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r > count) return;
+    seg[r] = (r < count && pre[r] < pre[count]) ? pos[pre[r]] : total_leaves;
+}
+
+// node j of segment r = product of its leaves [8j, 8j+8) (missing ones = 1)
+__global__ void batch_leaf_nodes(const uint32_t *leaves, const uint64_t *seg,
+                                 const uint64_t *node_pre, int count, uint32_t *out)
+{
+    const uint64_t total = node_pre[count];
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int r = find_segment(node_pre, count, t);
+    const uint64_t first = seg[r] + (t - node_pre[r]) * kBatchLeafSlot, end = seg[r + 1];
+    uint32_t acc[kBatchLeafSlot];
+#pragma unroll
+    for (int j = 0; j < kBatchLeafSlot; j++) acc[j] = j == 0;
+#pragma unroll
+    for (int k = 0; k < kBatchLeafSlot; k++) {
+        const uint32_t x = first + k < end ? leaves[first + k] : 1u;
+        uint32_t carry = 0;
+#pragma unroll
+        for (int j = 0; j < kBatchLeafSlot; j++) {
+            const uint64_t v = (uint64_t)acc[j] * x + carry;
+            acc[j] = (uint32_t)v;
+            carry = (uint32_t)(v >> 32);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kBatchLeafSlot; j++) out[t * kBatchLeafSlot + j] = acc[j];
+}
+
+// A copy job: `len` limbs from src to dst, then dst zero-filled up to `cap`;
+// src == null writes the value 1.
+struct CopyJob {
+    const uint32_t *src;
+    uint32_t *dst;
+    uint64_t len, cap;
+};
+
+__global__ void batch_copy(const CopyJob *jobs, int njobs)
+{
+    for (int j = blockIdx.y; j < njobs; j += gridDim.y) {
+        const CopyJob J = jobs[j];
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < J.cap;
+             i += (uint64_t)gridDim.x * blockDim.x) {
+            uint32_t v;
+            if (!J.src)
+                v = i == 0;
+            else
+                v = i < J.len ? J.src[i] : 0u;
+            J.dst[i] = v;
+        }
+    }
+}
+
+// normalised length of each output region (one block per request, scanning
+// down from the top)
+__global__ void batch_lengths(const uint32_t *out, const uint64_t *off, const uint64_t *cap,
+                              uint64_t *len)
+{
+    __shared__ unsigned long long best;
+    const int r = blockIdx.x;
+    if (threadIdx.x == 0) best = 0;
+    __syncthreads();
+    const uint32_t *o = out + off[r];
+    const uint64_t n = cap[r];
+    for (uint64_t top = n; top > 0 && best == 0;) {
+        const uint64_t lo = top > blockDim.x ? top - blockDim.x : 0;
+        const uint64_t i = lo + threadIdx.x;
+        if (i < top && o[i]) atomicMax(&best, (unsigned long long)(i + 1));
+        __syncthreads();
+        top = lo;
+    }
+    if (threadIdx.x == 0) len[r] = best;
+}
+
+template <typename T>
+DevBuf<T> upload(Ctx &c, const std::vector<T> &h, cudaStream_t s)
+{
+    DevBuf<T> d(c, h.size() ? h.size() : 1, s);
+    if (!h.empty())
+        CAT_CUDA(cudaMemcpyAsync(d.get(), h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice,
+                                 s));
+    return d;
+}
+
+}  // namespace
+
+// out: the results back to back, request r at offsets[r] with room for
+// bound_limbs(n_r, kind_r) limbs; lengths[r] = normalised length.
+void exact_batch(Ctx &c, const cat_request *reqs, size_t count, uint32_t *out, size_t cap,
+                 uint64_t *offsets, uint64_t *lengths, cudaStream_t s)
+{
+    if (count == 0) return;
+    std::vector<uint64_t> limits(count), caps(count);
+    std::vector<ReqDev> rd(count);
+    uint64_t M = 0, total_cap = 0;
+    for (size_t r = 0; r < count; r++) {
+        if (reqs[r].n >= (1ull << 31)) fail(CAT_EINVAL, "n must be below 2^31");
+        if (reqs[r].kind < CAT_CATALAN || reqs[r].kind > CAT_FACTORIAL)
+            fail(CAT_EINVAL, "unknown kind");
+        rd[r] = ReqDev{(uint32_t)reqs[r].n, reqs[r].kind};
+        limits[r] = reqs[r].kind == CAT_FACTORIAL ? reqs[r].n : 2 * reqs[r].n;
+        M = std::max(M, limits[r]);
+        caps[r] = bound_limbs(reqs[r].n, reqs[r].kind);
+        offsets[r] = total_cap;
+        total_cap += caps[r];
+    }
+    if (total_cap > cap) {
+        lengths[0] = total_cap;
+        fail(CAT_ERANGE, "output capacity too small for the batch");
+    }
+    const int nr = (int)count;
+    // ---- Phase 1: shared sieve, exponents, leaves
+    uint64_t np = 0;
+    DevBuf<uint32_t> primes = sieve_primes(c, std::max<uint64_t>(M, 2), &np, s);
+    DevBuf<uint64_t> d_limits = upload(c, limits, s);
+    DevBuf<uint64_t> d_pi(c, count, s);
+    count_primes_le<<<(nr + 255) / 256, 256, 0, s>>>(primes.get(), np, d_limits.get(), nr,
+                                                     d_pi.get());
+    CAT_LAUNCH("count_primes_le");
+    std::vector<uint64_t> pi(count), pre(count + 1, 0);
+    CAT_CUDA(cudaMemcpyAsync(pi.data(), d_pi.get(), 8 * count, cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    for (size_t r = 0; r < count; r++) pre[r + 1] = pre[r] + pi[r];
+    const uint64_t F = pre[count];
+    if (F >= (1ull << 32)) fail(CAT_EINVAL, "batch too large");
+    DevBuf<uint64_t> d_pre = upload(c, pre, s);
+    DevBuf<ReqDev> d_req = upload(c, rd, s);
+    DevBuf<uint32_t> pos(c, F + 1, s);
+    DevBuf<unsigned int> neg(c, 1, s);
+    CAT_CUDA(cudaMemsetAsync(neg.get(), 0, 4, s));
+    CAT_CUDA(cudaMemsetAsync(pos.get() + F, 0, 4, s));
+    const unsigned fb = (unsigned)((F + 255) / 256);
+    int tok = prof_begin(c, "batch_exponents", s);
+    if (F) batch_exponents<<<fb, 256, 0, s>>>(primes.get(), d_pre.get(), nr, d_req.get(),
+                                              pos.get(), neg.get());
+    CAT_LAUNCH("batch_exponents");
+    prof_end(c, tok, s, 8.0 * (double)F);
+    // exclusive scan over F + 1 entries: pos[F] becomes the total leaf count
+    exclusive_scan_u32(c, pos.get(), F + 1, s);
+    uint32_t total_leaves = 0;
+    unsigned int hneg = 0;
+    CAT_CUDA(cudaMemcpyAsync(&total_leaves, pos.get() + F, 4, cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaMemcpyAsync(&hneg, neg.get(), 4, cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    if (hneg) fail(CAT_ENOTINTEGRAL, "a prime exponent is negative");
+    DevBuf<uint32_t> leaves(c, total_leaves ? total_leaves : 1, s);
+    tok = prof_begin(c, "batch_leaves", s);
+    if (F) batch_leaves<<<fb, 256, 0, s>>>(primes.get(), d_pre.get(), nr, d_req.get(),
+                                           pos.get(), leaves.get());
+    CAT_LAUNCH("batch_leaves");
+    prof_end(c, tok, s, 8.0 * (double)F + 4.0 * total_leaves);
+    DevBuf<uint64_t> d_seg(c, count + 1, s);
+    batch_seg_starts<<<(nr + 256) / 256, 256, 0, s>>>(d_pre.get(), nr, pos.get(), total_leaves,
+                                                      d_seg.get());
+    CAT_LAUNCH("batch_seg_starts");
+    std::vector<uint64_t> seg(count + 1);
+    CAT_CUDA(cudaMemcpyAsync(seg.data(), d_seg.get(), 8 * (count + 1), cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    primes.reset();
+    pos.reset();
+
+    // ---- Phase 2: segmented level-synchronous tree
+    std::vector<CopyJob> finish;
+    std::vector<uint64_t> nodes(count, 0), node_pre(count + 1, 0);
+    for (size_t r = 0; r < count; r++) {
+        const uint64_t L = seg[r + 1] - seg[r];
+        nodes[r] = (L + kBatchLeafSlot - 1) / kBatchLeafSlot;
+        node_pre[r + 1] = node_pre[r] + nodes[r];
+        if (L == 0) finish.push_back(CopyJob{nullptr, out + offsets[r], 1, caps[r]});
+    }
+    size_t slot = kBatchLeafSlot;
+    DevBuf<uint32_t> cur(c, node_pre[count] * slot + 1, s);
+    {
+        DevBuf<uint64_t> d_np = upload(c, node_pre, s);
+        const uint64_t tn = node_pre[count];
+        tok = prof_begin(c, "batch_leaf_nodes", s);
+        if (tn)
+            batch_leaf_nodes<<<(unsigned)((tn + 255) / 256), 256, 0, s>>>(
+                leaves.get(), d_seg.get(), d_np.get(), nr, cur.get());
+        CAT_LAUNCH("batch_leaf_nodes");
+        prof_end(c, tok, s, 4.0 * total_leaves + 32.0 * (double)tn);
+    }
+    leaves.reset();
+    // cur holds, for every still-active request, its nodes (slot limbs each)
+    // at node_pre[r]; requests with exactly one node are finished.
+    for (;;) {
+        std::vector<CopyJob> gather;
+        std::vector<uint64_t> next_pre(count + 1, 0);
+        uint64_t padded = 0;
+        for (size_t r = 0; r < count; r++) {
+            next_pre[r + 1] = next_pre[r];
+            if (nodes[r] == 1) {
+                finish.push_back(CopyJob{cur.get() + node_pre[r] * slot, out + offsets[r],
+                                         std::min<uint64_t>(slot, caps[r]), caps[r]});
+                nodes[r] = 0;
+            } else if (nodes[r] >= 2) {
+                const uint64_t cnt = nodes[r] + (nodes[r] & 1);
+                gather.push_back(CopyJob{cur.get() + node_pre[r] * slot, nullptr,
+                                         nodes[r] * slot, cnt * slot});
+                // dst filled below once the padded array exists
+                next_pre[r + 1] = next_pre[r] + cnt / 2;
+                padded += cnt;
+            }
+        }
+        if (!finish.empty()) {
+            DevBuf<CopyJob> d_jobs = upload(c, finish, s);
+            const int nj = (int)finish.size();
+            batch_copy<<<dim3(64, std::min(nj, 4096)), 256, 0, s>>>(d_jobs.get(), nj);
+            CAT_LAUNCH("batch_copy");
+            CAT_CUDA(cudaStreamSynchronize(s));
+            finish.clear();
+        }
+        if (padded == 0) break;
+        // padded level: each active segment's nodes, plus a node of value 1
+        // when its count is odd
+        DevBuf<uint32_t> lvl(c, padded * slot, s);
+        {
+            uint64_t at = 0;
+            std::vector<CopyJob> jobs;
+            for (auto &g : gather) {
+                const uint64_t n_own = g.len / slot, cnt = g.cap / slot;
+                jobs.push_back(CopyJob{g.src, lvl.get() + at * slot, g.len, g.len});
+                if (cnt > n_own)
+                    jobs.push_back(CopyJob{nullptr, lvl.get() + (at + n_own) * slot, 1, slot});
+                at += cnt;
+            }
+            DevBuf<CopyJob> d_jobs = upload(c, jobs, s);
+            const int nj = (int)jobs.size();
+            tok = prof_begin(c, "batch_gather", s);
+            batch_copy<<<dim3(64, std::min(nj, 4096)), 256, 0, s>>>(d_jobs.get(), nj);
+            CAT_LAUNCH("batch_copy");
+            prof_end(c, tok, s, 8.0 * (double)padded * slot);
+            CAT_CUDA(cudaStreamSynchronize(s));
+        }
+        const size_t nprod = padded / 2, ns = 2 * slot;
+        DevBuf<uint32_t> nxt(c, nprod * ns, s);
+        if (slot > c.comba_max_slot || !comba_level(c, lvl.get(), slot, nprod, nxt.get(), s))
+            ntt_level(c, lvl.get(), slot, nprod, nxt.get(), s);
+        lvl.reset();
+        cur = std::move(nxt);
+        slot = ns;
+        node_pre = next_pre;
+        for (size_t r = 0; r < count; r++) nodes[r] = next_pre[r + 1] - next_pre[r];
+    }
+    // ---- lengths
+    DevBuf<uint64_t> d_off = upload(c, std::vector<uint64_t>(offsets, offsets + count), s);
+    DevBuf<uint64_t> d_cap = upload(c, caps, s);
+    DevBuf<uint64_t> d_len(c, count, s);
+    batch_lengths<<<nr, 256, 0, s>>>(out, d_off.get(), d_cap.get(), d_len.get());
+    CAT_LAUNCH("batch_lengths");
+    CAT_CUDA(cudaMemcpyAsync(lengths, d_len.get(), 8 * count, cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+}
+
+size_t batch_bound(const cat_request *reqs, size_t count)
+{
+    size_t t = 0;
+    for (size_t r = 0; r < count; r++) t += bound_limbs(reqs[r].n, reqs[r].kind);
+    return t;
+}
+
+}  // namespace cat

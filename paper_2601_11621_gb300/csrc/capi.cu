@@ -14,6 +14,9 @@ struct cat_ctx {
 namespace cat {
 void ctx_init(Ctx &c, int device, size_t budget);
 void ctx_release(Ctx &c);
+void exact_batch(Ctx &c, const cat_request *reqs, size_t count, uint32_t *out, size_t cap,
+                 uint64_t *offsets, uint64_t *lengths, cudaStream_t s);
+size_t batch_bound(const cat_request *reqs, size_t count);
 }  // namespace cat
 
 namespace {
@@ -219,6 +222,26 @@ int cat_exact(cat_ctx *ctx, int kind, uint64_t n, uint32_t *out, size_t cap,
             cat::factor_free(ctx->c, &f);
             throw;
         }
+    });
+}
+
+int cat_batch_bound(const cat_request *reqs, size_t count, size_t *total)
+{
+    if (!total || (count && !reqs)) return CAT_EINVAL;
+    for (size_t r = 0; r < count; r++)
+        if (reqs[r].n >= (1ull << 31) || reqs[r].kind < CAT_CATALAN ||
+            reqs[r].kind > CAT_FACTORIAL)
+            return CAT_EINVAL;
+    *total = cat::batch_bound(reqs, count);
+    return CAT_OK;
+}
+
+int cat_exact_batch(cat_ctx *ctx, const cat_request *reqs, size_t count, uint32_t *out,
+                    size_t cap, uint64_t *offsets, uint64_t *lengths, void *stream)
+{
+    if (!ctx || (count && (!reqs || !offsets || !lengths)) || (cap && !out)) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        cat::exact_batch(ctx->c, reqs, count, out, cap, offsets, lengths, as_stream(stream));
     });
 }
 

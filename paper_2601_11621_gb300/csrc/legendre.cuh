@@ -1,0 +1,45 @@
+// legendre.cuh -- the exponent of a prime in the three quantities (Sec. 2,
+// Legendre's formula, and Sec. 3.1, Algorithm 1), shared by the single and
+// batched Phase-1 kernels.  2n < 2^32, so every term floor(m / p^k) is a
+// 32-bit division; primes above sqrt(m) take one division per factorial.
+#pragma once
+
+#include "cat_internal.cuh"
+
+namespace cat {
+
+// v_p(m!) = sum_k floor(m / p^k)
+__device__ __forceinline__ uint32_t legendre32(uint32_t m, uint32_t p)
+{
+    uint32_t s = 0;
+    uint64_t pk = p;
+    while (pk <= m) {
+        s += m / (uint32_t)pk;
+        pk *= p;
+    }
+    return s;
+}
+
+// v_p(x) for x > 0
+__device__ __forceinline__ uint32_t valuation32(uint32_t x, uint32_t p)
+{
+    uint32_t v = 0;
+    while (x % p == 0) {
+        x /= p;
+        v++;
+    }
+    return v;
+}
+
+// e_p by kind: Catalan v_p((2n)!) - 2 v_p(n!) - v_p(n+1); central binomial
+// v_p((2n)!) - 2 v_p(n!); factorial v_p(n!).  c_p = v_p(n+1) is the exponent
+// of p in the trial-division factorisation of n+1 (Algorithm 1 step 2).
+__device__ __forceinline__ int64_t exponent_of(uint32_t p, uint32_t n, int kind)
+{
+    if (kind == CAT_FACTORIAL) return legendre32(n, p);
+    int64_t e = (int64_t)legendre32(2 * n, p) - 2 * (int64_t)legendre32(n, p);
+    if (kind == CAT_CATALAN) e -= valuation32(n + 1, p);
+    return e;
+}
+
+}  // namespace cat

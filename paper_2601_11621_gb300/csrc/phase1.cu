@@ -20,6 +20,7 @@
 // radix sort, pairs with e = 0 dropped in the first pass), so primes stay
 // ascending within each group; group starts are then collected.
 #include "cat_internal.cuh"
+#include "legendre.cuh"
 
 #include <algorithm>
 #include <math.h>
@@ -163,36 +164,6 @@ __global__ void __launch_bounds__(kSieveThreads) sieve_segments(SieveArgs a)
 }
 
 // ----------------------------------------------------------- exponents
-
-// v_p(m!) = sum_k floor(m / p^k)  (Sec. 2)
-__device__ __forceinline__ uint32_t legendre32(uint32_t m, uint32_t p)
-{
-    uint32_t s = 0;
-    uint64_t pk = p;
-    while (pk <= m) {
-        s += m / (uint32_t)pk;
-        pk *= p;
-    }
-    return s;
-}
-
-__device__ __forceinline__ uint32_t valuation32(uint32_t x, uint32_t p)
-{
-    uint32_t v = 0;
-    while (x % p == 0) {
-        x /= p;
-        v++;
-    }
-    return v;
-}
-
-__device__ __forceinline__ int64_t exponent_of(uint32_t p, uint32_t n, int kind)
-{
-    if (kind == CAT_FACTORIAL) return legendre32(n, p);
-    int64_t e = (int64_t)legendre32(2 * n, p) - 2 * (int64_t)legendre32(n, p);
-    if (kind == CAT_CATALAN) e -= valuation32(n + 1, p);
-    return e;
-}
 
 struct ExpandArgs {
     const uint32_t *bits;
@@ -387,6 +358,60 @@ static uint64_t isqrt64(uint64_t x)
     return r;
 }
 
+// The segmented sieve up to `limit` (>= 2): per-segment bitmaps of the odd
+// primes and the exclusive scan of their counts.  sieved = pi(limit).
+struct SieveOut {
+    DevBuf<uint32_t> bits, offsets;
+    uint32_t nsegs = 0;
+    uint64_t sieved = 0;
+};
+
+static SieveOut run_sieve(Ctx &c, uint64_t limit, cudaStream_t s)
+{
+    SieveOut o;
+    const uint64_t root = isqrt64(limit);
+    DevBuf<uint32_t> seeds(c, 8192, s);
+    DevBuf<uint32_t> nseeds(c, 1, s);
+    seed_sieve<<<1, 1024, 0, s>>>((uint32_t)root, seeds.get(), nseeds.get());
+    CAT_LAUNCH("seed_sieve");
+    uint32_t ns = 0;
+    CAT_CUDA(cudaMemcpyAsync(&ns, nseeds.get(), 4, cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    std::vector<uint32_t> hs(ns);
+    if (ns)
+        CAT_CUDA(cudaMemcpyAsync(hs.data(), seeds.get(), 4 * ns, cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    // odd seeds only for the segment sieve
+    const uint32_t *odd = seeds.get() + (ns > 0 && hs[0] == 2 ? 1 : 0);
+    const uint32_t nodd = ns > 0 ? ns - 1 : 0;
+    uint32_t i_med = 0, i_large = 0;
+    for (uint32_t k = 0; k < nodd; k++) {
+        const uint32_t p = hs[k + 1];
+        if (p < kMediumPrime) i_med = k + 1;
+        if (p < kLargePrime) i_large = k + 1;
+    }
+    // segments over odd indices 0..imax (odd number 2i+1 <= limit)
+    const uint32_t imax = (uint32_t)((limit - 1) / 2);
+    o.nsegs = imax / kSegBits + 1;
+    o.bits = DevBuf<uint32_t>(c, (size_t)o.nsegs * kSegWords, s);
+    o.offsets = DevBuf<uint32_t>(c, o.nsegs, s);
+    SieveArgs sa{odd, i_med, i_large, nodd, imax, o.bits.get(), o.offsets.get()};
+    const int tok = prof_begin(c, "sieve_segments", s);
+    sieve_segments<<<o.nsegs, kSieveThreads, 0, s>>>(sa);
+    CAT_LAUNCH("sieve_segments");
+    prof_end(c, tok, s, 4.0 * (double)o.nsegs * kSegWords);
+    uint32_t last_count = 0;
+    CAT_CUDA(cudaMemcpyAsync(&last_count, o.offsets.get() + o.nsegs - 1, 4,
+                             cudaMemcpyDeviceToHost, s));
+    exclusive_scan_u32(c, o.offsets.get(), o.nsegs, s);
+    uint32_t last_off = 0;
+    CAT_CUDA(cudaMemcpyAsync(&last_off, o.offsets.get() + o.nsegs - 1, 4,
+                             cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    o.sieved = (uint64_t)last_off + last_count + 1;  // plus the prime 2
+    return o;
+}
+
 void factor(Ctx &c, uint64_t n, int kind, cat_factorization *out, cudaStream_t s)
 {
     if (n >= (1ull << 31)) fail(CAT_EINVAL, "n must be below 2^31");
@@ -397,48 +422,12 @@ void factor(Ctx &c, uint64_t n, int kind, cat_factorization *out, cudaStream_t s
     DevBuf<uint32_t> primes_out;
     uint64_t sieved = 0, npos = 0;
     if (limit >= 2) {
-        // seeds
-        const uint64_t root = isqrt64(limit);
-        DevBuf<uint32_t> seeds(c, 8192, s);
-        DevBuf<uint32_t> nseeds(c, 1, s);
-        seed_sieve<<<1, 1024, 0, s>>>((uint32_t)root, seeds.get(), nseeds.get());
-        CAT_LAUNCH("seed_sieve");
-        uint32_t ns = 0;
-        CAT_CUDA(cudaMemcpyAsync(&ns, nseeds.get(), 4, cudaMemcpyDeviceToHost, s));
-        CAT_CUDA(cudaStreamSynchronize(s));
-        std::vector<uint32_t> hs(ns);
-        if (ns)
-            CAT_CUDA(cudaMemcpyAsync(hs.data(), seeds.get(), 4 * ns, cudaMemcpyDeviceToHost, s));
-        CAT_CUDA(cudaStreamSynchronize(s));
-        // odd seeds only for the segment sieve
-        const uint32_t *odd = seeds.get() + (ns > 0 && hs[0] == 2 ? 1 : 0);
-        const uint32_t nodd = ns > 0 ? ns - 1 : 0;
-        uint32_t i_med = 0, i_large = 0;
-        for (uint32_t k = 0; k < nodd; k++) {
-            const uint32_t p = hs[k + 1];
-            if (p < kMediumPrime) i_med = k + 1;
-            if (p < kLargePrime) i_large = k + 1;
-        }
-        // segments over odd indices 0..imax (odd number 2i+1 <= limit)
-        const uint32_t imax = (uint32_t)((limit - 1) / 2);
-        const uint32_t nsegs = imax / kSegBits + 1;
-        DevBuf<uint32_t> bits(c, (size_t)nsegs * kSegWords, s);
-        DevBuf<uint32_t> counts(c, nsegs, s);
-        SieveArgs sa{odd, i_med, i_large, nodd, imax, bits.get(), counts.get()};
-        int tok = prof_begin(c, "sieve_segments", s);
-        sieve_segments<<<nsegs, kSieveThreads, 0, s>>>(sa);
-        CAT_LAUNCH("sieve_segments");
-        prof_end(c, tok, s, 4.0 * (double)nsegs * kSegWords);
-        uint32_t last_count = 0;
-        CAT_CUDA(cudaMemcpyAsync(&last_count, counts.get() + nsegs - 1, 4,
-                                 cudaMemcpyDeviceToHost, s));
-        exclusive_scan_u32(c, counts.get(), nsegs, s);
-        uint32_t last_off = 0;
-        CAT_CUDA(cudaMemcpyAsync(&last_off, counts.get() + nsegs - 1, 4,
-                                 cudaMemcpyDeviceToHost, s));
-        CAT_CUDA(cudaStreamSynchronize(s));
-        const uint64_t nodd_primes = (uint64_t)last_off + last_count;
-        sieved = nodd_primes + 1;  // plus the prime 2
+        SieveOut sv = run_sieve(c, limit, s);
+        const uint32_t nsegs = sv.nsegs;
+        sieved = sv.sieved;
+        DevBuf<uint32_t> &bits = sv.bits;
+        DevBuf<uint32_t> &counts = sv.offsets;
+        int tok;
         // exponents
         DevBuf<uint64_t> items(c, sieved, s);
         DevBuf<unsigned int> flags(c, 2, s);
@@ -535,6 +524,59 @@ void factor(Ctx &c, uint64_t n, int kind, cat_factorization *out, cudaStream_t s
     out->exps = d_exps.release();
     out->offsets = d_offs.release();
     out->primes = primes_out.release();
+}
+
+// One block per segment: its primes in order (no exponents).
+__global__ void __launch_bounds__(kSieveThreads) expand_primes(const uint32_t *bits,
+                                                              const uint32_t *seg_offsets,
+                                                              uint32_t *primes)
+{
+    __shared__ uint32_t pre[kSieveThreads];
+    constexpr int kWordsPerThread = kSegWords / kSieveThreads;
+    const uint32_t seg = blockIdx.x;
+    const uint32_t *b = bits + (size_t)seg * kSegWords + threadIdx.x * kWordsPerThread;
+    uint32_t w[kWordsPerThread];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int k = 0; k < kWordsPerThread; k++) {
+        w[k] = b[k];
+        cnt += __popc(w[k]);
+    }
+    pre[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int off = 1; off < kSieveThreads; off <<= 1) {
+        const uint32_t v = threadIdx.x >= (unsigned)off ? pre[threadIdx.x - off] : 0;
+        __syncthreads();
+        pre[threadIdx.x] += v;
+        __syncthreads();
+    }
+    size_t pos = (size_t)seg_offsets[seg] + pre[threadIdx.x] - cnt + 1;  // after the prime 2
+    const uint32_t ibase = seg * (uint32_t)kSegBits + threadIdx.x * kWordsPerThread * 32;
+#pragma unroll
+    for (int k = 0; k < kWordsPerThread; k++) {
+        uint32_t v = w[k];
+        while (v) {
+            const int bb = __ffs(v) - 1;
+            v &= v - 1;
+            primes[pos++] = 2 * (ibase + 32 * k + bb) + 1;
+        }
+    }
+    if (seg == 0 && threadIdx.x == 0) primes[0] = 2;
+}
+
+DevBuf<uint32_t> sieve_primes(Ctx &c, uint64_t limit, uint64_t *count, cudaStream_t s)
+{
+    *count = 0;
+    if (limit < 2) return DevBuf<uint32_t>(c, 1, s);
+    SieveOut sv = run_sieve(c, limit, s);
+    DevBuf<uint32_t> primes(c, sv.sieved, s);
+    const int tok = prof_begin(c, "expand_primes", s);
+    expand_primes<<<sv.nsegs, kSieveThreads, 0, s>>>(sv.bits.get(), sv.offsets.get(),
+                                                      primes.get());
+    CAT_LAUNCH("expand_primes");
+    prof_end(c, tok, s, 4.0 * (double)sv.nsegs * kSegWords + 4.0 * (double)sv.sieved);
+    *count = sv.sieved;
+    return primes;
 }
 
 void factor_free(Ctx &c, cat_factorization *f)
