@@ -214,7 +214,9 @@ int cat_batch_bound(const cat_request *reqs, size_t count, size_t *total);
  * request) and Phase 2 as one segmented product tree whose every level, for
  * all requests at once, is a single batched multiplication (each request's
  * product runs over its primes with multiplicity e_p, which equals
- * prod_e Q_e^e of Algorithm 2).  Results go back to back into the device
+ * prod_e Q_e^e of Algorithm 2).  Factorials with n >= 64, whose exponents
+ * are large, are computed one by one through the grouped path of cat_exact
+ * inside the same call.  Results go back to back into the device
  * buffer out (cap limbs, at least cat_batch_bound): request r at
  * offsets[r] (host array, written by the call; the prefix sums of
  * cat_bound_limbs), normalised length lengths[r] (host array).
@@ -222,6 +224,60 @@ int cat_batch_bound(const cat_request *reqs, size_t count, size_t *total);
  * needed), CAT_ENOMEM, CAT_ENOTINTEGRAL, CAT_ECUDA. */
 int cat_exact_batch(cat_ctx *ctx, const cat_request *reqs, size_t count, uint32_t *out,
                     size_t cap, uint64_t *offsets, uint64_t *lengths, void *stream);
+
+/* ------------------------------------------------------------------ serving
+ * A continuous-batching request engine on one device (the paper has a single
+ * offline run; this is the serving layer around the same computation).
+ * `workers` threads each own a context and a CUDA stream.  An idle worker
+ * admits the queued requests in arrival order while their estimated device
+ * footprint fits its share of hbm_budget_bytes (0 = no cap; at least one
+ * request is always admitted) and at most max_batch of them (0 = 4096), and
+ * computes them together with cat_exact_batch.  Requests that arrive while
+ * batches are running are admitted by the next idle worker, so batches
+ * overlap on the GPU.  Results stay in device memory until released.
+ * All functions are thread-safe. */
+typedef struct cat_server cat_server;
+
+typedef struct {
+    int kind;
+    uint64_t n;
+    const uint32_t *limbs;     /* device pointer, valid until release   */
+    uint64_t length;           /* normalised limb count                  */
+    uint64_t t_submit_ns;      /* steady-clock times of submission,      */
+    uint64_t t_start_ns;       /* admission into a batch and completion  */
+    uint64_t t_end_ns;
+    uint64_t batch;            /* id of the batch that computed it       */
+} cat_server_result;
+
+/* Errors: CAT_EINVAL (workers outside 1..64), CAT_ECUDA. */
+int cat_server_create(int device, size_t hbm_budget_bytes, int workers, size_t max_batch,
+                      cat_server **out);
+
+/* Queues one request; *ticket identifies it.  Errors: CAT_EINVAL. */
+int cat_server_submit(cat_server *sv, int kind, uint64_t n, uint64_t *ticket);
+
+/* CAT_EBUSY while queued or running; CAT_OK with *res filled when done; the
+ * request's error code if it failed; CAT_EINVAL for an unknown ticket. */
+int cat_server_poll(cat_server *sv, uint64_t ticket, cat_server_result *res);
+
+/* As cat_server_poll, waiting up to timeout_ms (CAT_ETIMEOUT if still busy). */
+int cat_server_wait(cat_server *sv, uint64_t ticket, uint64_t timeout_ms,
+                    cat_server_result *res);
+
+/* Copies a finished result (length limbs) into dst (host memory if to_host,
+ * else device memory) of cap limbs; *out_len = its length.  The ticket stays
+ * valid.  Errors: CAT_EBUSY, CAT_ERANGE, CAT_EINVAL, CAT_ECUDA. */
+int cat_server_fetch(cat_server *sv, uint64_t ticket, uint32_t *dst, size_t cap, int to_host,
+                     size_t *out_len);
+
+/* Forgets a finished ticket and frees its result (CAT_EBUSY while pending). */
+int cat_server_release(cat_server *sv, uint64_t ticket);
+
+/* Requests waiting for admission / tickets held (queued, running, done). */
+int cat_server_pending(cat_server *sv, size_t *queued, size_t *total);
+
+/* Stops the workers (running batches finish), frees all results. */
+void cat_server_destroy(cat_server *sv);
 
 #ifdef __cplusplus
 }

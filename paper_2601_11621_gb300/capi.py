@@ -29,7 +29,10 @@ EXPORTED = ["cat_ctx_create", "cat_ctx_destroy", "cat_last_error", "cat_ctx_memo
             "catalan_factor", "cat_factor_free", "cat_factor_copy_primes", "bigint_mul",
             "bigint_mul_noalloc", "bigint_pow",
             "product_tree", "cat_reconstruct", "cat_bound_limbs", "cat_exact",
-            "catalan_exact", "cat_exact_host", "cat_batch_bound", "cat_exact_batch"]
+            "catalan_exact", "cat_exact_host", "cat_batch_bound", "cat_exact_batch",
+            "cat_server_create", "cat_server_submit", "cat_server_poll", "cat_server_wait",
+            "cat_server_fetch", "cat_server_release", "cat_server_pending",
+            "cat_server_destroy"]
 
 
 class CatError(RuntimeError):
@@ -49,6 +52,13 @@ class Factorization(ctypes.Structure):
 
 class Request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_uint64)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_uint64), ("limbs", ctypes.c_void_p),
+                ("length", ctypes.c_uint64), ("t_submit_ns", ctypes.c_uint64),
+                ("t_start_ns", ctypes.c_uint64), ("t_end_ns", ctypes.c_uint64),
+                ("batch", ctypes.c_uint64)]
 
 
 _lib = None
@@ -109,6 +119,23 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cat_batch_bound.restype = i32
     L.cat_exact_batch.argtypes = [vp, ctypes.POINTER(Request), sz, vp, sz, u64p, u64p, vp]
     L.cat_exact_batch.restype = i32
+    resp = ctypes.POINTER(ServerResult)
+    L.cat_server_create.argtypes = [i32, sz, i32, sz, ctypes.POINTER(vp)]
+    L.cat_server_create.restype = i32
+    L.cat_server_submit.argtypes = [vp, i32, u64, u64p]
+    L.cat_server_submit.restype = i32
+    L.cat_server_poll.argtypes = [vp, u64, resp]
+    L.cat_server_poll.restype = i32
+    L.cat_server_wait.argtypes = [vp, u64, u64, resp]
+    L.cat_server_wait.restype = i32
+    L.cat_server_fetch.argtypes = [vp, u64, vp, sz, i32, szp]
+    L.cat_server_fetch.restype = i32
+    L.cat_server_release.argtypes = [vp, u64]
+    L.cat_server_release.restype = i32
+    L.cat_server_pending.argtypes = [vp, szp, szp]
+    L.cat_server_pending.restype = i32
+    L.cat_server_destroy.argtypes = [vp]
+    L.cat_server_destroy.restype = None
     _lib = L
     return L
 

@@ -124,14 +124,6 @@ __global__ void batch_leaf_nodes(const uint32_t *leaves, const uint64_t *seg,
     for (int j = 0; j < kBatchLeafSlot; j++) out[t * kBatchLeafSlot + j] = acc[j];
 }
 
-// A copy job: `len` limbs from src to dst, then dst zero-filled up to `cap`;
-// src == null writes the value 1.
-struct CopyJob {
-    const uint32_t *src;
-    uint32_t *dst;
-    uint64_t len, cap;
-};
-
 __global__ void batch_copy(const CopyJob *jobs, int njobs)
 {
     for (int j = blockIdx.y; j < njobs; j += gridDim.y) {
@@ -181,29 +173,136 @@ DevBuf<T> upload(Ctx &c, const std::vector<T> &h, cudaStream_t s)
 
 }  // namespace
 
-// out: the results back to back, request r at offsets[r] with room for
-// bound_limbs(n_r, kind_r) limbs; lengths[r] = normalised length.
-void exact_batch(Ctx &c, const cat_request *reqs, size_t count, uint32_t *out, size_t cap,
-                 uint64_t *offsets, uint64_t *lengths, cudaStream_t s)
+void run_copy_jobs(Ctx &c, const std::vector<CopyJob> &jobs, cudaStream_t s)
+{
+    if (jobs.empty()) return;
+    DevBuf<CopyJob> d_jobs = upload(c, jobs, s);
+    const int nj = (int)jobs.size();
+    batch_copy<<<dim3(64, std::min(nj, 4096)), 256, 0, s>>>(d_jobs.get(), nj);
+    CAT_LAUNCH("batch_copy");
+    CAT_CUDA(cudaStreamSynchronize(s));
+}
+
+// The segmented level-synchronous product tree (see segmented_tree in
+// cat_internal.cuh).  Level 0 multiplies eight leaves per node; every later
+// level pads each active segment to an even node count with a node of value 1
+// and multiplies adjacent pairs of the whole level in one batched call.
+void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> &seg,
+                    std::vector<TreeRoot> &roots, cudaStream_t s)
+{
+    const size_t count = seg.size() - 1;
+    const int nr = (int)count;
+    std::vector<CopyJob> finish;
+    std::vector<uint64_t> nodes(count, 0), node_pre(count + 1, 0);
+    auto sink = [&](size_t r, const uint32_t *src, uint64_t len) {
+        TreeRoot &t = roots[r];
+        if (!t.dst) {
+            const uint64_t n = std::max<uint64_t>(len, 1);
+            t.big.buf = DevBuf<uint32_t>(c, n, s);
+            t.big.n = n;
+            finish.push_back(CopyJob{src, t.big.buf.get(), src ? len : 1, n});
+        } else {
+            finish.push_back(CopyJob{src, t.dst, src ? std::min<uint64_t>(len, t.cap) : 1, t.cap});
+        }
+    };
+    for (size_t r = 0; r < count; r++) {
+        const uint64_t L = seg[r + 1] - seg[r];
+        nodes[r] = (L + kBatchLeafSlot - 1) / kBatchLeafSlot;
+        node_pre[r + 1] = node_pre[r] + nodes[r];
+        if (L == 0) sink(r, nullptr, 1);
+    }
+    size_t slot = kBatchLeafSlot;
+    DevBuf<uint32_t> cur(c, node_pre[count] * slot + 1, s);
+    {
+        DevBuf<uint64_t> d_seg = upload(c, seg, s);
+        DevBuf<uint64_t> d_np = upload(c, node_pre, s);
+        const uint64_t tn = node_pre[count];
+        const int tok = prof_begin(c, "batch_leaf_nodes", s);
+        if (tn)
+            batch_leaf_nodes<<<(unsigned)((tn + 255) / 256), 256, 0, s>>>(
+                leaves, d_seg.get(), d_np.get(), nr, cur.get());
+        CAT_LAUNCH("batch_leaf_nodes");
+        prof_end(c, tok, s, 4.0 * (double)(seg[count] - seg[0]) + 32.0 * (double)tn);
+        CAT_CUDA(cudaStreamSynchronize(s));
+    }
+    // cur holds, for every still-active segment, its nodes (slot limbs each)
+    // at node_pre[r]; a segment with exactly one node is finished.  A root of
+    // L leaves fits in L limbs.
+    for (;;) {
+        std::vector<CopyJob> gather;
+        std::vector<uint64_t> next_pre(count + 1, 0);
+        uint64_t padded = 0;
+        for (size_t r = 0; r < count; r++) {
+            next_pre[r + 1] = next_pre[r];
+            if (nodes[r] == 1) {
+                sink(r, cur.get() + node_pre[r] * slot,
+                     std::min<uint64_t>(slot, seg[r + 1] - seg[r]));
+                nodes[r] = 0;
+            } else if (nodes[r] >= 2) {
+                const uint64_t cnt = nodes[r] + (nodes[r] & 1);
+                gather.push_back(CopyJob{cur.get() + node_pre[r] * slot, nullptr,
+                                         nodes[r] * slot, cnt * slot});
+                next_pre[r + 1] = next_pre[r] + cnt / 2;
+                padded += cnt;
+            }
+        }
+        if (!finish.empty()) {
+            DevBuf<CopyJob> d_jobs = upload(c, finish, s);
+            const int nj = (int)finish.size();
+            batch_copy<<<dim3(64, std::min(nj, 4096)), 256, 0, s>>>(d_jobs.get(), nj);
+            CAT_LAUNCH("batch_copy");
+            CAT_CUDA(cudaStreamSynchronize(s));
+            finish.clear();
+        }
+        if (padded == 0) break;
+        // padded level: each active segment's nodes, plus a node of value 1
+        // when its count is odd
+        DevBuf<uint32_t> lvl(c, padded * slot, s);
+        {
+            uint64_t at = 0;
+            std::vector<CopyJob> jobs;
+            for (auto &g : gather) {
+                const uint64_t n_own = g.len / slot, cnt = g.cap / slot;
+                jobs.push_back(CopyJob{g.src, lvl.get() + at * slot, g.len, g.len});
+                if (cnt > n_own)
+                    jobs.push_back(CopyJob{nullptr, lvl.get() + (at + n_own) * slot, 1, slot});
+                at += cnt;
+            }
+            DevBuf<CopyJob> d_jobs = upload(c, jobs, s);
+            const int nj = (int)jobs.size();
+            const int tok = prof_begin(c, "batch_gather", s);
+            batch_copy<<<dim3(64, std::min(nj, 4096)), 256, 0, s>>>(d_jobs.get(), nj);
+            CAT_LAUNCH("batch_copy");
+            prof_end(c, tok, s, 8.0 * (double)padded * slot);
+            CAT_CUDA(cudaStreamSynchronize(s));
+        }
+        const size_t nprod = padded / 2, ns = 2 * slot;
+        DevBuf<uint32_t> nxt(c, nprod * ns, s);
+        if (slot > c.comba_max_slot || !comba_level(c, lvl.get(), slot, nprod, nxt.get(), s))
+            ntt_level(c, lvl.get(), slot, nprod, nxt.get(), s);
+        lvl.reset();
+        cur = std::move(nxt);
+        slot = ns;
+        node_pre = next_pre;
+        for (size_t r = 0; r < count; r++) nodes[r] = next_pre[r + 1] - next_pre[r];
+    }
+}
+
+// Batched Phase 1 + Phase 2 for requests whose exponents are small (every
+// prime written e_p times); request r's result goes to out + offsets[r]
+// (room for bound_limbs limbs), its normalised length to lengths[r].
+static void batch_core(Ctx &c, const cat_request *reqs, size_t count, uint32_t *out,
+                       const uint64_t *offsets, uint64_t *lengths, cudaStream_t s)
 {
     if (count == 0) return;
     std::vector<uint64_t> limits(count), caps(count);
     std::vector<ReqDev> rd(count);
-    uint64_t M = 0, total_cap = 0;
+    uint64_t M = 0;
     for (size_t r = 0; r < count; r++) {
-        if (reqs[r].n >= (1ull << 31)) fail(CAT_EINVAL, "n must be below 2^31");
-        if (reqs[r].kind < CAT_CATALAN || reqs[r].kind > CAT_FACTORIAL)
-            fail(CAT_EINVAL, "unknown kind");
         rd[r] = ReqDev{(uint32_t)reqs[r].n, reqs[r].kind};
         limits[r] = reqs[r].kind == CAT_FACTORIAL ? reqs[r].n : 2 * reqs[r].n;
         M = std::max(M, limits[r]);
         caps[r] = bound_limbs(reqs[r].n, reqs[r].kind);
-        offsets[r] = total_cap;
-        total_cap += caps[r];
-    }
-    if (total_cap > cap) {
-        lengths[0] = total_cap;
-        fail(CAT_ERANGE, "output capacity too small for the batch");
     }
     const int nr = (int)count;
     // ---- Phase 1: shared sieve, exponents, leaves
@@ -256,89 +355,14 @@ void exact_batch(Ctx &c, const cat_request *reqs, size_t count, uint32_t *out, s
     primes.reset();
     pos.reset();
 
-    // ---- Phase 2: segmented level-synchronous tree
-    std::vector<CopyJob> finish;
-    std::vector<uint64_t> nodes(count, 0), node_pre(count + 1, 0);
+    // ---- Phase 2: one segmented tree over all requests
+    std::vector<TreeRoot> roots(count);
     for (size_t r = 0; r < count; r++) {
-        const uint64_t L = seg[r + 1] - seg[r];
-        nodes[r] = (L + kBatchLeafSlot - 1) / kBatchLeafSlot;
-        node_pre[r + 1] = node_pre[r] + nodes[r];
-        if (L == 0) finish.push_back(CopyJob{nullptr, out + offsets[r], 1, caps[r]});
+        roots[r].dst = out + offsets[r];
+        roots[r].cap = caps[r];
     }
-    size_t slot = kBatchLeafSlot;
-    DevBuf<uint32_t> cur(c, node_pre[count] * slot + 1, s);
-    {
-        DevBuf<uint64_t> d_np = upload(c, node_pre, s);
-        const uint64_t tn = node_pre[count];
-        tok = prof_begin(c, "batch_leaf_nodes", s);
-        if (tn)
-            batch_leaf_nodes<<<(unsigned)((tn + 255) / 256), 256, 0, s>>>(
-                leaves.get(), d_seg.get(), d_np.get(), nr, cur.get());
-        CAT_LAUNCH("batch_leaf_nodes");
-        prof_end(c, tok, s, 4.0 * total_leaves + 32.0 * (double)tn);
-    }
+    segmented_tree(c, leaves.get(), seg, roots, s);
     leaves.reset();
-    // cur holds, for every still-active request, its nodes (slot limbs each)
-    // at node_pre[r]; requests with exactly one node are finished.
-    for (;;) {
-        std::vector<CopyJob> gather;
-        std::vector<uint64_t> next_pre(count + 1, 0);
-        uint64_t padded = 0;
-        for (size_t r = 0; r < count; r++) {
-            next_pre[r + 1] = next_pre[r];
-            if (nodes[r] == 1) {
-                finish.push_back(CopyJob{cur.get() + node_pre[r] * slot, out + offsets[r],
-                                         std::min<uint64_t>(slot, caps[r]), caps[r]});
-                nodes[r] = 0;
-            } else if (nodes[r] >= 2) {
-                const uint64_t cnt = nodes[r] + (nodes[r] & 1);
-                gather.push_back(CopyJob{cur.get() + node_pre[r] * slot, nullptr,
-                                         nodes[r] * slot, cnt * slot});
-                // dst filled below once the padded array exists
-                next_pre[r + 1] = next_pre[r] + cnt / 2;
-                padded += cnt;
-            }
-        }
-        if (!finish.empty()) {
-            DevBuf<CopyJob> d_jobs = upload(c, finish, s);
-            const int nj = (int)finish.size();
-            batch_copy<<<dim3(64, std::min(nj, 4096)), 256, 0, s>>>(d_jobs.get(), nj);
-            CAT_LAUNCH("batch_copy");
-            CAT_CUDA(cudaStreamSynchronize(s));
-            finish.clear();
-        }
-        if (padded == 0) break;
-        // padded level: each active segment's nodes, plus a node of value 1
-        // when its count is odd
-        DevBuf<uint32_t> lvl(c, padded * slot, s);
-        {
-            uint64_t at = 0;
-            std::vector<CopyJob> jobs;
-            for (auto &g : gather) {
-                const uint64_t n_own = g.len / slot, cnt = g.cap / slot;
-                jobs.push_back(CopyJob{g.src, lvl.get() + at * slot, g.len, g.len});
-                if (cnt > n_own)
-                    jobs.push_back(CopyJob{nullptr, lvl.get() + (at + n_own) * slot, 1, slot});
-                at += cnt;
-            }
-            DevBuf<CopyJob> d_jobs = upload(c, jobs, s);
-            const int nj = (int)jobs.size();
-            tok = prof_begin(c, "batch_gather", s);
-            batch_copy<<<dim3(64, std::min(nj, 4096)), 256, 0, s>>>(d_jobs.get(), nj);
-            CAT_LAUNCH("batch_copy");
-            prof_end(c, tok, s, 8.0 * (double)padded * slot);
-            CAT_CUDA(cudaStreamSynchronize(s));
-        }
-        const size_t nprod = padded / 2, ns = 2 * slot;
-        DevBuf<uint32_t> nxt(c, nprod * ns, s);
-        if (slot > c.comba_max_slot || !comba_level(c, lvl.get(), slot, nprod, nxt.get(), s))
-            ntt_level(c, lvl.get(), slot, nprod, nxt.get(), s);
-        lvl.reset();
-        cur = std::move(nxt);
-        slot = ns;
-        node_pre = next_pre;
-        for (size_t r = 0; r < count; r++) nodes[r] = next_pre[r + 1] - next_pre[r];
-    }
     // ---- lengths
     DevBuf<uint64_t> d_off = upload(c, std::vector<uint64_t>(offsets, offsets + count), s);
     DevBuf<uint64_t> d_cap = upload(c, caps, s);
@@ -347,6 +371,62 @@ void exact_batch(Ctx &c, const cat_request *reqs, size_t count, uint32_t *out, s
     CAT_LAUNCH("batch_lengths");
     CAT_CUDA(cudaMemcpyAsync(lengths, d_len.get(), 8 * count, cudaMemcpyDeviceToHost, s));
     CAT_CUDA(cudaStreamSynchronize(s));
+}
+
+// Factorials beyond this n have exponents far above 1 (v_2(n!) ~ n), so
+// writing every prime e_p times would blow up the tree; they are computed one
+// by one through the grouped path instead.
+constexpr uint64_t kBatchFactorialMax = 64;
+
+// out: the results back to back, request r at offsets[r] with room for
+// bound_limbs(n_r, kind_r) limbs; lengths[r] = normalised length.
+void exact_batch(Ctx &c, const cat_request *reqs, size_t count, uint32_t *out, size_t cap,
+                 uint64_t *offsets, uint64_t *lengths, cudaStream_t s)
+{
+    if (count == 0) return;
+    uint64_t total_cap = 0;
+    for (size_t r = 0; r < count; r++) {
+        if (reqs[r].n >= (1ull << 31)) fail(CAT_EINVAL, "n must be below 2^31");
+        if (reqs[r].kind < CAT_CATALAN || reqs[r].kind > CAT_FACTORIAL)
+            fail(CAT_EINVAL, "unknown kind");
+        offsets[r] = total_cap;
+        total_cap += bound_limbs(reqs[r].n, reqs[r].kind);
+    }
+    if (total_cap > cap) {
+        lengths[0] = total_cap;
+        fail(CAT_ERANGE, "output capacity too small for the batch");
+    }
+    std::vector<cat_request> small;
+    std::vector<uint64_t> small_off, small_len;
+    std::vector<size_t> small_idx, single_idx;
+    for (size_t r = 0; r < count; r++) {
+        if (reqs[r].kind == CAT_FACTORIAL && reqs[r].n >= kBatchFactorialMax) {
+            single_idx.push_back(r);
+        } else {
+            small_idx.push_back(r);
+            small.push_back(reqs[r]);
+            small_off.push_back(offsets[r]);
+        }
+    }
+    small_len.resize(small.size());
+    batch_core(c, small.data(), small.size(), out, small_off.data(), small_len.data(), s);
+    for (size_t i = 0; i < small_idx.size(); i++) lengths[small_idx[i]] = small_len[i];
+    for (size_t r : single_idx) {
+        cat_factorization f{};
+        factor(c, reqs[r].n, reqs[r].kind, &f, s);
+        Big v;
+        try {
+            v = reconstruct(c, &f, s);
+        } catch (...) {
+            factor_free(c, &f);
+            throw;
+        }
+        factor_free(c, &f);
+        const uint64_t capr = bound_limbs(reqs[r].n, reqs[r].kind);
+        if (v.n > capr) fail(CAT_ERANGE, "result longer than its bound");
+        run_copy_jobs(c, {CopyJob{v.buf.get(), out + offsets[r], v.n, capr}}, s);
+        lengths[r] = v.n;
+    }
 }
 
 size_t batch_bound(const cat_request *reqs, size_t count)

@@ -234,6 +234,31 @@ struct Big {
     size_t n = 0;
 };
 
+// A device copy job: `len` limbs from src to dst, then dst zero-filled up to
+// `cap`; src == null writes the value 1.  run_copy_jobs runs a list of them
+// in one launch and waits for it.
+struct CopyJob {
+    const uint32_t *src;
+    uint32_t *dst;
+    uint64_t len, cap;
+};
+void run_copy_jobs(Ctx &c, const std::vector<CopyJob> &jobs, cudaStream_t s);
+
+// Where the product of one segment of a segmented product tree goes: into a
+// caller's region of `cap` limbs (zero-filled above the value), or, with dst
+// null, into `big` (length = an upper bound on the normalised length).
+struct TreeRoot {
+    uint32_t *dst = nullptr;
+    uint64_t cap = 0;
+    Big big;
+};
+
+// Products of the segments leaves[seg[j] .. seg[j+1]) for all j at once: one
+// level-synchronous tree in which every level of every segment is a single
+// batched multiplication.  An empty segment's product is 1.
+void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> &seg,
+                    std::vector<TreeRoot> &roots, cudaStream_t s);
+
 // ------------------------------------------------------- internal entry points
 // (all on stream s; lengths are limb counts)
 

@@ -132,11 +132,60 @@ Big power(Ctx &c, const uint32_t *a, size_t na, uint64_t e, cudaStream_t s)
     return r;
 }
 
+// Factorisations with more exponent groups than this (n! has about 2 sqrt(n))
+// take the bit-decomposed form below; Catalan numbers and central binomials
+// (at most 33 groups) always take Algorithm 2 as written.
+constexpr uint64_t kManyGroups = 64;
+
+// prod_e Q_e^e = prod_b R_b^(2^b), R_b = prod of Q_e over the groups whose
+// exponent has bit b set.  All R_b come from one segmented tree over the
+// primes (segment b = the primes of those groups), then
+// X = R_top; X = X^2 R_b for b below the top bit.  Same integer as
+// Algorithm 2 with about 2 log2(max e) large multiplications instead of one
+// powering chain per group.
+static Big reconstruct_bits(Ctx &c, const cat_factorization *f, cudaStream_t s)
+{
+    uint64_t emax = 0;
+    for (uint64_t g = 0; g < f->num_groups; g++) emax = std::max(emax, f->host_exps[g]);
+    int B = 0;
+    while (B < 64 && (emax >> B)) B++;
+    std::vector<uint64_t> seg(B + 1, 0);
+    for (uint64_t g = 0; g < f->num_groups; g++)
+        for (int b = 0; b < B; b++)
+            if ((f->host_exps[g] >> b) & 1)
+                seg[b + 1] += f->host_offsets[g + 1] - f->host_offsets[g];
+    for (int b = 0; b < B; b++) seg[b + 1] += seg[b];
+    DevBuf<uint32_t> leaves(c, std::max<uint64_t>(seg[B], 1), s);
+    std::vector<CopyJob> jobs;
+    std::vector<uint64_t> at(seg.begin(), seg.end() - 1);
+    for (uint64_t g = 0; g < f->num_groups; g++) {
+        const uint64_t off = f->host_offsets[g], cnt = f->host_offsets[g + 1] - off;
+        if (!cnt) continue;
+        for (int b = 0; b < B; b++)
+            if ((f->host_exps[g] >> b) & 1) {
+                jobs.push_back(CopyJob{f->primes + off, leaves.get() + at[b], cnt, cnt});
+                at[b] += cnt;
+            }
+    }
+    run_copy_jobs(c, jobs, s);
+    std::vector<TreeRoot> R(B);
+    segmented_tree(c, leaves.get(), seg, R, s);
+    leaves.reset();
+    for (int b = 0; b < B; b++) R[b].big.n = trim(c, R[b].big.buf.get(), R[b].big.n, s);
+    Big X = std::move(R[B - 1].big);
+    for (int b = B - 2; b >= 0; b--) {
+        X = mul_big(c, X, X, s);
+        if (seg[b + 1] > seg[b]) X = mul_big(c, X, R[b].big, s);
+    }
+    return X;
+}
+
 // Algorithm 2: Q_e by the tree, P_e = Q_e^e, then the P_e combined by
 // repeatedly multiplying the two shortest (equal-length operands meet
 // first, so intermediates stay as short as possible).
 Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s)
 {
+    if (f->num_groups > kManyGroups) return reconstruct_bits(c, f, s);
     std::vector<Big> P;
     for (uint64_t g = 0; g < f->num_groups; g++) {
         const uint64_t off = f->host_offsets[g], cnt = f->host_offsets[g + 1] - off;
