@@ -36,6 +36,31 @@ METRIC = "sec per exact C(n) at n=2.05e9"
 ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
 
+NTT_SOURCES = ["paper_2601_11621_gb300/csrc/ntt.cu", "paper_2601_11621_gb300/csrc/ntt_kernels.cuh",
+               "paper_2601_11621_gb300/csrc/cat_internal.cuh"]
+
+
+def captured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, or
+    None when there is none or the kernel sources changed since the capture."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in NTT_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    digest = h.hexdigest()[:16]
+    for path in glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_traffic_*.md")):
+        fields = {}
+        for line in open(path):
+            if ":" in line and not line.startswith(" "):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        if fields.get("source_sha256_16") == digest and "traffic_bytes_per_launch" in fields:
+            return float(fields["traffic_bytes_per_launch"])
+    return None
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -255,6 +280,7 @@ def main():
     roof = None
     if dom:
         name, (cnt, kms, kbytes, kops) = dom
+        traffic = captured_traffic(name)
         secs = kms / 1000.0
         gbs = kbytes / secs / 1e9 if secs > 0 else 0.0
         tops = kops / secs / 1e12 if secs > 0 else 0.0
@@ -268,10 +294,10 @@ def main():
             roof = {"bound": "alu", "achieved": round(tops, 3), "peak": ALU_PEAK_TOPS,
                     "unit": "Tops/s", "frac": round(tops / ALU_PEAK_TOPS, 4),
                     "peak_source": "derived: 152 SMs x 128 lanes x 2.07 GHz",
-                    "traffic": None, **common}
+                    "traffic": traffic, **common}
         else:
             roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(gbs / peak, 4), "peak_source": peak_kind, "traffic": None,
+                    "frac": round(gbs / peak, 4), "peak_source": peak_kind, "traffic": traffic,
                     **common}
     if args.profile_json and rank == 0:
         with open(args.profile_json, "w") as f:
