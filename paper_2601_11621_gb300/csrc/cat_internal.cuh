@@ -36,6 +36,14 @@ void check_cuda(cudaError_t e, const char *what);
 
 constexpr int kNumPrimes = 3;
 constexpr int kLogMaxNtt = 27;  // largest transform: 2^27 points
+// Two sets of three NTT primes.  Set 0: q < 2^31 with 2^26 | q - 1, for
+// transforms up to 2^26 points (product ~2^90.5 > 2^25 (2^32 - 1)^2, the
+// largest coefficient when na + nb <= 2^26); q < 2^31 makes a modular add,
+// subtract or Montgomery correction three integer instructions (a min of
+// two candidates).  Set 1: q < 2^32 with 2^27 | q - 1, for 2^27 points
+// (product ~2^93.6 > 2^26 (2^32 - 1)^2).  Primes ascend within a set.
+constexpr int kNumSets = 2;
+constexpr int kLogMaxSmallSet = 26;
 // Twiddle tables per (prime, direction), w the primitive 2^27-th root of
 // unity (or its inverse), entries (Montgomery form, that times q^-1 mod 2^32):
 //   [0, 2^13)               w^(j 2^14): the roots of order <= 2^13 used by
@@ -46,10 +54,17 @@ constexpr int kTwStage = 1 << 13;
 constexpr int kTwSmall = 512;
 constexpr int kTwPerDir = kTwStage + 3 * kTwSmall;  // uint2 entries per (prime, direction)
 
-__host__ __device__ constexpr uint32_t ntt_prime(int i)
+__host__ __device__ constexpr uint32_t ntt_prime(int set, int i)
 {
-    return i == 0 ? 2013265921u : (i == 1 ? 2281701377u : 3221225473u);
+    return set == 0 ? (i == 0 ? 469762049u : (i == 1 ? 1811939329u : 2013265921u))
+                    : (i == 0 ? 2013265921u : (i == 1 ? 2281701377u : 3221225473u));
 }
+
+// log2 of the order of the root of unity the twiddle tables of a set use
+__host__ __device__ constexpr int set_log_root(int set) { return set == 0 ? kLogMaxSmallSet : kLogMaxNtt; }
+
+// the prime set a transform of 2^n points uses
+__host__ __device__ constexpr int set_for(int n) { return n <= kLogMaxSmallSet ? 0 : 1; }
 
 // q^-1 mod 2^32 by Newton's iteration x <- x (2 - q x)
 __host__ __device__ constexpr uint32_t inv32(uint32_t q)
@@ -130,6 +145,61 @@ __device__ __forceinline__ uint32_t reduce32(uint32_t x, uint32_t q)
     return x;
 }
 
+// The same operations for a prime set: S (q < 2^31) takes the min-of-two
+// forms, whose candidates never wrap because 2q < 2^32.
+template <bool S>
+__device__ __forceinline__ uint32_t add_m(uint32_t a, uint32_t b, uint32_t q)
+{
+    if (S) {
+        const uint32_t s = a + b;
+        return min(s, s - q);
+    }
+    return add_mod(a, b, q);
+}
+
+template <bool S>
+__device__ __forceinline__ uint32_t sub_m(uint32_t a, uint32_t b, uint32_t q)
+{
+    if (S) {
+        const uint32_t d = a - b + q;
+        return min(d, d - q);
+    }
+    return sub_mod(a, b, q);
+}
+
+template <bool S>
+__device__ __forceinline__ uint32_t mont_pre(uint32_t a, uint32_t w, uint32_t wp, uint32_t q)
+{
+    if (S) {
+        const uint32_t hi = __umulhi(a, w);
+        const uint32_t m = a * wp;
+        const uint32_t t = hi - __umulhi(m, q) + q;
+        return min(t, t - q);
+    }
+    return mont_mul_pre(a, w, wp, q);
+}
+
+template <bool S>
+__device__ __forceinline__ uint32_t mont(uint32_t a, uint32_t b, uint32_t q, uint32_t qinv)
+{
+    if (S) {
+        const uint32_t hi = __umulhi(a, b);
+        const uint32_t m = (a * b) * qinv;
+        const uint32_t t = hi - __umulhi(m, q) + q;
+        return min(t, t - q);
+    }
+    return mont_mul(a, b, q, qinv);
+}
+
+// x mod q for any 32-bit x: for S one Montgomery product with 2^32 mod q
+// (x 2^32 2^-32), otherwise at most two subtractions (q > 2^30).
+template <bool S>
+__device__ __forceinline__ uint32_t reduce_m(uint32_t x, uint32_t q, uint32_t qinv, uint32_t r1)
+{
+    if (S) return mont<true>(x, r1, q, qinv);
+    return reduce32(x, q);
+}
+
 __device__ __forceinline__ uint32_t bitrev(uint32_t x, int bits)
 {
     return bits == 0 ? 0u : (__brev(x) >> (32 - bits));
@@ -177,7 +247,8 @@ int prof_begin(Ctx &c, const char *name, cudaStream_t s);
 void prof_end(Ctx &c, int token, cudaStream_t s, double bytes, double ops = 0);
 void prof_resolve(Ctx &c);
 
-// Fills h[kNumPrimes * 2 * kTwPerDir] with the twiddle tables (host side).
+// Fills h[kTwTotal] with the twiddle tables of both sets (host side).
+constexpr size_t kTwTotal = (size_t)kNumSets * kNumPrimes * 2 * kTwPerDir;
 void twiddle_tables_host(uint2 *h);
 
 // Device allocation from the context's stream-ordered pool (cudaMallocAsync on

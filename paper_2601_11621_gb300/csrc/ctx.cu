@@ -169,19 +169,23 @@ static void fill_powers(uint2 *T, int count, uint32_t step, uint32_t q)
     }
 }
 
-// Table layout per (prime i, direction d), w the primitive 2^27-th root of
-// unity (d = 0) or its inverse (d = 1): see kTwStage / kTwSmall.
+// Table layout per (set, prime i, direction d), w the primitive 2^L-th root
+// of unity of the set (L = set_log_root) (d = 0) or its inverse (d = 1): see
+// kTwStage / kTwSmall.
 void twiddle_tables_host(uint2 *h)
 {
+    for (int set = 0; set < kNumSets; set++)
     for (int i = 0; i < kNumPrimes; i++) {
-        const uint32_t q = ntt_prime(i);
-        const uint32_t w = powmod_u32(find_generator(q), (q - 1) >> kLogMaxNtt, q);
-        if (powmod_u32(w, 1u << (kLogMaxNtt - 1), q) != q - 1)
+        const int L = set_log_root(set);
+        const uint32_t q = ntt_prime(set, i);
+        if ((q - 1) % (1u << L)) fail(CAT_ECUDA, "prime without the needed roots of unity");
+        const uint32_t w = powmod_u32(find_generator(q), (q - 1) >> L, q);
+        if (powmod_u32(w, 1u << (L - 1), q) != q - 1)
             fail(CAT_ECUDA, "twiddle root check failed");
         for (int d = 0; d < 2; d++) {
-            const uint32_t root = d == 0 ? w : powmod_u32(w, (1u << kLogMaxNtt) - 1, q);
-            uint2 *T = h + ((size_t)i * 2 + d) * kTwPerDir;
-            fill_powers(T, kTwStage, powmod_u32(root, 1u << 14, q), q);
+            const uint32_t root = d == 0 ? w : powmod_u32(w, (1u << L) - 1, q);
+            uint2 *T = h + (((size_t)set * kNumPrimes + i) * 2 + d) * kTwPerDir;
+            fill_powers(T, kTwStage, powmod_u32(root, 1u << (L - 13), q), q);
             fill_powers(T + kTwStage, kTwSmall, root, q);
             fill_powers(T + kTwStage + kTwSmall, kTwSmall, powmod_u32(root, 1u << 9, q), q);
             fill_powers(T + kTwStage + 2 * kTwSmall, kTwSmall, powmod_u32(root, 1u << 18, q), q);
@@ -191,7 +195,7 @@ void twiddle_tables_host(uint2 *h)
 
 static void build_twiddles(Ctx &c)
 {
-    std::vector<uint2> h((size_t)kNumPrimes * 2 * kTwPerDir);
+    std::vector<uint2> h(kTwTotal);
     twiddle_tables_host(h.data());
     CAT_CUDA(cudaMalloc(&c.twiddles, h.size() * sizeof(uint2)));
     CAT_CUDA(cudaMemcpy(c.twiddles, h.data(), h.size() * sizeof(uint2),

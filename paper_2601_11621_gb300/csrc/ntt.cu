@@ -31,30 +31,40 @@ namespace cat {
 
 // --------------------------------------------------------------- constants
 
-__constant__ uint32_t c_q[kNumPrimes] = {ntt_prime(0), ntt_prime(1), ntt_prime(2)};
-__constant__ uint32_t c_qinv[kNumPrimes] = {inv32(ntt_prime(0)), inv32(ntt_prime(1)),
-                                            inv32(ntt_prime(2))};
+__constant__ uint32_t c_q[kNumSets][kNumPrimes] = {
+    {ntt_prime(0, 0), ntt_prime(0, 1), ntt_prime(0, 2)},
+    {ntt_prime(1, 0), ntt_prime(1, 1), ntt_prime(1, 2)}};
+__constant__ uint32_t c_qinv[kNumSets][kNumPrimes] = {
+    {inv32(ntt_prime(0, 0)), inv32(ntt_prime(0, 1)), inv32(ntt_prime(0, 2))},
+    {inv32(ntt_prime(1, 0)), inv32(ntt_prime(1, 1)), inv32(ntt_prime(1, 2))}};
+// 2^32 mod q (Montgomery form of 1), used to reduce raw limbs for set 0
+__constant__ uint32_t c_r1[kNumSets][kNumPrimes] = {
+    {to_mont_c(1, ntt_prime(0, 0)), to_mont_c(1, ntt_prime(0, 1)), to_mont_c(1, ntt_prime(0, 2))},
+    {to_mont_c(1, ntt_prime(1, 0)), to_mont_c(1, ntt_prime(1, 1)), to_mont_c(1, ntt_prime(1, 2))}};
 
-// Garner constants in Montgomery form.
-constexpr uint32_t kQ0 = ntt_prime(0), kQ1 = ntt_prime(1), kQ2 = ntt_prime(2);
-constexpr uint32_t kQinv1 = inv32(kQ1), kQinv2 = inv32(kQ2);
-constexpr uint32_t kInvQ0ModQ1 = to_mont_c(powmod_u32(kQ0 % kQ1, kQ1 - 2, kQ1), kQ1);
-constexpr uint32_t kQ0ModQ2 = to_mont_c(kQ0 % kQ2, kQ2);
-constexpr uint32_t kInvQ0Q1ModQ2 =
-    to_mont_c(powmod_u32(mulmod_u64(kQ0, kQ1, kQ2), kQ2 - 2, kQ2), kQ2);
-static_assert(kQ0 < kQ1 && kQ1 < kQ2, "Garner order assumes q0 < q1 < q2");
+// Garner constants of a set, in Montgomery form.
+template <int PS>
+struct Garner {
+    static constexpr uint32_t q0 = ntt_prime(PS, 0), q1 = ntt_prime(PS, 1), q2 = ntt_prime(PS, 2);
+    static constexpr uint32_t qinv1 = inv32(q1), qinv2 = inv32(q2);
+    static constexpr uint32_t inv_q0_mod_q1 = to_mont_c(powmod_u32(q0 % q1, q1 - 2, q1), q1);
+    static constexpr uint32_t q0_mod_q2 = to_mont_c(q0 % q2, q2);
+    static constexpr uint32_t inv_q0q1_mod_q2 =
+        to_mont_c(powmod_u32(mulmod_u64(q0, q1, q2), q2 - 2, q2), q2);
+    static_assert(q0 < q1 && q1 < q2, "Garner order assumes q0 < q1 < q2");
+};
 
 // Pointwise scale: Montgomery constant R^2 * 2^-n mod q, so that
-// mont_mul(mont_mul(x, y), scale) = x * y * 2^-n.
+// mont(mont(x, y), scale) = x * y * 2^-n.
 struct Scale {
     uint32_t c[kNumPrimes];
 };
 
-static Scale make_scale(int n)
+static Scale make_scale(int set, int n)
 {
     Scale s;
     for (int i = 0; i < kNumPrimes; i++) {
-        uint32_t q = ntt_prime(i);
+        uint32_t q = ntt_prime(set, i);
         uint32_t inv2n = powmod_u32((q + 1) / 2, (uint64_t)n, q);   // 2^-n
         uint32_t r = to_mont_c(inv2n, q);                            // R 2^-n
         s.c[i] = to_mont_c(r, q);                                    // R^2 2^-n
@@ -64,38 +74,42 @@ static Scale make_scale(int n)
 
 // -------------------------------------------------------------- twiddles
 
-__device__ __forceinline__ const uint2 *tw_table(const uint2 *tw, int p, int dir)
+__device__ __forceinline__ const uint2 *tw_table(const uint2 *tw, int set, int p, int dir)
 {
-    return tw + ((size_t)p * 2 + dir) * kTwPerDir;
+    return tw + (((size_t)set * kNumPrimes + p) * 2 + dir) * kTwPerDir;
 }
 
-// x * w^E for E in [0, 2^27), w the primitive 2^27-th root of the table:
+// x * w^E for E below the set's root order, w the set's root of unity:
 // three products with entries of the three 512-entry tables (which stay in
 // L1), w^E = w^(E mod 512) * w^(512 ((E >> 9) mod 512)) * w^(2^18 (E >> 18)).
+template <bool S>
 __device__ __forceinline__ uint32_t tw_apply(uint32_t x, const uint2 *T, uint32_t E, uint32_t q)
 {
     const uint2 a = __ldg(&T[kTwStage + (E & (kTwSmall - 1))]);
     const uint2 b = __ldg(&T[kTwStage + kTwSmall + ((E >> 9) & (kTwSmall - 1))]);
     const uint2 c = __ldg(&T[kTwStage + 2 * kTwSmall + (E >> 18)]);
-    x = mont_mul_pre(x, a.x, a.y, q);
-    x = mont_mul_pre(x, b.x, b.y, q);
-    return mont_mul_pre(x, c.x, c.y, q);
+    x = mont_pre<S>(x, a.x, a.y, q);
+    x = mont_pre<S>(x, b.x, b.y, q);
+    return mont_pre<S>(x, c.x, c.y, q);
 }
 
 // ----------------------------------------------- remaindering and carries
 
 // Garner: the coefficient c < q0 q1 q2 with c = r_i mod q_i, as three words.
+template <int PS>
 __device__ __forceinline__ void crt3(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t &c0,
                                      uint32_t &c1, uint32_t &c2)
 {
-    const uint32_t x0 = r0;
-    const uint32_t x1 = mont_mul(sub_mod(r1, x0, kQ1), kInvQ0ModQ1, kQ1, kQinv1);
-    uint32_t t = sub_mod(r2, x0, kQ2);
-    t = sub_mod(t, mont_mul(x1, kQ0ModQ2, kQ2, kQinv2), kQ2);
-    const uint32_t x2 = mont_mul(t, kInvQ0Q1ModQ2, kQ2, kQinv2);
-    const uint64_t y = (uint64_t)kQ1 * x2 + x1;                 // < q1 q2
-    const uint64_t lo = (uint64_t)kQ0 * (uint32_t)y + x0;
-    const uint64_t hi = (uint64_t)kQ0 * (uint32_t)(y >> 32) + (lo >> 32);
+    using G = Garner<PS>;
+    constexpr bool S = PS == 0;
+    const uint32_t x0 = r0;  // < q0 < q1 < q2
+    const uint32_t x1 = mont<S>(sub_m<S>(r1, x0, G::q1), G::inv_q0_mod_q1, G::q1, G::qinv1);
+    uint32_t t = sub_m<S>(r2, x0, G::q2);
+    t = sub_m<S>(t, mont<S>(x1, G::q0_mod_q2, G::q2, G::qinv2), G::q2);
+    const uint32_t x2 = mont<S>(t, G::inv_q0q1_mod_q2, G::q2, G::qinv2);
+    const uint64_t y = (uint64_t)G::q1 * x2 + x1;                 // < q1 q2
+    const uint64_t lo = (uint64_t)G::q0 * (uint32_t)y + x0;
+    const uint64_t hi = (uint64_t)G::q0 * (uint32_t)(y >> 32) + (lo >> 32);
     c0 = (uint32_t)lo;
     c1 = (uint32_t)hi;
     c2 = (uint32_t)(hi >> 32);
@@ -218,6 +232,7 @@ struct CrtArgs {
     uint8_t *tile_maps; // [product][tiles]
 };
 
+template <int PS>
 __global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
 {
     __shared__ uint32_t cw[3][kTile + 2];
@@ -230,7 +245,7 @@ __global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
     for (int i = threadIdx.x; i < kTile + 2; i += blockDim.x) {
         const long j = j0 + i - 2;
         uint32_t c0 = 0, c1 = 0, c2 = 0;
-        if (j >= 0) crt3(g0[j], g0[a.gpstride + j], g0[2 * a.gpstride + j], c0, c1, c2);
+        if (j >= 0) crt3<PS>(g0[j], g0[a.gpstride + j], g0[2 * a.gpstride + j], c0, c1, c2);
         cw[0][i] = c0;
         cw[1][i] = c1;
         cw[2][i] = c2;
@@ -324,20 +339,20 @@ __global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
     __syncthreads();
 #pragma unroll 1
     for (int p = 0; p < kNumPrimes; p++) {
-        const uint32_t q = c_q[p], qinv = c_qinv[p];
-        const uint2 *T = tw_table(a.tw, p, 0);
-        const uint2 *Ti = tw_table(a.tw, p, 1);
+        const uint32_t q = c_q[0][p], qinv = c_qinv[0][p], r1 = c_r1[0][p];
+        const uint2 *T = tw_table(a.tw, 0, p, 0);
+        const uint2 *Ti = tw_table(a.tw, 0, p, 1);
         const uint32_t sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
         for (int i = threadIdx.x; i < L; i += blockDim.x) {
-            X[swz(i)] = reduce32(rawA[i], q);
-            Y[swz(i)] = reduce32(gb ? rawB[i] : rawA[i], q);
+            X[swz(i)] = reduce_m<true>(rawA[i], q, qinv, r1);
+            Y[swz(i)] = reduce_m<true>(gb ? rawB[i] : rawA[i], q, qinv, r1);
         }
         __syncthreads();
         dif_smem<LR, 2>(X, T, q);
         uint32_t *Z = Rr[p];
         // elementwise in the swizzled space: Z, X, Y share the permutation
         for (int i = threadIdx.x; i < L; i += blockDim.x)
-            Z[i] = mont_mul(mont_mul(X[i], Y[i], q, qinv), sc, q, qinv);
+            Z[i] = mont<true>(mont<true>(X[i], Y[i], q, qinv), sc, q, qinv);
         __syncthreads();
         dit_smem<LR, 1>(Z, Ti, q);
     }
@@ -346,7 +361,7 @@ __global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
         uint32_t c0 = 0, c1 = 0, c2 = 0;
         if (i >= 2) {
             const int j = swz(i - 2);
-            crt3(Rr[0][j], Rr[1][j], Rr[2][j], c0, c1, c2);
+            crt3<0>(Rr[0][j], Rr[1][j], Rr[2][j], c0, c1, c2);
         }
         cw0[i] = c0;
         cw1[i] = c1;
@@ -391,21 +406,22 @@ static void set_smem(K kernel, size_t bytes)
                                       (int)bytes));
 }
 
-template <int LR>
+template <int LR, int PS>
 static void launch_col(bool fwd, dim3 grid, cudaStream_t s, const ColArgs &a)
 {
     const size_t smem = ((size_t)1 << (LR + col_log_c(LR))) * sizeof(uint32_t);
     if (fwd) {
-        set_smem(ntt_col_fwd<LR>, smem);
-        ntt_col_fwd<LR><<<grid, kColThreads, smem, s>>>(a);
+        set_smem(ntt_col_fwd<LR, PS>, smem);
+        ntt_col_fwd<LR, PS><<<grid, kColThreads, smem, s>>>(a);
     } else {
-        set_smem(ntt_col_inv<LR>, smem);
-        ntt_col_inv<LR><<<grid, kColThreads, smem, s>>>(a);
+        set_smem(ntt_col_inv<LR, PS>, smem);
+        ntt_col_inv<LR, PS><<<grid, kColThreads, smem, s>>>(a);
     }
 }
 
-static void col_pass(Ctx &c, bool fwd, uint32_t *data, size_t pstride, size_t total, int m,
-                     int r, const uint32_t *src, size_t src_tstride, size_t src_len,
+// ps: prime set (0 for transforms up to 2^26 points, 1 for 2^27)
+static void col_pass(Ctx &c, int ps, bool fwd, uint32_t *data, size_t pstride, size_t total,
+                     int m, int r, const uint32_t *src, size_t src_tstride, size_t src_len,
                      cudaStream_t s)
 {
     ColArgs a;
@@ -423,18 +439,27 @@ static void col_pass(Ctx &c, bool fwd, uint32_t *data, size_t pstride, size_t to
     double bytes = 24.0 * (double)total;
     if (src) bytes = 12.0 * (double)total + 4.0 * (double)src_len * (double)(total >> m);
     const int tok = prof_begin(c, fwd ? (src ? "ntt_col_fwd_first" : "ntt_col_fwd") : "ntt_col_inv", s);
-    switch (r) {
-    case 1: launch_col<1>(fwd, grid, s, a); break;
-    case 2: launch_col<2>(fwd, grid, s, a); break;
-    case 3: launch_col<3>(fwd, grid, s, a); break;
-    case 4: launch_col<4>(fwd, grid, s, a); break;
-    case 5: launch_col<5>(fwd, grid, s, a); break;
-    case 6: launch_col<6>(fwd, grid, s, a); break;
-    case 7: launch_col<7>(fwd, grid, s, a); break;
-    case 8: launch_col<8>(fwd, grid, s, a); break;
-    case 9: launch_col<9>(fwd, grid, s, a); break;
-    case 10: launch_col<10>(fwd, grid, s, a); break;
-    default: fail(CAT_EINVAL, "column pass size out of range");
+    if (ps == 0) {
+        switch (r) {
+        case 1: launch_col<1, 0>(fwd, grid, s, a); break;
+        case 2: launch_col<2, 0>(fwd, grid, s, a); break;
+        case 3: launch_col<3, 0>(fwd, grid, s, a); break;
+        case 4: launch_col<4, 0>(fwd, grid, s, a); break;
+        case 5: launch_col<5, 0>(fwd, grid, s, a); break;
+        case 6: launch_col<6, 0>(fwd, grid, s, a); break;
+        case 7: launch_col<7, 0>(fwd, grid, s, a); break;
+        case 8: launch_col<8, 0>(fwd, grid, s, a); break;
+        case 9: launch_col<9, 0>(fwd, grid, s, a); break;
+        case 10: launch_col<10, 0>(fwd, grid, s, a); break;
+        default: fail(CAT_EINVAL, "column pass size out of range");
+        }
+    } else {
+        // 2^27-point transforms: plan [8, 7] + 12
+        switch (r) {
+        case 7: launch_col<7, 1>(fwd, grid, s, a); break;
+        case 8: launch_col<8, 1>(fwd, grid, s, a); break;
+        default: fail(CAT_EINVAL, "column pass size out of range");
+        }
     }
     CAT_LAUNCH(fwd ? "ntt_col_fwd" : "ntt_col_inv");
     // algorithmic ops: r/2 butterflies of 12 ops per point and one twiddle
@@ -442,18 +467,37 @@ static void col_pass(Ctx &c, bool fwd, uint32_t *data, size_t pstride, size_t to
     prof_end(c, tok, s, bytes, 3.0 * (double)total * (6.0 * r + 11.0));
 }
 
-template <int LR>
-static void launch_row(dim3 grid, cudaStream_t s, const RowArgs &a)
+template <int LR, int PS>
+static void launch_row_t(dim3 grid, cudaStream_t s, const RowArgs &a)
 {
     if (a.mode == PAIR_SQUARE) {
         const size_t smem = ((size_t)1 << kRowMaxLog) * sizeof(uint32_t);
-        set_smem(ntt_row_mul<LR, true>, smem);
-        ntt_row_mul<LR, true><<<grid, kRowThreads, smem, s>>>(a);
+        set_smem(ntt_row_mul<LR, true, PS>, smem);
+        ntt_row_mul<LR, true, PS><<<grid, kRowThreads, smem, s>>>(a);
     } else {
         const size_t smem = ((size_t)2 << kRowMaxLog) * sizeof(uint32_t);
-        set_smem(ntt_row_mul<LR, false>, smem);
-        ntt_row_mul<LR, false><<<grid, kRowThreads, smem, s>>>(a);
+        set_smem(ntt_row_mul<LR, false, PS>, smem);
+        ntt_row_mul<LR, false, PS><<<grid, kRowThreads, smem, s>>>(a);
     }
+}
+
+// The fused row pass of nprod products of 2^n points with prime set ps.
+static void launch_row(int ps, int lr, size_t nprod, int n, cudaStream_t s, const RowArgs &a)
+{
+    dim3 grid((unsigned)(nprod << (n - kRowMaxLog)), kNumPrimes);
+    if (ps == 0) {
+        switch (lr) {
+        case 9: launch_row_t<9, 0>(grid, s, a); break;
+        case 10: launch_row_t<10, 0>(grid, s, a); break;
+        case 11: launch_row_t<11, 0>(grid, s, a); break;
+        case 12: launch_row_t<12, 0>(grid, s, a); break;
+        default: fail(CAT_EINVAL, "row pass size out of range");
+        }
+    } else {
+        if (lr != 12) fail(CAT_EINVAL, "row pass size out of range");
+        launch_row_t<12, 1>(grid, s, a);
+    }
+    CAT_LAUNCH("ntt_row_mul");
 }
 
 // One operand source of a batched product.
@@ -473,20 +517,21 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
                               cudaStream_t s)
 {
     const NttPlan P = make_plan(n);
+    const int PS = set_for(n);
     const size_t L = (size_t)1 << n;
     const size_t ntf = mode == PAIR_ADJACENT ? 2 * nprod : (mode == PAIR_SQUARE ? nprod : 2);
     const size_t fp = ntf * L;
     DevBuf<uint32_t> F(c, fp * kNumPrimes, s);
     // forward column passes
     if (mode == PAIR_FIRST_TWO) {
-        col_pass(c, true, F.get(), fp, L, n, P.rcol[0], x.p, 0, x.len, s);
-        col_pass(c, true, F.get() + L, fp, L, n, P.rcol[0], y.p, 0, y.len, s);
+        col_pass(c, PS, true, F.get(), fp, L, n, P.rcol[0], x.p, 0, x.len, s);
+        col_pass(c, PS, true, F.get() + L, fp, L, n, P.rcol[0], y.p, 0, y.len, s);
     } else {
-        col_pass(c, true, F.get(), fp, fp, n, P.rcol[0], x.p, x.tstride, x.len, s);
+        col_pass(c, PS, true, F.get(), fp, fp, n, P.rcol[0], x.p, x.tstride, x.len, s);
     }
     int m = n - P.rcol[0];
     for (int i = 1; i < P.ncol; i++) {
-        col_pass(c, true, F.get(), fp, fp, m, P.rcol[i], nullptr, 0, 0, s);
+        col_pass(c, PS, true, F.get(), fp, fp, m, P.rcol[i], nullptr, 0, 0, s);
         m -= P.rcol[i];
     }
     // fused row pass
@@ -500,17 +545,9 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     ra.n = n;
     ra.mode = mode;
     ra.tw = c.twiddles;
-    ra.scale = make_scale(n);
-    dim3 rgrid((unsigned)(nprod << (n - kRowMaxLog)), kNumPrimes);
+    ra.scale = make_scale(PS, n);
     int tok = prof_begin(c, "ntt_row_mul", s);
-    switch (P.rrow) {
-    case 9: launch_row<9>(rgrid, s, ra); break;
-    case 10: launch_row<10>(rgrid, s, ra); break;
-    case 11: launch_row<11>(rgrid, s, ra); break;
-    case 12: launch_row<12>(rgrid, s, ra); break;
-    default: fail(CAT_EINVAL, "row pass size out of range");
-    }
-    CAT_LAUNCH("ntt_row_mul");
+    launch_row(PS, P.rrow, nprod, n, s, ra);
     prof_end(c, tok, s, (mode == PAIR_SQUARE ? 24.0 : 36.0) * (double)gp,
              3.0 * (double)gp * ((mode == PAIR_SQUARE ? 12.0 : 18.0) * P.rrow + 12.0));
     F.reset();
@@ -518,7 +555,7 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     for (int i = P.ncol - 1; i >= 0; i--) {
         int mi = n;
         for (int j = 0; j < i; j++) mi -= P.rcol[j];
-        col_pass(c, false, G.get(), gp, gp, mi, P.rcol[i], nullptr, 0, 0, s);
+        col_pass(c, PS, false, G.get(), gp, gp, mi, P.rcol[i], nullptr, 0, 0, s);
     }
     // remaindering and carries
     const size_t tiles = L / kTile;
@@ -532,7 +569,10 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     ca.out_len = out_len;
     ca.tile_maps = maps.get();
     tok = prof_begin(c, "crt_carry_tiles", s);
-    crt_carry_tiles<<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
+    if (PS == 0)
+        crt_carry_tiles<0><<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
+    else
+        crt_carry_tiles<1><<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
     CAT_LAUNCH("crt_carry_tiles");
     prof_end(c, tok, s, 12.0 * (double)gp + 4.0 * (double)nprod * (double)out_len,
              40.0 * (double)gp);
@@ -571,7 +611,7 @@ static void ntt_mul_small(Ctx &c, int n, size_t nprod, Operand x, Operand y, boo
     a.out_tstride = out_tstride;
     a.out_len = out_len;
     a.tw = c.twiddles;
-    a.scale = make_scale(n);
+    a.scale = make_scale(0, n);
     const unsigned grid = (unsigned)nprod;
     const int tok = prof_begin(c, "ntt_mul_fused", s);
     switch (n) {
@@ -655,7 +695,7 @@ constexpr size_t kNoAllocMapWords = 64;
 constexpr size_t kNoAllocWords = kNoAllocF + kNoAllocG + kNoAllocMapWords + 2;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
-static __device__ __align__(256) uint2 g_noalloc_twiddles[(size_t)kNumPrimes * 2 * kTwPerDir];
+static __device__ __align__(256) uint2 g_noalloc_twiddles[kTwTotal];
 
 // Largest i + 1 with x[i] != 0 into *top (which the caller clears).
 __global__ void noalloc_top(const uint32_t *x, size_t n, unsigned long long *top)
@@ -677,7 +717,7 @@ struct NoAllocDevice {
     uint2 *twiddles = nullptr;    // device address of g_noalloc_twiddles
 };
 static NoAllocDevice g_noalloc_dev[64];
-static uint2 g_noalloc_tw_host[(size_t)kNumPrimes * 2 * kTwPerDir];
+static uint2 g_noalloc_tw_host[kTwTotal];
 
 // Once per device, with that device current: resolve the device addresses of
 // the two arrays and fill the twiddle table (same layout as the context's).
@@ -725,11 +765,11 @@ static void noalloc_mul(const NoAllocDevice &d, const uint32_t *a, size_t na, co
     uint32_t *G = d.scratch + kNoAllocF;
     uint8_t *maps = (uint8_t *)(d.scratch + kNoAllocF + kNoAllocG);
     const size_t fp = 2 * L, gp = L;
-    col_pass(local, true, F, fp, L, n, P.rcol[0], x.p, 0, x.len, s);
-    col_pass(local, true, F + L, fp, L, n, P.rcol[0], y.p, 0, y.len, s);
+    col_pass(local, 0, true, F, fp, L, n, P.rcol[0], x.p, 0, x.len, s);
+    col_pass(local, 0, true, F + L, fp, L, n, P.rcol[0], y.p, 0, y.len, s);
     int m = n - P.rcol[0];
     for (int i = 1; i < P.ncol; i++) {
-        col_pass(local, true, F, fp, fp, m, P.rcol[i], nullptr, 0, 0, s);
+        col_pass(local, 0, true, F, fp, fp, m, P.rcol[i], nullptr, 0, 0, s);
         m -= P.rcol[i];
     }
     RowArgs ra;
@@ -740,20 +780,12 @@ static void noalloc_mul(const NoAllocDevice &d, const uint32_t *a, size_t na, co
     ra.n = n;
     ra.mode = PAIR_FIRST_TWO;
     ra.tw = d.twiddles;
-    ra.scale = make_scale(n);
-    dim3 rgrid((unsigned)(L >> kRowMaxLog), kNumPrimes);
-    switch (P.rrow) {
-    case 9: launch_row<9>(rgrid, s, ra); break;
-    case 10: launch_row<10>(rgrid, s, ra); break;
-    case 11: launch_row<11>(rgrid, s, ra); break;
-    case 12: launch_row<12>(rgrid, s, ra); break;
-    default: fail(CAT_EINVAL, "row pass size out of range");
-    }
-    CAT_LAUNCH("ntt_row_mul");
+    ra.scale = make_scale(0, n);
+    launch_row(0, P.rrow, 1, n, s, ra);
     for (int i = P.ncol - 1; i >= 0; i--) {
         int mi = n;
         for (int j = 0; j < i; j++) mi -= P.rcol[j];
-        col_pass(local, false, G, gp, gp, mi, P.rcol[i], nullptr, 0, 0, s);
+        col_pass(local, 0, false, G, gp, gp, mi, P.rcol[i], nullptr, 0, 0, s);
     }
     const size_t tiles = L / kTile;
     CrtArgs ca;
@@ -764,7 +796,7 @@ static void noalloc_mul(const NoAllocDevice &d, const uint32_t *a, size_t na, co
     ca.out_tstride = 0;
     ca.out_len = len;
     ca.tile_maps = maps;
-    crt_carry_tiles<<<(unsigned)tiles, kTileThreads, 0, s>>>(ca);
+    crt_carry_tiles<0><<<(unsigned)tiles, kTileThreads, 0, s>>>(ca);
     CAT_LAUNCH("crt_carry_tiles");
     carry_tile_scan<<<1, 1024, 0, s>>>(maps, tiles);
     CAT_LAUNCH("carry_tile_scan");
