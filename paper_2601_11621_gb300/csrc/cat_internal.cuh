@@ -1,12 +1,9 @@
 // cat_internal.cuh -- shared internals of libcatalan (context, errors, device
-// memory, 32-bit Montgomery arithmetic for the NTT primes).
+// memory, 32-bit modular arithmetic for the NTT primes).
 //
 // Integer representation: little-endian uint32 limbs.  The NTT works modulo
-// three primes q = k * 2^m + 1 below 2^32 whose multiplicative groups contain
-// 2^27-th roots of unity, so one transform covers up to 2^27 points; the
-// product of the three primes (~2^93.6) exceeds the largest convolution
-// coefficient 2^26 * (2^32 - 1)^2 < 2^90 of two operands whose lengths add up
-// to at most 2^27 limbs, so the Chinese remaindering is exact.
+// three primes q = k * 2^m + 1 (one of three prime sets, by transform size,
+// see below); one transform covers up to 2^27 points.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -36,19 +33,31 @@ void check_cuda(cudaError_t e, const char *what);
 
 constexpr int kNumPrimes = 3;
 constexpr int kLogMaxNtt = 27;  // largest transform: 2^27 points
-// Two sets of three NTT primes.  Set 0: q < 2^31 with 2^26 | q - 1, for
-// transforms up to 2^26 points (product ~2^90.5 > 2^25 (2^32 - 1)^2, the
-// largest coefficient when na + nb <= 2^26); q < 2^31 makes a modular add,
-// subtract or Montgomery correction three integer instructions (a min of
-// two candidates).  Set 1: q < 2^32 with 2^27 | q - 1, for 2^27 points
-// (product ~2^93.6 > 2^26 (2^32 - 1)^2).  Primes ascend within a set.
-constexpr int kNumSets = 2;
-constexpr int kLogMaxSmallSet = 26;
-// Twiddle tables per (prime, direction), w the primitive 2^27-th root of
-// unity (or its inverse), entries (Montgomery form, that times q^-1 mod 2^32):
-//   [0, 2^13)               w^(j 2^14): the roots of order <= 2^13 used by
+// Three sets of three NTT primes q = k 2^m + 1, chosen by the transform size
+// 2^n.  In each set the product of the primes exceeds the largest convolution
+// coefficient 2^(n-1) (2^32 - 1)^2 of two operands whose lengths add up to 2^n
+// limbs, so the Chinese remaindering is exact.
+//   set 0, n <= 23: q < 2^30, 2^23 | q - 1 (product ~2^89.35 > 2^86).  As
+//          4q < 2^32, residues stay unreduced inside a transform: in [0, 2q)
+//          in the forward direction and [0, 4q) in the inverse one (Harvey's
+//          lazy butterflies), one correction per butterfly;
+//   set 1, n <= 26: q < 2^31, 2^26 | q - 1 (product ~2^90.47 > 2^89);
+//          residues in [0, q), every correction a min of two candidates,
+//          which cannot wrap because 2q < 2^32;
+//   set 2, n = 27:  q < 2^32, 2^27 | q - 1 (product ~2^93.6 > 2^90);
+//          residues in [0, q), compare-and-subtract corrections.
+// Sets 0 and 1 multiply by known factors with Shoup's method (the factor w and
+// floor(w 2^32 / q) are stored); set 2 with Montgomery's (2^32 w mod q and
+// that times q^-1 mod 2^32).  Primes ascend within a set.
+constexpr int kNumSets = 3;
+constexpr int kLogSet0 = 23;
+constexpr int kLogSet1 = 26;
+// Twiddle tables per (set, prime, direction), w the set's primitive 2^L-th
+// root of unity (L = set_log_root) or its inverse, entries as pairs in the
+// set's multiplier form:
+//   [0, 2^13)               w^(j 2^(L-13)): the roots of order <= 2^13 used by
 //                           the butterfly stages of a sub-transform;
-//   three tables of 512     w^j, w^(512 j), w^(2^18 j): any w^E, E < 2^27,
+//   three tables of 512     w^j, w^(512 j), w^(2^18 j): any w^E, E < 2^L,
 //                           as a product of three small-table entries.
 constexpr int kTwStage = 1 << 13;
 constexpr int kTwSmall = 512;
@@ -56,15 +65,25 @@ constexpr int kTwPerDir = kTwStage + 3 * kTwSmall;  // uint2 entries per (prime,
 
 __host__ __device__ constexpr uint32_t ntt_prime(int set, int i)
 {
-    return set == 0 ? (i == 0 ? 469762049u : (i == 1 ? 1811939329u : 2013265921u))
-                    : (i == 0 ? 2013265921u : (i == 1 ? 2281701377u : 3221225473u));
+    return set == 0   ? (i == 0 ? 880803841u : (i == 1 ? 897581057u : 998244353u))
+           : set == 1 ? (i == 0 ? 469762049u : (i == 1 ? 1811939329u : 2013265921u))
+                      : (i == 0 ? 2013265921u : (i == 1 ? 2281701377u : 3221225473u));
 }
 
 // log2 of the order of the root of unity the twiddle tables of a set use
-__host__ __device__ constexpr int set_log_root(int set) { return set == 0 ? kLogMaxSmallSet : kLogMaxNtt; }
+__host__ __device__ constexpr int set_log_root(int set)
+{
+    return set == 0 ? kLogSet0 : (set == 1 ? kLogSet1 : kLogMaxNtt);
+}
 
 // the prime set a transform of 2^n points uses
-__host__ __device__ constexpr int set_for(int n) { return n <= kLogMaxSmallSet ? 0 : 1; }
+__host__ __device__ constexpr int set_for(int n)
+{
+    return n <= kLogSet0 ? 0 : (n <= kLogSet1 ? 1 : 2);
+}
+
+// whether a set stores its multipliers in Shoup's form
+__host__ __device__ constexpr bool set_shoup(int set) { return set < 2; }
 
 // q^-1 mod 2^32 by Newton's iteration x <- x (2 - q x)
 __host__ __device__ constexpr uint32_t inv32(uint32_t q)
@@ -95,6 +114,12 @@ __host__ __device__ constexpr uint32_t powmod_u32(uint64_t a, uint64_t e, uint32
 __host__ __device__ constexpr uint32_t to_mont_c(uint64_t x, uint32_t q)
 {
     return (uint32_t)(((x % q) << 32) % q);
+}
+
+// floor(w 2^32 / q): Shoup's companion of a multiplier w < q
+__host__ __device__ constexpr uint32_t shoup_c(uint32_t w, uint32_t q)
+{
+    return (uint32_t)(((uint64_t)w << 32) / q);
 }
 
 // ------------------------------------------------ device modular arithmetic
@@ -145,38 +170,33 @@ __device__ __forceinline__ uint32_t reduce32(uint32_t x, uint32_t q)
     return x;
 }
 
-// The same operations for a prime set: S (q < 2^31) takes the min-of-two
-// forms, whose candidates never wrap because 2q < 2^32.
+// Shoup's product: a w - floor(a wp / 2^32) q with wp = floor(w 2^32 / q)
+// equals a w mod q or that plus q, for any a < 2^32 and w < q < 2^31
+// (the quotient estimate is short by at most one), so it lies in [0, 2q) and
+// the 32-bit wrap-around arithmetic is exact.
+__device__ __forceinline__ uint32_t shoup(uint32_t a, uint32_t w, uint32_t wp, uint32_t q)
+{
+    return a * w - __umulhi(a, wp) * q;
+}
+
+// x - m when x >= m, for x < 2m <= 2^32: when x < m the difference wraps to
+// at least 2^32 - m > x, so the smaller candidate is always the answer.
+__device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m) { return min(x, x - m); }
+
+// Modular add, subtract and Montgomery products for q < 2^31 (S) in the
+// min-of-two form, or for any q < 2^32.  Inputs below q, results below q.
 template <bool S>
 __device__ __forceinline__ uint32_t add_m(uint32_t a, uint32_t b, uint32_t q)
 {
-    if (S) {
-        const uint32_t s = a + b;
-        return min(s, s - q);
-    }
+    if (S) return csub(a + b, q);
     return add_mod(a, b, q);
 }
 
 template <bool S>
 __device__ __forceinline__ uint32_t sub_m(uint32_t a, uint32_t b, uint32_t q)
 {
-    if (S) {
-        const uint32_t d = a - b + q;
-        return min(d, d - q);
-    }
+    if (S) return csub(a - b + q, q);
     return sub_mod(a, b, q);
-}
-
-template <bool S>
-__device__ __forceinline__ uint32_t mont_pre(uint32_t a, uint32_t w, uint32_t wp, uint32_t q)
-{
-    if (S) {
-        const uint32_t hi = __umulhi(a, w);
-        const uint32_t m = a * wp;
-        const uint32_t t = hi - __umulhi(m, q) + q;
-        return min(t, t - q);
-    }
-    return mont_mul_pre(a, w, wp, q);
 }
 
 template <bool S>
@@ -185,19 +205,136 @@ __device__ __forceinline__ uint32_t mont(uint32_t a, uint32_t b, uint32_t q, uin
     if (S) {
         const uint32_t hi = __umulhi(a, b);
         const uint32_t m = (a * b) * qinv;
-        const uint32_t t = hi - __umulhi(m, q) + q;
-        return min(t, t - q);
+        return csub(hi - __umulhi(m, q) + q, q);
     }
     return mont_mul(a, b, q, qinv);
 }
 
-// x mod q for any 32-bit x: for S one Montgomery product with 2^32 mod q
-// (x 2^32 2^-32), otherwise at most two subtractions (q > 2^30).
-template <bool S>
-__device__ __forceinline__ uint32_t reduce_m(uint32_t x, uint32_t q, uint32_t qinv, uint32_t r1)
+// ------------------------------------------- the transform data per set
+//
+// Forward-transform residues lie in [0, 2q) for set 0 and in [0, q)
+// otherwise; inverse-transform residues in [0, 4q) for set 0 and [0, q)
+// otherwise.  A multiplier is a uint2 in the set's form.
+
+// a w for any 32-bit a, into the forward range
+template <int PS>
+__device__ __forceinline__ uint32_t mul_w(uint32_t a, uint2 w, uint32_t q)
 {
-    if (S) return mont<true>(x, r1, q, qinv);
-    return reduce32(x, q);
+    if constexpr (PS == 0) return shoup(a, w.x, w.y, q);
+    else if constexpr (PS == 1) return csub(shoup(a, w.x, w.y, q), q);
+    else return mont_mul_pre(a, w.x, w.y, q);
+}
+
+// a w1 w2 w3 for any 32-bit a, into the forward range (set 1 corrects once:
+// Shoup's product accepts an unreduced input)
+template <int PS>
+__device__ __forceinline__ uint32_t mul_w3(uint32_t a, uint2 w1, uint2 w2, uint2 w3, uint32_t q)
+{
+    if constexpr (PS == 2)
+        return mont_mul_pre(mont_mul_pre(mont_mul_pre(a, w1.x, w1.y, q), w2.x, w2.y, q), w3.x,
+                            w3.y, q);
+    const uint32_t t = shoup(shoup(shoup(a, w1.x, w1.y, q), w2.x, w2.y, q), w3.x, w3.y, q);
+    return PS == 0 ? t : csub(t, q);
+}
+
+// Forward (decimation-in-frequency) butterfly (x, y) <- (x + y, (x - y) w)
+// on forward-range residues.
+template <int PS>
+__device__ __forceinline__ void bf_dif(uint32_t &x, uint32_t &y, uint2 w, uint32_t q)
+{
+    const uint32_t a = x, b = y;
+    if constexpr (PS == 0) {
+        x = csub(a + b, 2 * q);                 // [0, 4q) -> [0, 2q)
+        y = shoup(a - b + 2 * q, w.x, w.y, q);  // (0, 4q) times w -> [0, 2q)
+    } else if constexpr (PS == 1) {
+        x = csub(a + b, q);
+        y = csub(shoup(a - b + q, w.x, w.y, q), q);
+    } else {
+        x = add_mod(a, b, q);
+        y = mont_mul_pre(sub_mod(a, b, q), w.x, w.y, q);
+    }
+}
+
+// the same with w = 1
+template <int PS>
+__device__ __forceinline__ void bf_dif1(uint32_t &x, uint32_t &y, uint32_t q)
+{
+    const uint32_t a = x, b = y;
+    if constexpr (PS == 0) {
+        x = csub(a + b, 2 * q);
+        y = csub(a - b + 2 * q, 2 * q);
+    } else {
+        x = add_m<PS == 1>(a, b, q);
+        y = sub_m<PS == 1>(a, b, q);
+    }
+}
+
+// Inverse (decimation-in-time) butterfly (x, y) <- (x + y w, x - y w) on
+// inverse-range residues.
+template <int PS>
+__device__ __forceinline__ void bf_dit(uint32_t &x, uint32_t &y, uint2 w, uint32_t q)
+{
+    if constexpr (PS == 0) {
+        const uint32_t a = csub(x, 2 * q);          // [0, 2q)
+        const uint32_t t = shoup(y, w.x, w.y, q);   // [0, 2q)
+        x = a + t;                                  // [0, 4q)
+        y = a - t + 2 * q;                          // (0, 4q)
+    } else {
+        const uint32_t a = x, t = mul_w<PS>(y, w, q);
+        x = add_m<PS == 1>(a, t, q);
+        y = sub_m<PS == 1>(a, t, q);
+    }
+}
+
+template <int PS>
+__device__ __forceinline__ void bf_dit1(uint32_t &x, uint32_t &y, uint32_t q)
+{
+    if constexpr (PS == 0) {
+        const uint32_t a = csub(x, 2 * q), t = csub(y, 2 * q);
+        x = a + t;
+        y = a - t + 2 * q;
+    } else {
+        const uint32_t a = x, b = y;
+        x = add_m<PS == 1>(a, b, q);
+        y = sub_m<PS == 1>(a, b, q);
+    }
+}
+
+// A raw 32-bit limb into the forward range: Shoup's product with 1
+// (wp1 = floor(2^32 / q)) for sets 0 and 1, two subtractions for set 2.
+template <int PS>
+__device__ __forceinline__ uint32_t reduce_in(uint32_t x, uint32_t q, uint32_t wp1)
+{
+    if constexpr (PS == 0) return shoup(x, 1u, wp1, q);
+    else if constexpr (PS == 1) return csub(shoup(x, 1u, wp1, q), q);
+    else return reduce32(x, q);
+}
+
+// Pointwise product of two forward-range residues times the scale factor:
+// x y 2^-32 by Montgomery's reduction, then times sc = 2^32 2^-n (Shoup) for
+// sets 0 and 1 or sc = 2^64 2^-n (Montgomery) for set 2, giving x y 2^-n.
+// For set 0, x y < 4 q^2 < 2^32 q keeps hi(x y) - hi(m q) in (-q, q).
+template <int PS>
+__device__ __forceinline__ uint32_t pmul(uint32_t x, uint32_t y, uint2 sc, uint32_t q,
+                                         uint32_t qinv)
+{
+    if constexpr (PS == 0) {
+        const uint32_t hi = __umulhi(x, y);
+        const uint32_t m = (x * y) * qinv;
+        return shoup(hi - __umulhi(m, q) + q, sc.x, sc.y, q);
+    } else if constexpr (PS == 1) {
+        return csub(shoup(mont<true>(x, y, q, qinv), sc.x, sc.y, q), q);
+    } else {
+        return mont_mul(mont_mul(x, y, q, qinv), sc.x, q, qinv);
+    }
+}
+
+// An inverse-range residue reduced into [0, q).
+template <int PS>
+__device__ __forceinline__ uint32_t final_red(uint32_t r, uint32_t q)
+{
+    if constexpr (PS == 0) return csub(csub(r, 2 * q), q);
+    return r;
 }
 
 __device__ __forceinline__ uint32_t bitrev(uint32_t x, int bits)
@@ -231,7 +368,7 @@ struct Ctx {
     size_t in_use = 0;
     size_t peak = 0;
     std::string last_error;
-    uint2 *twiddles = nullptr;  // [prime][dir][kTwPerDir] (Montgomery w, w q^-1)
+    uint2 *twiddles = nullptr;  // [set][prime][dir][kTwPerDir] multiplier pairs
     int num_sms = 0;
     size_t comba_max_slot = 128;  // tree levels with slots up to this use schoolbook
     bool profiling = false;
@@ -247,7 +384,7 @@ int prof_begin(Ctx &c, const char *name, cudaStream_t s);
 void prof_end(Ctx &c, int token, cudaStream_t s, double bytes, double ops = 0);
 void prof_resolve(Ctx &c);
 
-// Fills h[kTwTotal] with the twiddle tables of both sets (host side).
+// Fills h[kTwTotal] with the twiddle tables of all sets (host side).
 constexpr size_t kTwTotal = (size_t)kNumSets * kNumPrimes * 2 * kTwPerDir;
 void twiddle_tables_host(uint2 *h);
 

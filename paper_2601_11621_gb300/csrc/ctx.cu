@@ -156,15 +156,20 @@ static uint32_t find_generator(uint32_t q)
     }
 }
 
-// Powers 1, s, s^2, ... (count of them) of `step` into T, as (Montgomery
-// form, that times q^-1 mod 2^32).
-static void fill_powers(uint2 *T, int count, uint32_t step, uint32_t q)
+// Powers 1, s, s^2, ... (count of them) of `step` into T as multiplier pairs:
+// (x, floor(x 2^32 / q)) in Shoup's form, else (x 2^32 mod q, that times
+// q^-1 mod 2^32) in Montgomery's.
+static void fill_powers(uint2 *T, int count, uint32_t step, uint32_t q, bool shoup)
 {
     const uint32_t qi = inv32(q);
     uint64_t x = 1;
     for (int j = 0; j < count; j++) {
-        const uint32_t m = to_mont_c(x, q);
-        T[j] = make_uint2(m, m * qi);
+        if (shoup) {
+            T[j] = make_uint2((uint32_t)x, shoup_c((uint32_t)x, q));
+        } else {
+            const uint32_t m = to_mont_c(x, q);
+            T[j] = make_uint2(m, m * qi);
+        }
         x = x * step % q;
     }
 }
@@ -177,6 +182,7 @@ void twiddle_tables_host(uint2 *h)
     for (int set = 0; set < kNumSets; set++)
     for (int i = 0; i < kNumPrimes; i++) {
         const int L = set_log_root(set);
+        const bool sh = set_shoup(set);
         const uint32_t q = ntt_prime(set, i);
         if ((q - 1) % (1u << L)) fail(CAT_ECUDA, "prime without the needed roots of unity");
         const uint32_t w = powmod_u32(find_generator(q), (q - 1) >> L, q);
@@ -185,10 +191,11 @@ void twiddle_tables_host(uint2 *h)
         for (int d = 0; d < 2; d++) {
             const uint32_t root = d == 0 ? w : powmod_u32(w, (1u << L) - 1, q);
             uint2 *T = h + (((size_t)set * kNumPrimes + i) * 2 + d) * kTwPerDir;
-            fill_powers(T, kTwStage, powmod_u32(root, 1u << (L - 13), q), q);
-            fill_powers(T + kTwStage, kTwSmall, root, q);
-            fill_powers(T + kTwStage + kTwSmall, kTwSmall, powmod_u32(root, 1u << 9, q), q);
-            fill_powers(T + kTwStage + 2 * kTwSmall, kTwSmall, powmod_u32(root, 1u << 18, q), q);
+            fill_powers(T, kTwStage, powmod_u32(root, 1u << (L - 13), q), q, sh);
+            fill_powers(T + kTwStage, kTwSmall, root, q, sh);
+            fill_powers(T + kTwStage + kTwSmall, kTwSmall, powmod_u32(root, 1u << 9, q), q, sh);
+            fill_powers(T + kTwStage + 2 * kTwSmall, kTwSmall, powmod_u32(root, 1u << 18, q), q,
+                        sh);
         }
     }
 }

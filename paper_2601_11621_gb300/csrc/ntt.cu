@@ -31,16 +31,19 @@ namespace cat {
 
 // --------------------------------------------------------------- constants
 
-__constant__ uint32_t c_q[kNumSets][kNumPrimes] = {
-    {ntt_prime(0, 0), ntt_prime(0, 1), ntt_prime(0, 2)},
-    {ntt_prime(1, 0), ntt_prime(1, 1), ntt_prime(1, 2)}};
-__constant__ uint32_t c_qinv[kNumSets][kNumPrimes] = {
-    {inv32(ntt_prime(0, 0)), inv32(ntt_prime(0, 1)), inv32(ntt_prime(0, 2))},
-    {inv32(ntt_prime(1, 0)), inv32(ntt_prime(1, 1)), inv32(ntt_prime(1, 2))}};
-// 2^32 mod q (Montgomery form of 1), used to reduce raw limbs for set 0
-__constant__ uint32_t c_r1[kNumSets][kNumPrimes] = {
-    {to_mont_c(1, ntt_prime(0, 0)), to_mont_c(1, ntt_prime(0, 1)), to_mont_c(1, ntt_prime(0, 2))},
-    {to_mont_c(1, ntt_prime(1, 0)), to_mont_c(1, ntt_prime(1, 1)), to_mont_c(1, ntt_prime(1, 2))}};
+#define CAT_SET_CONST(f)                                                              \
+    {{f(ntt_prime(0, 0)), f(ntt_prime(0, 1)), f(ntt_prime(0, 2))},                    \
+     {f(ntt_prime(1, 0)), f(ntt_prime(1, 1)), f(ntt_prime(1, 2))},                    \
+     {f(ntt_prime(2, 0)), f(ntt_prime(2, 1)), f(ntt_prime(2, 2))}}
+#define CAT_Q(q) (q)
+#define CAT_WP1(q) shoup_c(1u, q)
+__constant__ uint32_t c_q[kNumSets][kNumPrimes] = CAT_SET_CONST(CAT_Q);
+__constant__ uint32_t c_qinv[kNumSets][kNumPrimes] = CAT_SET_CONST(inv32);
+// floor(2^32 / q): Shoup's companion of 1, which reduces raw limbs
+__constant__ uint32_t c_wp1[kNumSets][kNumPrimes] = CAT_SET_CONST(CAT_WP1);
+#undef CAT_SET_CONST
+#undef CAT_Q
+#undef CAT_WP1
 
 // Garner constants of a set, in Montgomery form.
 template <int PS>
@@ -54,20 +57,21 @@ struct Garner {
     static_assert(q0 < q1 && q1 < q2, "Garner order assumes q0 < q1 < q2");
 };
 
-// Pointwise scale: Montgomery constant R^2 * 2^-n mod q, so that
-// mont(mont(x, y), scale) = x * y * 2^-n.
+// Pointwise scale 2^-n folded into the product's second factor: 2^32 2^-n mod
+// q in Shoup's form for sets 0 and 1, 2^64 2^-n mod q (Montgomery) for set 2,
+// so that pmul(x, y) = x y 2^-n.
 struct Scale {
-    uint32_t c[kNumPrimes];
+    uint2 c[kNumPrimes];
 };
 
 static Scale make_scale(int set, int n)
 {
     Scale s;
     for (int i = 0; i < kNumPrimes; i++) {
-        uint32_t q = ntt_prime(set, i);
-        uint32_t inv2n = powmod_u32((q + 1) / 2, (uint64_t)n, q);   // 2^-n
-        uint32_t r = to_mont_c(inv2n, q);                            // R 2^-n
-        s.c[i] = to_mont_c(r, q);                                    // R^2 2^-n
+        const uint32_t q = ntt_prime(set, i);
+        const uint32_t inv2n = powmod_u32((q + 1) / 2, (uint64_t)n, q);  // 2^-n
+        const uint32_t r = to_mont_c(inv2n, q);                           // 2^32 2^-n
+        s.c[i] = set_shoup(set) ? make_uint2(r, shoup_c(r, q)) : make_uint2(to_mont_c(r, q), 0u);
     }
     return s;
 }
@@ -82,26 +86,29 @@ __device__ __forceinline__ const uint2 *tw_table(const uint2 *tw, int set, int p
 // x * w^E for E below the set's root order, w the set's root of unity:
 // three products with entries of the three 512-entry tables (which stay in
 // L1), w^E = w^(E mod 512) * w^(512 ((E >> 9) mod 512)) * w^(2^18 (E >> 18)).
-template <bool S>
+// Any 32-bit x; the result is in the set's forward range.
+template <int PS>
 __device__ __forceinline__ uint32_t tw_apply(uint32_t x, const uint2 *T, uint32_t E, uint32_t q)
 {
     const uint2 a = __ldg(&T[kTwStage + (E & (kTwSmall - 1))]);
     const uint2 b = __ldg(&T[kTwStage + kTwSmall + ((E >> 9) & (kTwSmall - 1))]);
     const uint2 c = __ldg(&T[kTwStage + 2 * kTwSmall + (E >> 18)]);
-    x = mont_pre<S>(x, a.x, a.y, q);
-    x = mont_pre<S>(x, b.x, b.y, q);
-    return mont_pre<S>(x, c.x, c.y, q);
+    return mul_w3<PS>(x, a, b, c, q);
 }
 
 // ----------------------------------------------- remaindering and carries
 
-// Garner: the coefficient c < q0 q1 q2 with c = r_i mod q_i, as three words.
+// Garner: the coefficient c < q0 q1 q2 with c = r_i mod q_i, as three words,
+// from inverse-transform residues (reduced into [0, q_i) first).
 template <int PS>
 __device__ __forceinline__ void crt3(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t &c0,
                                      uint32_t &c1, uint32_t &c2)
 {
     using G = Garner<PS>;
-    constexpr bool S = PS == 0;
+    constexpr bool S = G::q2 < (1u << 31);
+    r0 = final_red<PS>(r0, G::q0);
+    r1 = final_red<PS>(r1, G::q1);
+    r2 = final_red<PS>(r2, G::q2);
     const uint32_t x0 = r0;  // < q0 < q1 < q2
     const uint32_t x1 = mont<S>(sub_m<S>(r1, x0, G::q1), G::inv_q0_mod_q1, G::q1, G::qinv1);
     uint32_t t = sub_m<S>(r2, x0, G::q2);
@@ -339,22 +346,21 @@ __global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
     __syncthreads();
 #pragma unroll 1
     for (int p = 0; p < kNumPrimes; p++) {
-        const uint32_t q = c_q[0][p], qinv = c_qinv[0][p], r1 = c_r1[0][p];
+        const uint32_t q = c_q[0][p], qinv = c_qinv[0][p], wp1 = c_wp1[0][p];
         const uint2 *T = tw_table(a.tw, 0, p, 0);
         const uint2 *Ti = tw_table(a.tw, 0, p, 1);
-        const uint32_t sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
+        const uint2 sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
         for (int i = threadIdx.x; i < L; i += blockDim.x) {
-            X[swz(i)] = reduce_m<true>(rawA[i], q, qinv, r1);
-            Y[swz(i)] = reduce_m<true>(gb ? rawB[i] : rawA[i], q, qinv, r1);
+            X[swz(i)] = reduce_in<0>(rawA[i], q, wp1);
+            Y[swz(i)] = reduce_in<0>(gb ? rawB[i] : rawA[i], q, wp1);
         }
         __syncthreads();
-        dif_smem<LR, 2>(X, T, q);
+        dif_smem<LR, 2, 0>(X, T, q);
         uint32_t *Z = Rr[p];
         // elementwise in the swizzled space: Z, X, Y share the permutation
-        for (int i = threadIdx.x; i < L; i += blockDim.x)
-            Z[i] = mont<true>(mont<true>(X[i], Y[i], q, qinv), sc, q, qinv);
+        for (int i = threadIdx.x; i < L; i += blockDim.x) Z[i] = pmul<0>(X[i], Y[i], sc, q, qinv);
         __syncthreads();
-        dit_smem<LR, 1>(Z, Ti, q);
+        dit_smem<LR, 1, 0>(Z, Ti, q);
     }
     uint32_t *cw0 = sm + 3 * L, *cw1 = cw0 + (L + 2), *cw2 = cw1 + (L + 2);
     for (int i = threadIdx.x; i < L + 2; i += blockDim.x) {
@@ -419,7 +425,7 @@ static void launch_col(bool fwd, dim3 grid, cudaStream_t s, const ColArgs &a)
     }
 }
 
-// ps: prime set (0 for transforms up to 2^26 points, 1 for 2^27)
+// ps: the prime set of the transform (set_for)
 static void col_pass(Ctx &c, int ps, bool fwd, uint32_t *data, size_t pstride, size_t total,
                      int m, int r, const uint32_t *src, size_t src_tstride, size_t src_len,
                      cudaStream_t s)
@@ -453,11 +459,18 @@ static void col_pass(Ctx &c, int ps, bool fwd, uint32_t *data, size_t pstride, s
         case 10: launch_col<10, 0>(fwd, grid, s, a); break;
         default: fail(CAT_EINVAL, "column pass size out of range");
         }
-    } else {
-        // 2^27-point transforms: plan [8, 7] + 12
+    } else if (ps == 1) {
+        // 2^24 .. 2^26 points: plans [6, 6], [7, 6], [7, 7] + 12
         switch (r) {
+        case 6: launch_col<6, 1>(fwd, grid, s, a); break;
         case 7: launch_col<7, 1>(fwd, grid, s, a); break;
-        case 8: launch_col<8, 1>(fwd, grid, s, a); break;
+        default: fail(CAT_EINVAL, "column pass size out of range");
+        }
+    } else {
+        // 2^27 points: plan [8, 7] + 12
+        switch (r) {
+        case 7: launch_col<7, 2>(fwd, grid, s, a); break;
+        case 8: launch_col<8, 2>(fwd, grid, s, a); break;
         default: fail(CAT_EINVAL, "column pass size out of range");
         }
     }
@@ -495,7 +508,10 @@ static void launch_row(int ps, int lr, size_t nprod, int n, cudaStream_t s, cons
         }
     } else {
         if (lr != 12) fail(CAT_EINVAL, "row pass size out of range");
-        launch_row_t<12, 1>(grid, s, a);
+        if (ps == 1)
+            launch_row_t<12, 1>(grid, s, a);
+        else
+            launch_row_t<12, 2>(grid, s, a);
     }
     CAT_LAUNCH("ntt_row_mul");
 }
@@ -571,8 +587,10 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     tok = prof_begin(c, "crt_carry_tiles", s);
     if (PS == 0)
         crt_carry_tiles<0><<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
-    else
+    else if (PS == 1)
         crt_carry_tiles<1><<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
+    else
+        crt_carry_tiles<2><<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
     CAT_LAUNCH("crt_carry_tiles");
     prof_end(c, tok, s, 12.0 * (double)gp + 4.0 * (double)nprod * (double)out_len,
              40.0 * (double)gp);

@@ -47,35 +47,9 @@ __host__ __device__ constexpr int dit_base(int lr, int rd)
 // which makes every round's access pattern free of bank conflicts.
 __device__ __forceinline__ int swz(int a) { return a ^ ((a >> 5) & 31); }
 
-template <bool S>
-__device__ __forceinline__ void bf_dif(uint32_t &x, uint32_t &y, uint2 w, uint32_t q)
-{
-    const uint32_t a = x, b = y;
-    x = add_m<S>(a, b, q);
-    y = mont_pre<S>(sub_m<S>(a, b, q), w.x, w.y, q);
-}
-
-template <bool S>
-__device__ __forceinline__ void bf_dit(uint32_t &x, uint32_t &y, uint2 w, uint32_t q)
-{
-    const uint32_t t = mont_pre<S>(y, w.x, w.y, q);
-    const uint32_t a = x;
-    x = add_m<S>(a, t, q);
-    y = sub_m<S>(a, t, q);
-}
-
-// butterfly with twiddle 1 (same in both directions)
-template <bool S>
-__device__ __forceinline__ void bf_unit(uint32_t &x, uint32_t &y, uint32_t q)
-{
-    const uint32_t a = x, b = y;
-    x = add_m<S>(a, b, q);
-    y = sub_m<S>(a, b, q);
-}
-
 // In a round with B = 0 the twiddle index is a compile-time constant, and the
 // butterflies with (k mod 2^st) = 0 have twiddle w^0 = 1: no multiply.
-template <int E, int B, int NA, bool S>
+template <int E, int B, int NA, int PS>
 __device__ __forceinline__ void dif_stages(uint32_t (&x)[NA][1 << E], int glow, const uint2 *T,
                                            uint32_t q)
 {
@@ -86,18 +60,18 @@ __device__ __forceinline__ void dif_stages(uint32_t (&x)[NA][1 << E], int glow, 
             if (k & (1 << st)) continue;
             if (B == 0 && (k & ((1 << st) - 1)) == 0) {
 #pragma unroll
-                for (int a = 0; a < NA; a++) bf_unit<S>(x[a][k], x[a][k + (1 << st)], q);
+                for (int a = 0; a < NA; a++) bf_dif1<PS>(x[a][k], x[a][k + (1 << st)], q);
                 continue;
             }
             const int p = glow + ((k & ((1 << st) - 1)) << B);
             const uint2 w = __ldg(&T[p << (12 - B - st)]);
 #pragma unroll
-            for (int a = 0; a < NA; a++) bf_dif<S>(x[a][k], x[a][k + (1 << st)], w, q);
+            for (int a = 0; a < NA; a++) bf_dif<PS>(x[a][k], x[a][k + (1 << st)], w, q);
         }
     }
 }
 
-template <int E, int B, int NA, bool S>
+template <int E, int B, int NA, int PS>
 __device__ __forceinline__ void dit_stages(uint32_t (&x)[NA][1 << E], int glow, const uint2 *Ti,
                                            uint32_t q)
 {
@@ -108,13 +82,13 @@ __device__ __forceinline__ void dit_stages(uint32_t (&x)[NA][1 << E], int glow, 
             if (k & (1 << st)) continue;
             if (B == 0 && (k & ((1 << st) - 1)) == 0) {
 #pragma unroll
-                for (int a = 0; a < NA; a++) bf_unit<S>(x[a][k], x[a][k + (1 << st)], q);
+                for (int a = 0; a < NA; a++) bf_dit1<PS>(x[a][k], x[a][k + (1 << st)], q);
                 continue;
             }
             const int p = glow + ((k & ((1 << st) - 1)) << B);
             const uint2 w = __ldg(&Ti[p << (12 - B - st)]);
 #pragma unroll
-            for (int a = 0; a < NA; a++) bf_dit<S>(x[a][k], x[a][k + (1 << st)], w, q);
+            for (int a = 0; a < NA; a++) bf_dit<PS>(x[a][k], x[a][k + (1 << st)], w, q);
         }
     }
 }
@@ -124,7 +98,7 @@ __device__ __forceinline__ void dit_stages(uint32_t (&x)[NA][1 << E], int glow, 
 // `out`.  COLFAST: consecutive threads take consecutive columns (strided
 // columns in global memory); otherwise consecutive threads take consecutive
 // groups of one column (contiguous rows in global memory).  No barrier.
-template <int LR, int C, int B, int E, bool FWD, int NA, bool COLFAST, bool S, class IN, class OUT>
+template <int LR, int C, int B, int E, bool FWD, int NA, bool COLFAST, int PS, class IN, class OUT>
 __device__ __forceinline__ void round_io(const IN &in, const OUT &out, const uint2 *T, uint32_t q)
 {
     constexpr int NGC = (1 << LR) >> E;  // groups per column
@@ -137,9 +111,9 @@ __device__ __forceinline__ void round_io(const IN &in, const OUT &out, const uin
         uint32_t x[NA][1 << E];
         in.template load<E, B, NA>(x, base, c);
         if (FWD)
-            dif_stages<E, B, NA, S>(x, glow, T, q);
+            dif_stages<E, B, NA, PS>(x, glow, T, q);
         else
-            dit_stages<E, B, NA, S>(x, glow, T, q);
+            dit_stages<E, B, NA, PS>(x, glow, T, q);
         out.template store<E, B, NA>(x, base, c);
     }
 }
@@ -174,38 +148,38 @@ struct SmemIO {
     }
 };
 
-// All-shared-memory transforms (used by the one-block multiply, which always
-// uses prime set 0).  Caller synchronises before; these return synchronised.
-template <int LR, int NA>
+// All-shared-memory transforms (used by the one-block multiply).  Caller
+// synchronises before; these return synchronised.
+template <int LR, int NA, int PS>
 __device__ __forceinline__ void dif_smem(uint32_t *s, const uint2 *T, uint32_t q)
 {
     constexpr int NR = rounds_of(LR);
     SmemIO<LR, 1, true> S{s};
-    round_io<LR, 1, dif_base(LR, 0), round_size(LR, 0), true, NA, true, true>(S, S, T, q);
+    round_io<LR, 1, dif_base(LR, 0), round_size(LR, 0), true, NA, true, PS>(S, S, T, q);
     __syncthreads();
     if constexpr (NR >= 2) {
-        round_io<LR, 1, dif_base(LR, 1), round_size(LR, 1), true, NA, true, true>(S, S, T, q);
+        round_io<LR, 1, dif_base(LR, 1), round_size(LR, 1), true, NA, true, PS>(S, S, T, q);
         __syncthreads();
     }
     if constexpr (NR >= 3) {
-        round_io<LR, 1, dif_base(LR, 2), round_size(LR, 2), true, NA, true, true>(S, S, T, q);
+        round_io<LR, 1, dif_base(LR, 2), round_size(LR, 2), true, NA, true, PS>(S, S, T, q);
         __syncthreads();
     }
 }
 
-template <int LR, int NA>
+template <int LR, int NA, int PS>
 __device__ __forceinline__ void dit_smem(uint32_t *s, const uint2 *Ti, uint32_t q)
 {
     constexpr int NR = rounds_of(LR);
     SmemIO<LR, 1, true> S{s};
-    round_io<LR, 1, dit_base(LR, 0), dit_size(LR, 0), false, NA, true, true>(S, S, Ti, q);
+    round_io<LR, 1, dit_base(LR, 0), dit_size(LR, 0), false, NA, true, PS>(S, S, Ti, q);
     __syncthreads();
     if constexpr (NR >= 2) {
-        round_io<LR, 1, dit_base(LR, 1), dit_size(LR, 1), false, NA, true, true>(S, S, Ti, q);
+        round_io<LR, 1, dit_base(LR, 1), dit_size(LR, 1), false, NA, true, PS>(S, S, Ti, q);
         __syncthreads();
     }
     if constexpr (NR >= 3) {
-        round_io<LR, 1, dit_base(LR, 2), dit_size(LR, 2), false, NA, true, true>(S, S, Ti, q);
+        round_io<LR, 1, dit_base(LR, 2), dit_size(LR, 2), false, NA, true, PS>(S, S, Ti, q);
         __syncthreads();
     }
 }
@@ -232,12 +206,12 @@ struct ColArgs {
 
 // Column tile in global memory: element (row, c) at p[row * S + col0 + c].
 // With `src`, elements come from limbs instead (zero past src_len, reduced).
-template <bool SQ>
+template <int PS>
 struct ColIn {
     const uint32_t *p;
     const uint32_t *src;
     size_t S, col0, src_len;
-    uint32_t q, qinv, r1;
+    uint32_t q, wp1;
     template <int E, int B, int NA>
     __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
@@ -245,7 +219,7 @@ struct ColIn {
         for (int k = 0; k < (1 << E); k++) {
             const size_t idx = (size_t)(base + (k << B)) * S + col0 + c;
             if (src)
-                x[0][k] = idx < src_len ? reduce_m<SQ>(src[idx], q, qinv, r1) : 0u;
+                x[0][k] = idx < src_len ? reduce_in<PS>(src[idx], q, wp1) : 0u;
             else
                 x[0][k] = p[idx];
         }
@@ -253,7 +227,7 @@ struct ColIn {
 };
 
 // Forward pass output: element (row, col) times w_M^(col * bitrev(row)).
-template <int LR, bool SQ>
+template <int LR, int PS>
 struct ColOutTw {
     uint32_t *p;
     size_t S, col0;
@@ -269,14 +243,14 @@ struct ColOutTw {
             const int row = base + (k << B);
             const uint32_t e = (gcol * bitrev((uint32_t)row, LR)) << shift;
             uint32_t v = x[0][k];
-            if (e) v = tw_apply<SQ>(v, T, e, q);
+            if (e) v = tw_apply<PS>(v, T, e, q);
             p[(size_t)row * S + gcol] = v;
         }
     }
 };
 
 // Inverse pass input: element (row, col) times w_M^-(col * bitrev(row)).
-template <int LR, bool SQ>
+template <int LR, int PS>
 struct ColInTw {
     const uint32_t *p;
     size_t S, col0;
@@ -292,7 +266,7 @@ struct ColInTw {
             const int row = base + (k << B);
             uint32_t v = p[(size_t)row * S + gcol];
             const uint32_t e = (gcol * bitrev((uint32_t)row, LR)) << shift;
-            if (e) v = tw_apply<SQ>(v, Ti, e, q);
+            if (e) v = tw_apply<PS>(v, Ti, e, q);
             x[0][k] = v;
         }
     }
@@ -315,7 +289,6 @@ template <int LR, int PS>
 __global__ void __launch_bounds__(kColThreads) ntt_col_fwd(ColArgs a)
 {
     extern __shared__ uint32_t sm[];
-    constexpr bool S = PS == 0;
     constexpr int LC = col_log_c(LR), C = 1 << LC;
     constexpr int NR = rounds_of(LR);
     const int p = blockIdx.y;
@@ -326,20 +299,20 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_fwd(ColArgs a)
     const size_t col0 = (blockIdx.x % groups) << LC;
     uint32_t *base = a.data + p * a.pstride + (blk << a.m);
     const uint2 *T = tw_table(a.tw, PS, p, 0);
-    const ColIn<S> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, Sr, col0, a.src_len,
-                      q, c_qinv[PS][p], c_r1[PS][p]};
-    const ColOutTw<LR, S> out{base, Sr, col0, T, q, set_log_root(PS) - a.m};
+    const ColIn<PS> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, Sr, col0, a.src_len,
+                       q, c_wp1[PS][p]};
+    const ColOutTw<LR, PS> out{base, Sr, col0, T, q, set_log_root(PS) - a.m};
     if constexpr (NR == 1) {
-        round_io<LR, C, 0, LR, true, 1, true, S>(in, out, T, q);
+        round_io<LR, C, 0, LR, true, 1, true, PS>(in, out, T, q);
     } else {
         const SmemIO<LR, C, true> sio{sm};
-        round_io<LR, C, dif_base(LR, 0), round_size(LR, 0), true, 1, true, S>(in, sio, T, q);
+        round_io<LR, C, dif_base(LR, 0), round_size(LR, 0), true, 1, true, PS>(in, sio, T, q);
         __syncthreads();
         if constexpr (NR == 3) {
-            round_io<LR, C, dif_base(LR, 1), round_size(LR, 1), true, 1, true, S>(sio, sio, T, q);
+            round_io<LR, C, dif_base(LR, 1), round_size(LR, 1), true, 1, true, PS>(sio, sio, T, q);
             __syncthreads();
         }
-        round_io<LR, C, 0, round_size(LR, NR - 1), true, 1, true, S>(sio, out, T, q);
+        round_io<LR, C, 0, round_size(LR, NR - 1), true, 1, true, PS>(sio, out, T, q);
     }
 }
 
@@ -348,7 +321,6 @@ template <int LR, int PS>
 __global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
 {
     extern __shared__ uint32_t sm[];
-    constexpr bool S = PS == 0;
     constexpr int LC = col_log_c(LR), C = 1 << LC;
     constexpr int NR = rounds_of(LR);
     const int p = blockIdx.y;
@@ -359,19 +331,19 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
     const size_t col0 = (blockIdx.x % groups) << LC;
     uint32_t *base = a.data + p * a.pstride + (blk << a.m);
     const uint2 *Ti = tw_table(a.tw, PS, p, 1);
-    const ColInTw<LR, S> in{base, Sr, col0, Ti, q, set_log_root(PS) - a.m};
+    const ColInTw<LR, PS> in{base, Sr, col0, Ti, q, set_log_root(PS) - a.m};
     const ColOut out{base, Sr, col0};
     if constexpr (NR == 1) {
-        round_io<LR, C, 0, LR, false, 1, true, S>(in, out, Ti, q);
+        round_io<LR, C, 0, LR, false, 1, true, PS>(in, out, Ti, q);
     } else {
         const SmemIO<LR, C, true> sio{sm};
-        round_io<LR, C, 0, dit_size(LR, 0), false, 1, true, S>(in, sio, Ti, q);
+        round_io<LR, C, 0, dit_size(LR, 0), false, 1, true, PS>(in, sio, Ti, q);
         __syncthreads();
         if constexpr (NR == 3) {
-            round_io<LR, C, dit_base(LR, 1), dit_size(LR, 1), false, 1, true, S>(sio, sio, Ti, q);
+            round_io<LR, C, dit_base(LR, 1), dit_size(LR, 1), false, 1, true, PS>(sio, sio, Ti, q);
             __syncthreads();
         }
-        round_io<LR, C, dit_base(LR, NR - 1), dit_size(LR, NR - 1), false, 1, true, S>(sio, out,
+        round_io<LR, C, dit_base(LR, NR - 1), dit_size(LR, NR - 1), false, 1, true, PS>(sio, out,
                                                                                         Ti, q);
     }
 }
@@ -431,7 +403,6 @@ template <int LR, bool SQ, int PS>
 __global__ void __launch_bounds__(kRowThreads) ntt_row_mul(RowArgs a)
 {
     extern __shared__ uint32_t sm[];
-    constexpr bool S = PS == 0;
     constexpr int NR = rounds_of(LR);
     constexpr int NA = SQ ? 1 : 2;
     constexpr int EL = round_size(LR, NR - 1);
@@ -450,14 +421,14 @@ __global__ void __launch_bounds__(kRowThreads) ntt_row_mul(RowArgs a)
     const uint32_t *fb = a.F + p * a.fpstride + (tb << a.n) + off;
     const uint2 *T = tw_table(a.tw, PS, p, 0);
     const uint2 *Ti = tw_table(a.tw, PS, p, 1);
-    const uint32_t sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
+    const uint2 sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
     const SmemIO<LR, C, false> sio{sm};
     // forward rounds but the last
-    round_io<LR, C, dif_base(LR, 0), round_size(LR, 0), true, NA, false, S>(RowIn<LR>{fa, fb},
+    round_io<LR, C, dif_base(LR, 0), round_size(LR, 0), true, NA, false, PS>(RowIn<LR>{fa, fb},
                                                                              sio, T, q);
     __syncthreads();
     if constexpr (NR == 3) {
-        round_io<LR, C, dif_base(LR, 1), round_size(LR, 1), true, NA, false, S>(sio, sio, T, q);
+        round_io<LR, C, dif_base(LR, 1), round_size(LR, 1), true, NA, false, PS>(sio, sio, T, q);
         __syncthreads();
     }
     // last forward round + pointwise product + first inverse round
@@ -467,23 +438,23 @@ __global__ void __launch_bounds__(kRowThreads) ntt_row_mul(RowArgs a)
         const int base = (g & (NGC - 1)) << EL;
         uint32_t x[NA][1 << EL];
         sio.template load<EL, 0, NA>(x, base, c);
-        dif_stages<EL, 0, NA, S>(x, 0, T, q);
+        dif_stages<EL, 0, NA, PS>(x, 0, T, q);
         uint32_t z[1][1 << EL];
 #pragma unroll
         for (int j = 0; j < (1 << EL); j++)
-            z[0][j] = mont<S>(mont<S>(x[0][j], x[NA - 1][j], q, qinv), sc, q, qinv);
-        dit_stages<EL, 0, 1, S>(z, 0, Ti, q);
+            z[0][j] = pmul<PS>(x[0][j], x[NA - 1][j], sc, q, qinv);
+        dit_stages<EL, 0, 1, PS>(z, 0, Ti, q);
         sio.template store<EL, 0, 1>(z, base, c);
     }
     __syncthreads();
     uint32_t *g = a.G + p * a.gpstride + (k << a.n) + off;
     if constexpr (NR == 2) {
-        round_io<LR, C, dit_base(LR, 1), dit_size(LR, 1), false, 1, false, S>(sio, RowOut<LR>{g},
+        round_io<LR, C, dit_base(LR, 1), dit_size(LR, 1), false, 1, false, PS>(sio, RowOut<LR>{g},
                                                                                Ti, q);
     } else {
-        round_io<LR, C, dit_base(LR, 1), dit_size(LR, 1), false, 1, false, S>(sio, sio, Ti, q);
+        round_io<LR, C, dit_base(LR, 1), dit_size(LR, 1), false, 1, false, PS>(sio, sio, Ti, q);
         __syncthreads();
-        round_io<LR, C, dit_base(LR, 2), dit_size(LR, 2), false, 1, false, S>(sio, RowOut<LR>{g},
+        round_io<LR, C, dit_base(LR, 2), dit_size(LR, 2), false, 1, false, PS>(sio, RowOut<LR>{g},
                                                                                Ti, q);
     }
 }
