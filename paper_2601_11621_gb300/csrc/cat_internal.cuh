@@ -55,8 +55,10 @@ constexpr int kLogSet1 = 26;
 // Twiddle tables per (set, prime, direction), w the set's primitive 2^L-th
 // root of unity (L = set_log_root) or its inverse, entries as pairs in the
 // set's multiplier form:
-//   [0, 2^13)               w^(j 2^(L-13)): the roots of order <= 2^13 used by
-//                           the butterfly stages of a sub-transform;
+//   [2^s, 2^(s+1))          w_{2^(s+1)}^j, j < 2^s, for s < 13: the twiddles
+//                           of butterfly stage s (half-span 2^s) of a
+//                           sub-transform, consecutive in j so that the
+//                           lanes of a warp read consecutive entries;
 //   three tables of 512     w^j, w^(512 j), w^(2^18 j): any w^E, E < 2^L,
 //                           as a product of three small-table entries.
 constexpr int kTwStage = 1 << 13;
@@ -223,18 +225,6 @@ __device__ __forceinline__ uint32_t mul_w(uint32_t a, uint2 w, uint32_t q)
     if constexpr (PS == 0) return shoup(a, w.x, w.y, q);
     else if constexpr (PS == 1) return csub(shoup(a, w.x, w.y, q), q);
     else return mont_mul_pre(a, w.x, w.y, q);
-}
-
-// a w1 w2 w3 for any 32-bit a, into the forward range (set 1 corrects once:
-// Shoup's product accepts an unreduced input)
-template <int PS>
-__device__ __forceinline__ uint32_t mul_w3(uint32_t a, uint2 w1, uint2 w2, uint2 w3, uint32_t q)
-{
-    if constexpr (PS == 2)
-        return mont_mul_pre(mont_mul_pre(mont_mul_pre(a, w1.x, w1.y, q), w2.x, w2.y, q), w3.x,
-                            w3.y, q);
-    const uint32_t t = shoup(shoup(shoup(a, w1.x, w1.y, q), w2.x, w2.y, q), w3.x, w3.y, q);
-    return PS == 0 ? t : csub(t, q);
 }
 
 // Forward (decimation-in-frequency) butterfly (x, y) <- (x + y, (x - y) w)

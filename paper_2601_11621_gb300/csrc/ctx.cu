@@ -191,7 +191,11 @@ void twiddle_tables_host(uint2 *h)
         for (int d = 0; d < 2; d++) {
             const uint32_t root = d == 0 ? w : powmod_u32(w, (1u << L) - 1, q);
             uint2 *T = h + (((size_t)set * kNumPrimes + i) * 2 + d) * kTwPerDir;
-            fill_powers(T, kTwStage, powmod_u32(root, 1u << (L - 13), q), q, sh);
+            // stage s (half-span 2^s, s < 13): w_{2^(s+1)}^j at 2^s + j, j < 2^s
+            fill_powers(T, 1, 1, q, sh);
+            for (int st = 0; st < 13; st++)
+                fill_powers(T + (1 << st), 1 << st, powmod_u32(root, 1u << (L - 1 - st), q), q,
+                            sh);
             fill_powers(T + kTwStage, kTwSmall, root, q, sh);
             fill_powers(T + kTwStage + kTwSmall, kTwSmall, powmod_u32(root, 1u << 9, q), q, sh);
             fill_powers(T + kTwStage + 2 * kTwSmall, kTwSmall, powmod_u32(root, 1u << 18, q), q,

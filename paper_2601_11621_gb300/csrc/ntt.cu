@@ -37,13 +37,17 @@ namespace cat {
      {f(ntt_prime(2, 0)), f(ntt_prime(2, 1)), f(ntt_prime(2, 2))}}
 #define CAT_Q(q) (q)
 #define CAT_WP1(q) shoup_c(1u, q)
+#define CAT_R2(q) to_mont_c(to_mont_c(1u, q), q)
 __constant__ uint32_t c_q[kNumSets][kNumPrimes] = CAT_SET_CONST(CAT_Q);
 __constant__ uint32_t c_qinv[kNumSets][kNumPrimes] = CAT_SET_CONST(inv32);
 // floor(2^32 / q): Shoup's companion of 1, which reduces raw limbs
 __constant__ uint32_t c_wp1[kNumSets][kNumPrimes] = CAT_SET_CONST(CAT_WP1);
+// 2^64 mod q: turns a residue v into its Montgomery form v 2^32 mod q
+__constant__ uint32_t c_r2[kNumSets][kNumPrimes] = CAT_SET_CONST(CAT_R2);
 #undef CAT_SET_CONST
 #undef CAT_Q
 #undef CAT_WP1
+#undef CAT_R2
 
 // Garner constants of a set, in Montgomery form.
 template <int PS>
@@ -83,17 +87,46 @@ __device__ __forceinline__ const uint2 *tw_table(const uint2 *tw, int set, int p
     return tw + (((size_t)set * kNumPrimes + p) * 2 + dir) * kTwPerDir;
 }
 
-// x * w^E for E below the set's root order, w the set's root of unity:
-// three products with entries of the three 512-entry tables (which stay in
-// L1), w^E = w^(E mod 512) * w^(512 ((E >> 9) mod 512)) * w^(2^18 (E >> 18)).
-// Any 32-bit x; the result is in the set's forward range.
+// w^E 2^32 mod q (the Montgomery form of w^E, below q) from the three small
+// tables: for Shoup-form sets the plain product, then one Montgomery product
+// with r2 = 2^64 mod q; for set 2 the entries already are Montgomery forms.
 template <int PS>
-__device__ __forceinline__ uint32_t tw_apply(uint32_t x, const uint2 *T, uint32_t E, uint32_t q)
+__device__ __forceinline__ uint32_t tw_pow_mont(const uint2 *T, uint32_t E, uint32_t q,
+                                                uint32_t qinv, uint32_t r2)
 {
     const uint2 a = __ldg(&T[kTwStage + (E & (kTwSmall - 1))]);
     const uint2 b = __ldg(&T[kTwStage + kTwSmall + ((E >> 9) & (kTwSmall - 1))]);
     const uint2 c = __ldg(&T[kTwStage + 2 * kTwSmall + (E >> 18)]);
-    return mul_w3<PS>(x, a, b, c, q);
+    if constexpr (PS == 2) {
+        return mont_mul_pre(mont_mul_pre(a.x, b.x, b.y, q), c.x, c.y, q);
+    } else {
+        const uint32_t v = csub(shoup(shoup(a.x, b.x, b.y, q), c.x, c.y, q), q);
+        return mont<true>(v, r2, q, qinv);
+    }
+}
+
+// x v for any 32-bit x and a Montgomery-form multiplier vm = v 2^32 mod q,
+// into the set's forward range (set 0: hi(x vm) - hi(m q) + q lies in (0, 2q)).
+template <int PS>
+__device__ __forceinline__ uint32_t mul_mont(uint32_t x, uint32_t vm, uint32_t q, uint32_t qinv)
+{
+    if constexpr (PS == 0) {
+        const uint32_t hi = __umulhi(x, vm);
+        const uint32_t m = (x * vm) * qinv;
+        return hi - __umulhi(m, q) + q;
+    } else if constexpr (PS == 1) {
+        return mont<true>(x, vm, q, qinv);
+    } else {
+        return mont_mul(x, vm, q, qinv);
+    }
+}
+
+// Product of two Montgomery-form multipliers, reduced below q.
+template <int PS>
+__device__ __forceinline__ uint32_t mont_step(uint32_t vm, uint32_t um, uint32_t q, uint32_t qinv)
+{
+    if constexpr (PS == 2) return mont_mul(vm, um, q, qinv);
+    return mont<true>(vm, um, q, qinv);
 }
 
 // ----------------------------------------------- remaindering and carries

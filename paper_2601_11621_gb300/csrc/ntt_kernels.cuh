@@ -10,8 +10,8 @@
 // round straight from global memory and writes its last round straight to
 // global memory; rounds in between exchange through shared memory (one
 // barrier per round).  Stage s (half-span 2^s) multiplies by
-// w_{2^(s+1)}^(i mod 2^s), entry (i mod 2^s) << (12 - s) of the table's high
-// part (2^(s+1) <= 2^13).
+// w_{2^(s+1)}^(i mod 2^s), entry 2^s + (i mod 2^s) of the stage table
+// (2^(s+1) <= 2^13).
 #pragma once
 
 __host__ __device__ constexpr int rounds_of(int lr) { return (lr + 3) / 4; }
@@ -43,9 +43,20 @@ __host__ __device__ constexpr int dit_base(int lr, int rd)
     return b;
 }
 
-// Shared-memory address swizzle: flips the bank bits by the row-of-32 index,
-// which makes every round's access pattern free of bank conflicts.
-__device__ __forceinline__ int swz(int a) { return a ^ ((a >> 5) & 31); }
+// Shared-memory address swizzle: the bank bits of address a are XORed with a
+// GF(2)-linear image f(t) of its row-of-32 index t = (a >> 5) mod 32, f
+// sending the bits of t to 1, 10, 20, 24, 16.  In a round with base bit
+// B < 5 the lanes of a warp differ in address bits [0, B) and in bits at and
+// above B + E; f is chosen so that those five bits always land on five
+// independent bank bits for the round shapes used here (E = 3 or 4 with
+// B = 0, 3 or 4 on contiguous rows; the group bit 7 of 16-column tiles), so
+// no round has a bank conflict.  Rounds with B >= 5 are conflict-free under
+// any such XOR.
+__device__ __forceinline__ int swz(int a)
+{
+    const int t = (a >> 5) & 31;
+    return a ^ t ^ ((t & 6) << 2) ^ ((t & 8) << 1);
+}
 
 // In a round with B = 0 the twiddle index is a compile-time constant, and the
 // butterflies with (k mod 2^st) = 0 have twiddle w^0 = 1: no multiply.
@@ -64,7 +75,7 @@ __device__ __forceinline__ void dif_stages(uint32_t (&x)[NA][1 << E], int glow, 
                 continue;
             }
             const int p = glow + ((k & ((1 << st) - 1)) << B);
-            const uint2 w = __ldg(&T[p << (12 - B - st)]);
+            const uint2 w = __ldg(&T[(1 << (B + st)) + p]);
 #pragma unroll
             for (int a = 0; a < NA; a++) bf_dif<PS>(x[a][k], x[a][k + (1 << st)], w, q);
         }
@@ -86,7 +97,7 @@ __device__ __forceinline__ void dit_stages(uint32_t (&x)[NA][1 << E], int glow, 
                 continue;
             }
             const int p = glow + ((k & ((1 << st) - 1)) << B);
-            const uint2 w = __ldg(&Ti[p << (12 - B - st)]);
+            const uint2 w = __ldg(&Ti[(1 << (B + st)) + p]);
 #pragma unroll
             for (int a = 0; a < NA; a++) bf_dit<PS>(x[a][k], x[a][k + (1 << st)], w, q);
         }
@@ -226,26 +237,51 @@ struct ColIn {
     }
 };
 
+__host__ __device__ constexpr int bitrev_c(int j, int bits)
+{
+    int r = 0;
+    for (int b = 0; b < bits; b++) r |= ((j >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+// The twiddle w_M^(col * bitrev(row)) of the last forward (first inverse)
+// round, whose groups are 2^E consecutive rows base + k (B = 0): with
+// bitrev_LR(base + k) = bitrev_LR(base) + bitrev_E(k) 2^(LR - E) it is
+// W0 U^bitrev_E(k), W0 = w^(col bitrev_LR(base)), U = w^(col 2^(LR - E)) (in
+// units of the root order, hence the shift), so a group takes two table
+// products and one Montgomery product per point to step through the powers.
+template <int LR, int PS>
+struct ColTw {
+    const uint2 *T;
+    uint32_t q, qinv, r2;
+    int shift;  // log2(root order) - m
+    template <int E, class F>
+    __device__ __forceinline__ void each(uint32_t gcol, int base, F &&f) const
+    {
+        uint32_t v = tw_pow_mont<PS>(T, (gcol * bitrev((uint32_t)base, LR)) << shift, q, qinv, r2);
+        const uint32_t u = tw_pow_mont<PS>(T, gcol << (LR - E + shift), q, qinv, r2);
+#pragma unroll
+        for (int j = 0; j < (1 << E); j++) {
+            f(bitrev_c(j, E), v);
+            if (j + 1 < (1 << E)) v = mont_step<PS>(v, u, q, qinv);
+        }
+    }
+};
+
 // Forward pass output: element (row, col) times w_M^(col * bitrev(row)).
 template <int LR, int PS>
 struct ColOutTw {
     uint32_t *p;
     size_t S, col0;
-    const uint2 *T;
-    uint32_t q;
-    int shift;  // log2(root order) - m
+    ColTw<LR, PS> tw;
     template <int E, int B, int NA>
     __device__ __forceinline__ void store(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
+        static_assert(B == 0, "the twiddled round has contiguous rows");
         const uint32_t gcol = (uint32_t)(col0 + c);
-#pragma unroll
-        for (int k = 0; k < (1 << E); k++) {
-            const int row = base + (k << B);
-            const uint32_t e = (gcol * bitrev((uint32_t)row, LR)) << shift;
-            uint32_t v = x[0][k];
-            if (e) v = tw_apply<PS>(v, T, e, q);
-            p[(size_t)row * S + gcol] = v;
-        }
+        tw.template each<E>(gcol, base, [&](int k, uint32_t v) {
+            p[(size_t)(base + k) * S + gcol] = mul_mont<PS>(x[0][k], v, tw.q, tw.qinv);
+        });
     }
 };
 
@@ -254,21 +290,15 @@ template <int LR, int PS>
 struct ColInTw {
     const uint32_t *p;
     size_t S, col0;
-    const uint2 *Ti;
-    uint32_t q;
-    int shift;
+    ColTw<LR, PS> tw;
     template <int E, int B, int NA>
     __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
+        static_assert(B == 0, "the twiddled round has contiguous rows");
         const uint32_t gcol = (uint32_t)(col0 + c);
-#pragma unroll
-        for (int k = 0; k < (1 << E); k++) {
-            const int row = base + (k << B);
-            uint32_t v = p[(size_t)row * S + gcol];
-            const uint32_t e = (gcol * bitrev((uint32_t)row, LR)) << shift;
-            if (e) v = tw_apply<PS>(v, Ti, e, q);
-            x[0][k] = v;
-        }
+        tw.template each<E>(gcol, base, [&](int k, uint32_t v) {
+            x[0][k] = mul_mont<PS>(p[(size_t)(base + k) * S + gcol], v, tw.q, tw.qinv);
+        });
     }
 };
 
@@ -301,7 +331,9 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_fwd(ColArgs a)
     const uint2 *T = tw_table(a.tw, PS, p, 0);
     const ColIn<PS> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, Sr, col0, a.src_len,
                        q, c_wp1[PS][p]};
-    const ColOutTw<LR, PS> out{base, Sr, col0, T, q, set_log_root(PS) - a.m};
+    const ColOutTw<LR, PS> out{
+        base, Sr, col0,
+        ColTw<LR, PS>{T, q, c_qinv[PS][p], c_r2[PS][p], set_log_root(PS) - a.m}};
     if constexpr (NR == 1) {
         round_io<LR, C, 0, LR, true, 1, true, PS>(in, out, T, q);
     } else {
@@ -331,7 +363,9 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
     const size_t col0 = (blockIdx.x % groups) << LC;
     uint32_t *base = a.data + p * a.pstride + (blk << a.m);
     const uint2 *Ti = tw_table(a.tw, PS, p, 1);
-    const ColInTw<LR, PS> in{base, Sr, col0, Ti, q, set_log_root(PS) - a.m};
+    const ColInTw<LR, PS> in{
+        base, Sr, col0,
+        ColTw<LR, PS>{Ti, q, c_qinv[PS][p], c_r2[PS][p], set_log_root(PS) - a.m}};
     const ColOut out{base, Sr, col0};
     if constexpr (NR == 1) {
         round_io<LR, C, 0, LR, false, 1, true, PS>(in, out, Ti, q);
