@@ -52,7 +52,7 @@ __host__ __device__ constexpr int dit_base(int lr, int rd)
 // B = 0, 3 or 4 on contiguous rows; the group bit 7 of 16-column tiles), so
 // no round has a bank conflict.  Rounds with B >= 5 are conflict-free under
 // any such XOR.
-__device__ __forceinline__ int swz(int a)
+__host__ __device__ constexpr int swz(int a)
 {
     const int t = (a >> 5) & 31;
     return a ^ t ^ ((t & 6) << 2) ^ ((t & 8) << 1);
@@ -129,33 +129,44 @@ __device__ __forceinline__ void round_io(const IN &in, const OUT &out, const uin
     }
 }
 
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
+
 // NA arrays of 2^LR x C words each, back to back, swizzled.  COLFAST: the
 // columns interleave (point i of column c at i C + c); otherwise each column
-// is contiguous (at c 2^LR + i).
+// is contiguous (at c 2^LR + i).  A group's points base + k 2^B have offsets
+// d_k = k 2^B (times C when interleaved) whose bits the group's own address
+// a0 never has, and swz is linear over XOR on disjoint bits, so the swizzled
+// address is swz(a0) ^ swz(d_k): one XOR with a compile-time constant.
 template <int LR, int C, bool COLFAST>
 struct SmemIO {
     uint32_t *s;
-    __device__ __forceinline__ static int at(int i, int c)
+    static constexpr int LC = ilog2c(C);
+    template <int B>
+    __device__ __forceinline__ static int group_addr(int base, int c)
     {
-        return COLFAST ? swz(i * C + c) : c * (1 << LR) + swz(i);
+        return COLFAST ? swz(base * C + c) : (c << LR) + swz(base);
     }
     template <int E, int B, int NA>
     __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
+        constexpr int SH = COLFAST ? B + LC : B;
+        const int a0 = group_addr<B>(base, c);
 #pragma unroll
         for (int a = 0; a < NA; a++)
 #pragma unroll
             for (int k = 0; k < (1 << E); k++)
-                x[a][k] = s[a * ((1 << LR) * C) + at(base + (k << B), c)];
+                x[a][k] = s[a * ((1 << LR) * C) + (a0 ^ swz(k << SH))];
     }
     template <int E, int B, int NA>
     __device__ __forceinline__ void store(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
+        constexpr int SH = COLFAST ? B + LC : B;
+        const int a0 = group_addr<B>(base, c);
 #pragma unroll
         for (int a = 0; a < NA; a++)
 #pragma unroll
             for (int k = 0; k < (1 << E); k++)
-                s[a * ((1 << LR) * C) + at(base + (k << B), c)] = x[a][k];
+                s[a * ((1 << LR) * C) + (a0 ^ swz(k << SH))] = x[a][k];
     }
 };
 
@@ -221,14 +232,15 @@ template <int PS>
 struct ColIn {
     const uint32_t *p;
     const uint32_t *src;
-    size_t S, col0, src_len;
+    uint32_t S, col0, src_len;  // offsets within one transform fit in 32 bits
     uint32_t q, wp1;
     template <int E, int B, int NA>
     __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
+        const uint32_t i0 = (uint32_t)base * S + col0 + c;
 #pragma unroll
         for (int k = 0; k < (1 << E); k++) {
-            const size_t idx = (size_t)(base + (k << B)) * S + col0 + c;
+            const uint32_t idx = i0 + (uint32_t)k * (S << B);
             if (src)
                 x[0][k] = idx < src_len ? reduce_in<PS>(src[idx], q, wp1) : 0u;
             else
@@ -272,15 +284,16 @@ struct ColTw {
 template <int LR, int PS>
 struct ColOutTw {
     uint32_t *p;
-    size_t S, col0;
+    uint32_t S, col0;
     ColTw<LR, PS> tw;
     template <int E, int B, int NA>
     __device__ __forceinline__ void store(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
         static_assert(B == 0, "the twiddled round has contiguous rows");
-        const uint32_t gcol = (uint32_t)(col0 + c);
+        const uint32_t gcol = col0 + c;
+        const uint32_t i0 = (uint32_t)base * S + gcol;
         tw.template each<E>(gcol, base, [&](int k, uint32_t v) {
-            p[(size_t)(base + k) * S + gcol] = mul_mont<PS>(x[0][k], v, tw.q, tw.qinv);
+            p[i0 + (uint32_t)k * S] = mul_mont<PS>(x[0][k], v, tw.q, tw.qinv);
         });
     }
 };
@@ -289,27 +302,29 @@ struct ColOutTw {
 template <int LR, int PS>
 struct ColInTw {
     const uint32_t *p;
-    size_t S, col0;
+    uint32_t S, col0;
     ColTw<LR, PS> tw;
     template <int E, int B, int NA>
     __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
         static_assert(B == 0, "the twiddled round has contiguous rows");
-        const uint32_t gcol = (uint32_t)(col0 + c);
+        const uint32_t gcol = col0 + c;
+        const uint32_t i0 = (uint32_t)base * S + gcol;
         tw.template each<E>(gcol, base, [&](int k, uint32_t v) {
-            x[0][k] = mul_mont<PS>(p[(size_t)(base + k) * S + gcol], v, tw.q, tw.qinv);
+            x[0][k] = mul_mont<PS>(p[i0 + (uint32_t)k * S], v, tw.q, tw.qinv);
         });
     }
 };
 
 struct ColOut {
     uint32_t *p;
-    size_t S, col0;
+    uint32_t S, col0;
     template <int E, int B, int NA>
     __device__ __forceinline__ void store(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
+        const uint32_t i0 = (uint32_t)base * S + col0 + c;
 #pragma unroll
-        for (int k = 0; k < (1 << E); k++) p[(size_t)(base + (k << B)) * S + col0 + c] = x[0][k];
+        for (int k = 0; k < (1 << E); k++) p[i0 + (uint32_t)k * (S << B)] = x[0][k];
     }
 };
 
@@ -329,10 +344,11 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_fwd(ColArgs a)
     const size_t col0 = (blockIdx.x % groups) << LC;
     uint32_t *base = a.data + p * a.pstride + (blk << a.m);
     const uint2 *T = tw_table(a.tw, PS, p, 0);
-    const ColIn<PS> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, Sr, col0, a.src_len,
+    const ColIn<PS> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, (uint32_t)Sr,
+                       (uint32_t)col0, (uint32_t)a.src_len,
                        q, c_wp1[PS][p]};
     const ColOutTw<LR, PS> out{
-        base, Sr, col0,
+        base, (uint32_t)Sr, (uint32_t)col0,
         ColTw<LR, PS>{T, q, c_qinv[PS][p], c_r2[PS][p], set_log_root(PS) - a.m}};
     if constexpr (NR == 1) {
         round_io<LR, C, 0, LR, true, 1, true, PS>(in, out, T, q);
@@ -364,9 +380,9 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
     uint32_t *base = a.data + p * a.pstride + (blk << a.m);
     const uint2 *Ti = tw_table(a.tw, PS, p, 1);
     const ColInTw<LR, PS> in{
-        base, Sr, col0,
+        base, (uint32_t)Sr, (uint32_t)col0,
         ColTw<LR, PS>{Ti, q, c_qinv[PS][p], c_r2[PS][p], set_log_root(PS) - a.m}};
-    const ColOut out{base, Sr, col0};
+    const ColOut out{base, (uint32_t)Sr, (uint32_t)col0};
     if constexpr (NR == 1) {
         round_io<LR, C, 0, LR, false, 1, true, PS>(in, out, Ti, q);
     } else {
