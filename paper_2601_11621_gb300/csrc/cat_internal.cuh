@@ -60,7 +60,10 @@ constexpr int kLogSet1 = 26;
 //                           sub-transform, consecutive in j so that the
 //                           lanes of a warp read consecutive entries;
 //   three tables of 512     w^j, w^(512 j), w^(2^18 j): any w^E, E < 2^L,
-//                           as a product of three small-table entries.
+//                           as a product of three small-table entries (in
+//                           Shoup-form sets the third table is stored times
+//                           2^32 mod q, so the product is w^E's Montgomery
+//                           form).
 constexpr int kTwStage = 1 << 13;
 constexpr int kTwSmall = 512;
 constexpr int kTwPerDir = kTwStage + 3 * kTwSmall;  // uint2 entries per (prime, direction)

@@ -156,13 +156,14 @@ static uint32_t find_generator(uint32_t q)
     }
 }
 
-// Powers 1, s, s^2, ... (count of them) of `step` into T as multiplier pairs:
-// (x, floor(x 2^32 / q)) in Shoup's form, else (x 2^32 mod q, that times
-// q^-1 mod 2^32) in Montgomery's.
-static void fill_powers(uint2 *T, int count, uint32_t step, uint32_t q, bool shoup)
+// Powers f, f s, f s^2, ... (count of them) of `step` into T as multiplier
+// pairs: (x, floor(x 2^32 / q)) in Shoup's form, else (x 2^32 mod q, that
+// times q^-1 mod 2^32) in Montgomery's.
+static void fill_powers(uint2 *T, int count, uint32_t step, uint32_t q, bool shoup,
+                        uint32_t first = 1)
 {
     const uint32_t qi = inv32(q);
-    uint64_t x = 1;
+    uint64_t x = first % q;
     for (int j = 0; j < count; j++) {
         if (shoup) {
             T[j] = make_uint2((uint32_t)x, shoup_c((uint32_t)x, q));
@@ -198,8 +199,10 @@ void twiddle_tables_host(uint2 *h)
                             sh);
             fill_powers(T + kTwStage, kTwSmall, root, q, sh);
             fill_powers(T + kTwStage + kTwSmall, kTwSmall, powmod_u32(root, 1u << 9, q), q, sh);
+            // the third table times 2^32 in Shoup-form sets, so that products
+            // of small-table entries come out in Montgomery form
             fill_powers(T + kTwStage + 2 * kTwSmall, kTwSmall, powmod_u32(root, 1u << 18, q), q,
-                        sh);
+                        sh, sh ? to_mont_c(1, q) : 1u);
         }
     }
 }

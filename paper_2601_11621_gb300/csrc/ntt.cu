@@ -37,17 +37,14 @@ namespace cat {
      {f(ntt_prime(2, 0)), f(ntt_prime(2, 1)), f(ntt_prime(2, 2))}}
 #define CAT_Q(q) (q)
 #define CAT_WP1(q) shoup_c(1u, q)
-#define CAT_R2(q) to_mont_c(to_mont_c(1u, q), q)
 __constant__ uint32_t c_q[kNumSets][kNumPrimes] = CAT_SET_CONST(CAT_Q);
 __constant__ uint32_t c_qinv[kNumSets][kNumPrimes] = CAT_SET_CONST(inv32);
 // floor(2^32 / q): Shoup's companion of 1, which reduces raw limbs
 __constant__ uint32_t c_wp1[kNumSets][kNumPrimes] = CAT_SET_CONST(CAT_WP1);
-// 2^64 mod q: turns a residue v into its Montgomery form v 2^32 mod q
-__constant__ uint32_t c_r2[kNumSets][kNumPrimes] = CAT_SET_CONST(CAT_R2);
+
 #undef CAT_SET_CONST
 #undef CAT_Q
 #undef CAT_WP1
-#undef CAT_R2
 
 // Garner constants of a set, in Montgomery form.
 template <int PS>
@@ -88,11 +85,12 @@ __device__ __forceinline__ const uint2 *tw_table(const uint2 *tw, int set, int p
 }
 
 // w^E 2^32 mod q (the Montgomery form of w^E, below q) from the three small
-// tables: for Shoup-form sets the plain product, then one Montgomery product
-// with r2 = 2^64 mod q; for set 2 the entries already are Montgomery forms.
+// tables.  In Shoup-form sets the third table holds w^(2^18 j) 2^32, so two
+// Shoup products give the Montgomery form directly; in set 2 all entries are
+// Montgomery forms and Montgomery products keep that form.
 template <int PS>
 __device__ __forceinline__ uint32_t tw_pow_mont(const uint2 *T, uint32_t E, uint32_t q,
-                                                uint32_t qinv, uint32_t r2)
+                                                uint32_t qinv)
 {
     const uint2 a = __ldg(&T[kTwStage + (E & (kTwSmall - 1))]);
     const uint2 b = __ldg(&T[kTwStage + kTwSmall + ((E >> 9) & (kTwSmall - 1))]);
@@ -100,8 +98,7 @@ __device__ __forceinline__ uint32_t tw_pow_mont(const uint2 *T, uint32_t E, uint
     if constexpr (PS == 2) {
         return mont_mul_pre(mont_mul_pre(a.x, b.x, b.y, q), c.x, c.y, q);
     } else {
-        const uint32_t v = csub(shoup(shoup(a.x, b.x, b.y, q), c.x, c.y, q), q);
-        return mont<true>(v, r2, q, qinv);
+        return csub(shoup(shoup(a.x, b.x, b.y, q), c.x, c.y, q), q);
     }
 }
 

@@ -16,10 +16,12 @@
 
 __host__ __device__ constexpr int rounds_of(int lr) { return (lr + 3) / 4; }
 
-// size of DIF round rd (counted from the top stage bits)
+// size of DIF round rd (counted from the top stage bits); when the stages do
+// not split evenly the last rounds take the extra ones, so that the round at
+// stage bits [0, E) (which carries the column twiddles) is the largest
 __host__ __device__ constexpr int round_size(int lr, int rd)
 {
-    return lr / rounds_of(lr) + (rd < lr % rounds_of(lr) ? 1 : 0);
+    return lr / rounds_of(lr) + (rd >= rounds_of(lr) - lr % rounds_of(lr) ? 1 : 0);
 }
 
 // lowest stage bit of DIF round rd
@@ -265,17 +267,31 @@ __host__ __device__ constexpr int bitrev_c(int j, int bits)
 template <int LR, int PS>
 struct ColTw {
     const uint2 *T;
-    uint32_t q, qinv, r2;
-    int shift;  // log2(root order) - m
-    template <int E, class F>
+    uint32_t q, qinv;
+    int shift;   // log2(root order) - m
+    uint32_t u;  // U of this thread's column, when it has one column
+    static constexpr int E = round_size(LR, rounds_of(LR) - 1);
+    static constexpr bool kOneColumn = (1 << col_log_c(LR)) <= kColThreads;
+    __device__ __forceinline__ uint32_t step_of(uint32_t gcol) const
+    {
+        return tw_pow_mont<PS>(T, gcol << (LR - E + shift), q, qinv);
+    }
+    // Each thread's groups share one column when the tile has at most as many
+    // columns as the block has threads (c = threadIdx mod C): U once per thread.
+    __device__ __forceinline__ void init(uint32_t col0)
+    {
+        if (kOneColumn) u = step_of(col0 + (threadIdx.x & ((1u << col_log_c(LR)) - 1)));
+    }
+    template <int EE, class F>
     __device__ __forceinline__ void each(uint32_t gcol, int base, F &&f) const
     {
-        uint32_t v = tw_pow_mont<PS>(T, (gcol * bitrev((uint32_t)base, LR)) << shift, q, qinv, r2);
-        const uint32_t u = tw_pow_mont<PS>(T, gcol << (LR - E + shift), q, qinv, r2);
+        static_assert(EE == E, "twiddles are applied in the round at stage bits [0, E)");
+        uint32_t v = tw_pow_mont<PS>(T, (gcol * bitrev((uint32_t)base, LR)) << shift, q, qinv);
+        const uint32_t uu = kOneColumn ? u : step_of(gcol);
 #pragma unroll
         for (int j = 0; j < (1 << E); j++) {
             f(bitrev_c(j, E), v);
-            if (j + 1 < (1 << E)) v = mont_step<PS>(v, u, q, qinv);
+            if (j + 1 < (1 << E)) v = mont_step<PS>(v, uu, q, qinv);
         }
     }
 };
@@ -347,9 +363,9 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_fwd(ColArgs a)
     const ColIn<PS> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, (uint32_t)Sr,
                        (uint32_t)col0, (uint32_t)a.src_len,
                        q, c_wp1[PS][p]};
-    const ColOutTw<LR, PS> out{
-        base, (uint32_t)Sr, (uint32_t)col0,
-        ColTw<LR, PS>{T, q, c_qinv[PS][p], c_r2[PS][p], set_log_root(PS) - a.m}};
+    ColTw<LR, PS> tw{T, q, c_qinv[PS][p], set_log_root(PS) - a.m, 0u};
+    tw.init((uint32_t)col0);
+    const ColOutTw<LR, PS> out{base, (uint32_t)Sr, (uint32_t)col0, tw};
     if constexpr (NR == 1) {
         round_io<LR, C, 0, LR, true, 1, true, PS>(in, out, T, q);
     } else {
@@ -379,9 +395,9 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
     const size_t col0 = (blockIdx.x % groups) << LC;
     uint32_t *base = a.data + p * a.pstride + (blk << a.m);
     const uint2 *Ti = tw_table(a.tw, PS, p, 1);
-    const ColInTw<LR, PS> in{
-        base, (uint32_t)Sr, (uint32_t)col0,
-        ColTw<LR, PS>{Ti, q, c_qinv[PS][p], c_r2[PS][p], set_log_root(PS) - a.m}};
+    ColTw<LR, PS> tw{Ti, q, c_qinv[PS][p], set_log_root(PS) - a.m, 0u};
+    tw.init((uint32_t)col0);
+    const ColInTw<LR, PS> in{base, (uint32_t)Sr, (uint32_t)col0, tw};
     const ColOut out{base, (uint32_t)Sr, (uint32_t)col0};
     if constexpr (NR == 1) {
         round_io<LR, C, 0, LR, false, 1, true, PS>(in, out, Ti, q);
