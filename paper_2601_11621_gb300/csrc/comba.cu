@@ -92,41 +92,68 @@ __global__ void comba_thread(const uint32_t *in, size_t nprod, uint32_t *out)
 
 constexpr int kWarpsPerBlock = 8;
 
-// Lane l owns output columns [l W, l W + W), W = 2S/32 >= 2.  Its column sums
-// form a number N_l = low_l + high_l 2^(32W) with high_l < 2^41; the product
-// is sum_l (low_l + high_{l-1}) 2^(32 W l).  Each lane's addition
-// low_l + high_{l-1} carries at most one bit out, and the one-bit carries are
-// resolved by a generate/propagate scan across the warp.
+// Lane l owns output columns [l W, l W + W), W = 2S/32 >= 2, and the lanes
+// step through i = 0 .. S-1 together: column col gains A[i] B[col - i], B read
+// as zero outside [0, S).  At step i lane l needs B[l W - i + w], w < W: a
+// window that slides down by one word per step, so a step is one broadcast
+// read of A[i], one new word of B and W multiply-adds.  The zero-padded copy
+// of B (word j at j' = j + S, j' < 3S) is stored skewed, j' at j' + j' / W, so
+// that the lanes' reads, W words apart, fall in distinct banks (W + 1 is odd).
+//
+// The column sums form a number N_l = low_l + high_l 2^(32W) per lane with
+// high_l < 2^41; the product is sum_l (low_l + high_{l-1}) 2^(32 W l).  Each
+// lane's addition low_l + high_{l-1} carries at most one bit out, and the
+// one-bit carries are resolved by a generate/propagate scan across the warp.
 template <int S>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) comba_warp(const uint32_t *in,
                                                                   size_t nprod, uint32_t *out)
 {
     constexpr int W = 2 * S / 32;
     static_assert(W >= 2, "warp Comba needs at least two columns per lane");
-    __shared__ uint32_t sm[kWarpsPerBlock][2 * S];
+    constexpr int PADN = 3 * S;              // padded indices j' in [0, 3S)
+    constexpr int BWORDS = PADN + PADN / W;  // skewed layout
+    __shared__ uint32_t smA[kWarpsPerBlock][S];
+    __shared__ uint32_t smB[kWarpsPerBlock][BWORDS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const size_t k = (size_t)blockIdx.x * kWarpsPerBlock + wid;
     if (k >= nprod) return;
     const uint32_t *src = in + 2 * k * S;
-    uint32_t *A = sm[wid], *B = sm[wid] + S;
-    for (int i = lane; i < 2 * S; i += 32) A[i] = src[i];
+    uint32_t *A = smA[wid], *Bs = smB[wid];
+    for (int i = lane; i < S; i += 32) A[i] = src[i];
+    for (int jp = lane; jp < PADN; jp += 32) {
+        const int j = jp - S;
+        Bs[jp + jp / W] = (j >= 0 && j < S) ? src[S + j] : 0u;
+    }
     __syncwarp();
+    uint32_t c0[W], c1[W], c2[W], b[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        c0[w] = c1[w] = c2[w] = 0;
+        const int jp = lane * W + w + S;
+        b[w] = Bs[jp + jp / W];
+    }
+#pragma unroll
+    for (int i = 0; i < S; i++) {
+        const uint32_t a = A[i];
+#pragma unroll
+        for (int w = 0; w < W; w++) mac96(a, b[w], c0[w], c1[w], c2[w]);
+        if (i + 1 < S) {
+#pragma unroll
+            for (int w = W - 1; w > 0; w--) b[w] = b[w - 1];
+            // j' = l W + (S - i - 1) with S - i - 1 >= 0: j' / W = l + (S - i - 1) / W
+            b[0] = Bs[lane * (W + 1) + (S - i - 1) + (S - i - 1) / W];
+        }
+    }
     uint32_t limb[W];
-    // accumulate columns left to right, carrying the running 96-bit sum
+    // carry the running 96-bit sum through the lane's columns
     uint32_t r0 = 0, r1 = 0, r2 = 0;
 #pragma unroll
     for (int w = 0; w < W; w++) {
-        const int col = lane * W + w;
-        uint32_t c0 = 0, c1 = 0, c2 = 0;
-        const int lo = col - (S - 1) > 0 ? col - (S - 1) : 0;
-        const int hi = col < S - 1 ? col : S - 1;
-        for (int i = lo; i <= hi; i++) mac96(A[i], B[col - i], c0, c1, c2);
-        // r += c (96-bit)
         asm("add.cc.u32 %0, %0, %3;\n\t"
             "addc.cc.u32 %1, %1, %4;\n\t"
             "addc.u32 %2, %2, %5;\n\t"
             : "+r"(r0), "+r"(r1), "+r"(r2)
-            : "r"(c0), "r"(c1), "r"(c2));
+            : "r"(c0[w]), "r"(c1[w]), "r"(c2[w]));
         limb[w] = r0;
         r0 = r1;
         r1 = r2;

@@ -203,15 +203,46 @@ __device__ uint32_t block_map_scan(uint32_t f, uint32_t *wsm, uint32_t *total)
 
 constexpr int kLimbsPerThread = 8;
 
-// Limb sums and carries for one tile.  cw0/cw1/cw2 hold the three words of
-// the coefficients j = -2 .. tile_len-1 of the tile at index j + 2 (the two
-// halo coefficients precede the tile; they are zero at the product's start).
-// Limb j of the tile is cw0[j] + cw1[j-1] + cw2[j-2] plus carries.  Writes
-// limbs j < out_count to out; returns the tile's carry map in *tile_map
-// (valid in every thread).  The tile's own carry-in is assumed 0.
-__device__ void tile_carry(const uint32_t *cw0, const uint32_t *cw1, const uint32_t *cw2,
-                           int tile_len, uint32_t *out, long out_count, uint32_t *wsm,
-                           uint32_t *tile_map)
+// Coefficient words of a thread's run of kLimbsPerThread consecutive
+// coefficients j0 + i (c0 the low word, c1 the middle, c2 the high).  Limb j
+// sums c0[j] + c1[j-1] + c2[j-2], so the first two limbs of a run also need
+// c1[j0-1], c2[j0-2] and c2[j0-1] of the preceding run.
+struct CoefRun {
+    uint32_t c0[kLimbsPerThread], c1[kLimbsPerThread], c2[kLimbsPerThread];
+};
+
+// Those three halo words from the preceding thread: by shuffle inside a warp,
+// through hsm (3 x 32 words) across warps; thread 0 takes first1/first2a/
+// first2b (the block's predecessor).  Every thread of the block calls this.
+__device__ __forceinline__ void run_halo(const CoefRun &r, uint32_t first1, uint32_t first2a,
+                                         uint32_t first2b, uint32_t *hsm, uint32_t &h1,
+                                         uint32_t &h2a, uint32_t &h2b)
+{
+    constexpr int L = kLimbsPerThread;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    h1 = __shfl_up_sync(0xffffffffu, r.c1[L - 1], 1);
+    h2a = __shfl_up_sync(0xffffffffu, r.c2[L - 2], 1);
+    h2b = __shfl_up_sync(0xffffffffu, r.c2[L - 1], 1);
+    if (lane == 31) {
+        hsm[wid] = r.c1[L - 1];
+        hsm[32 + wid] = r.c2[L - 2];
+        hsm[64 + wid] = r.c2[L - 1];
+    }
+    __syncthreads();
+    if (lane == 0) {
+        h1 = wid ? hsm[wid - 1] : first1;
+        h2a = wid ? hsm[32 + wid - 1] : first2a;
+        h2b = wid ? hsm[64 + wid - 1] : first2b;
+    }
+}
+
+// Limb sums and carries for one tile of coefficient runs, one run per thread
+// (run j0 = kLimbsPerThread * threadIdx.x; coefficients at or past tile_len
+// are zero).  Writes limbs j < min(tile_len, out_count) to out and returns the
+// tile's carry map in *tile_map (valid in every thread).  The tile's own
+// carry-in is assumed 0.
+__device__ void tile_carry(const CoefRun &r, uint32_t h1, uint32_t h2a, uint32_t h2b, int tile_len,
+                           uint32_t *out, long out_count, uint32_t *wsm, uint32_t *tile_map)
 {
     const int j0 = threadIdx.x * kLimbsPerThread;
     uint32_t limb[kLimbsPerThread];
@@ -220,12 +251,9 @@ __device__ void tile_carry(const uint32_t *cw0, const uint32_t *cw1, const uint3
     if (j0 < tile_len) {
 #pragma unroll
         for (int i = 0; i < kLimbsPerThread; i++) {
-            const int j = j0 + i;
-            uint64_t v = 0;
-            if (j < tile_len)
-                v = (uint64_t)cw0[j + 2] + cw1[j + 1] + cw2[j] + carry;
-            else
-                v = carry;
+            const uint32_t m1 = i >= 1 ? r.c1[i - 1] : h1;
+            const uint32_t m2 = i >= 2 ? r.c2[i - 2] : (i == 0 ? h2a : h2b);
+            const uint64_t v = (uint64_t)r.c0[i] + m1 + m2 + carry;
             limb[i] = (uint32_t)v;
             carry = (uint32_t)(v >> 32);
         }
@@ -269,28 +297,44 @@ struct CrtArgs {
     uint8_t *tile_maps; // [product][tiles]
 };
 
+// One tile of 2048 coefficients per block: each thread remainders its run of
+// eight (two 16-byte loads per prime: tiles, runs and the prime arrays are
+// multiples of 8 words apart) and sums them into limbs.
 template <int PS>
 __global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
 {
-    __shared__ uint32_t cw[3][kTile + 2];
     __shared__ uint32_t wsm[32];
+    __shared__ uint32_t hsm[96];
     const size_t tiles = ((size_t)1 << a.n) / kTile;
     const size_t k = blockIdx.x / tiles;
     const size_t t = blockIdx.x % tiles;
-    const long j0 = (long)(t * kTile);
-    const uint32_t *g0 = a.G + (k << a.n);
-    for (int i = threadIdx.x; i < kTile + 2; i += blockDim.x) {
-        const long j = j0 + i - 2;
-        uint32_t c0 = 0, c1 = 0, c2 = 0;
-        if (j >= 0) crt3<PS>(g0[j], g0[a.gpstride + j], g0[2 * a.gpstride + j], c0, c1, c2);
-        cw[0][i] = c0;
-        cw[1][i] = c1;
-        cw[2][i] = c2;
+    const size_t jt = t * kTile;
+    const uint32_t *g0 = a.G + (k << a.n) + jt;
+    const int j0 = threadIdx.x * kLimbsPerThread;
+    uint32_t r[3][kLimbsPerThread];
+#pragma unroll
+    for (int p = 0; p < 3; p++) {
+        const uint4 *v = reinterpret_cast<const uint4 *>(g0 + p * a.gpstride + j0);
+        const uint4 x = v[0], y = v[1];
+        r[p][0] = x.x; r[p][1] = x.y; r[p][2] = x.z; r[p][3] = x.w;
+        r[p][4] = y.x; r[p][5] = y.y; r[p][6] = y.z; r[p][7] = y.w;
     }
-    __syncthreads();
-    const long remaining = (long)a.out_len - j0;
+    CoefRun run;
+#pragma unroll
+    for (int i = 0; i < kLimbsPerThread; i++)
+        crt3<PS>(r[0][i], r[1][i], r[2][i], run.c0[i], run.c1[i], run.c2[i]);
+    // the tile's predecessor: coefficients jt - 2 and jt - 1 (none for tile 0)
+    uint32_t f1 = 0, f2a = 0, f2b = 0;
+    if (threadIdx.x == 0 && t > 0) {
+        uint32_t d0, d1, e0, e1;
+        crt3<PS>(g0[-2], g0[a.gpstride - 2], g0[2 * a.gpstride - 2], d0, d1, f2a);
+        crt3<PS>(g0[-1], g0[a.gpstride - 1], g0[2 * a.gpstride - 1], e0, f1, f2b);
+    }
+    uint32_t h1, h2a, h2b;
+    run_halo(run, f1, f2a, f2b, hsm, h1, h2a, h2b);
+    const long remaining = (long)a.out_len - (long)jt;
     uint32_t map;
-    tile_carry(cw[0], cw[1], cw[2], kTile, a.out + k * a.out_tstride + j0, remaining, wsm, &map);
+    tile_carry(run, h1, h2a, h2b, kTile, a.out + k * a.out_tstride + jt, remaining, wsm, &map);
     if (threadIdx.x == 0) a.tile_maps[blockIdx.x] = (uint8_t)map;
 }
 
@@ -353,8 +397,8 @@ constexpr int kFusedThreads = 512;
 // prime) in shared memory, then remaindering and carries over one tile.
 // Layout (words): residues R0 [0,L) R1 [L,2L) R2 [2L,3L); raw A shares R2's
 // space (it is last read before R2 is written), raw B [3L,4L), transform pair
-// XY [4L,6L).  After the three rounds the remaindered words (3 (L+2)) go to
-// [3L, 6L+6).
+// XY [4L,6L).  Every thread owns a run of eight coefficients for the carries
+// (L <= 8 x threads).
 template <int LR>
 __global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
 {
@@ -392,20 +436,23 @@ __global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
         __syncthreads();
         dit_smem<LR, 1, 0>(Z, Ti, q);
     }
-    uint32_t *cw0 = sm + 3 * L, *cw1 = cw0 + (L + 2), *cw2 = cw1 + (L + 2);
-    for (int i = threadIdx.x; i < L + 2; i += blockDim.x) {
-        uint32_t c0 = 0, c1 = 0, c2 = 0;
-        if (i >= 2) {
-            const int j = swz(i - 2);
-            crt3<0>(Rr[0][j], Rr[1][j], Rr[2][j], c0, c1, c2);
+    // each thread remainders its run of eight coefficients straight from the
+    // swizzled residues (for a fixed i the lanes' words 8 t + i fall in
+    // distinct banks under swz)
+    __shared__ uint32_t hsm[96];
+    const int j0 = threadIdx.x * kLimbsPerThread;
+    CoefRun run;
+#pragma unroll
+    for (int i = 0; i < kLimbsPerThread; i++) {
+        run.c0[i] = run.c1[i] = run.c2[i] = 0;
+        if (j0 + i < L) {
+            const int j = swz(j0 + i);
+            crt3<0>(Rr[0][j], Rr[1][j], Rr[2][j], run.c0[i], run.c1[i], run.c2[i]);
         }
-        cw0[i] = c0;
-        cw1[i] = c1;
-        cw2[i] = c2;
     }
-    __syncthreads();
-    uint32_t map;
-    tile_carry(cw0, cw1, cw2, L, a.out + k * a.out_tstride, (long)a.out_len, wsm, &map);
+    uint32_t h1, h2a, h2b, map;
+    run_halo(run, 0u, 0u, 0u, hsm, h1, h2a, h2b);
+    tile_carry(run, h1, h2a, h2b, L, a.out + k * a.out_tstride, (long)a.out_len, wsm, &map);
 }
 
 // ------------------------------------------------------------ host side
@@ -434,10 +481,12 @@ static NttPlan make_plan(int n)
     return P;
 }
 
+// Raise the kernel's dynamic shared-memory limit when dynamic plus static
+// shared memory (a few hundred bytes here) could pass the default 48 KiB.
 template <typename K>
 static void set_smem(K kernel, size_t bytes)
 {
-    if (bytes > 48 * 1024)
+    if (bytes > 40 * 1024)
         CAT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)bytes));
 }
@@ -639,7 +688,7 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
 template <int LR>
 static void launch_fused(unsigned grid, cudaStream_t s, const FusedArgs &a)
 {
-    const size_t smem = (6 * ((size_t)1 << LR) + 8) * sizeof(uint32_t);
+    const size_t smem = 6 * ((size_t)1 << LR) * sizeof(uint32_t);
     set_smem(ntt_mul_fused<LR>, smem);
     const int threads = std::min(kFusedThreads, std::max(64, (1 << LR) / 8));
     ntt_mul_fused<LR><<<grid, threads, smem, s>>>(a);
