@@ -131,7 +131,9 @@ int cat_factor_copy_primes(cat_ctx *ctx, const cat_factorization *f, uint32_t *d
  * out = a * b.  a has na limbs, b has nb limbs (device).  out has room for
  * cap limbs; na + nb limbs always suffice.  *out_len = normalised length.
  * Errors: CAT_EINVAL, CAT_ERANGE (cap < normalised length), CAT_ENOMEM,
- * CAT_ECUDA.  Operands of up to 2^27 limbs each are supported. */
+ * CAT_ECUDA.  Products of up to 2^27 limbs take one three-prime transform;
+ * longer ones are summed from products of pieces of at most 2^26 limbs (any
+ * length that fits device memory). */
 int bigint_mul(cat_ctx *ctx, const uint32_t *a, size_t na, const uint32_t *b,
                size_t nb, uint32_t *out, size_t cap, size_t *out_len, void *stream);
 
@@ -224,6 +226,27 @@ int cat_batch_bound(const cat_request *reqs, size_t count, size_t *total);
  * needed), CAT_ENOMEM, CAT_ENOTINTEGRAL, CAT_ECUDA. */
 int cat_exact_batch(cat_ctx *ctx, const cat_request *reqs, size_t count, uint32_t *out,
                     size_t cap, uint64_t *offsets, uint64_t *lengths, void *stream);
+
+/* ----------------------------------------------------------- decimal output
+ * The optional decimal text output of the reconstructed number (Sec. 3.2;
+ * Table 1 of Sec. 5 states 1,234,567,890 digits for C(2,050,572,903)).
+ *
+ * cat_decimal_bound: an upper bound on the digit count of any number of n
+ * limbs (floor(32 n log10 2) + 2).
+ *
+ * to_decimal: the decimal digits of the little-endian uint32 number
+ * limbs[0..n) (device pointer; leading zero limbs allowed) as ASCII into the
+ * device buffer out of cap bytes: most significant digit first, no sign, no
+ * leading zeros, no terminator; "0" for zero.  *out_len = the digit count.
+ * Converted by a tree over the limbs in base 10^9 (batched three-prime
+ * products with the powers 2^(32 w), carries in base 10^9); scratch comes
+ * from the context's pool and is about 3x the input.  Returns when done.
+ * Errors: CAT_EINVAL (null pointer), CAT_ERANGE (cap too small; *out_len is
+ * the exact count, which cat_decimal_bound never undercuts), CAT_ENOMEM,
+ * CAT_ECUDA. */
+size_t cat_decimal_bound(size_t n);
+int to_decimal(cat_ctx *ctx, const uint32_t *limbs, size_t n, char *out, size_t cap,
+               size_t *out_len, void *stream);
 
 /* ------------------------------------------------------------------ serving
  * A continuous-batching request engine on one device (the paper has a single

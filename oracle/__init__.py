@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
         L.orc_is_prime.restype = ctypes.c_int
         L.orc_next_prime.argtypes = [u64]
         L.orc_next_prime.restype = u64
+        L.orc_to_decimal.argtypes = [u32p, u64, ctypes.c_char_p, u64]
+        L.orc_to_decimal.restype = u64
         _lib = L
     return _lib
 
@@ -311,6 +313,17 @@ def limbs_mod(limbs, q: int) -> int:
     """Limb array reduced mod q by Horner's rule from the top limb."""
     a = _limbs(limbs)
     return int(lib().orc_limbs_mod(_p32(a), len(a), q))
+
+
+def to_decimal(limbs) -> bytes:
+    """Decimal digits of a limb array (schoolbook division by 10^9)."""
+    a = _limbs(limbs)
+    cap = int(len(a) * 32 * 0.30103) + 2
+    buf = ctypes.create_string_buffer(max(cap, 1))
+    n = lib().orc_to_decimal(_p32(a), len(a), buf, cap)
+    if n == _U64_MAX:
+        raise ValueError("decimal buffer too small")
+    return buf.raw[:n]
 
 
 def mulmod_plain(a: int, b: int, q: int) -> int:

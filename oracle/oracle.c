@@ -705,3 +705,59 @@ uint64_t orc_next_prime(uint64_t x)
     while (!orc_is_prime(x)) x += 2;
     return x;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Decimal text of a result (Sec. 3.2: the optional decimal output; Table 1: */
+/* 1,234,567,890 digits at the paper's n).  The definition written out: the  */
+/* digits are the remainders of repeated division by ten, taken here nine at */
+/* a time (schoolbook long division of the limb array by 10^9, quadratic).   */
+/* Writes the digits most significant first, no sign, no terminator, "0" for */
+/* zero; returns the digit count, or UINT64_MAX when cap is too small.       */
+uint64_t orc_to_decimal(const limb_t *a, uint64_t n, char *out, uint64_t cap)
+{
+    n = norm_len(a, n);
+    if (n == 0) {
+        if (cap < 1) return UINT64_MAX;
+        out[0] = '0';
+        return 1;
+    }
+    limb_t *w = (limb_t *)malloc(n * sizeof(limb_t));
+    /* at most ceil(n * 32 / 29.89) + 1 chunks of nine digits */
+    uint64_t maxch = (n * 32) / 29 + 2;
+    uint32_t *ch = (uint32_t *)malloc(maxch * sizeof(uint32_t));
+    memcpy(w, a, n * sizeof(limb_t));
+    uint64_t len = n, nch = 0;
+    while (len > 0) {
+        uint64_t rem = 0; /* w = w / 10^9, rem = w mod 10^9 */
+        for (uint64_t i = len; i-- > 0;) {
+            uint64_t cur = (rem << 32) | w[i];
+            w[i] = (limb_t)(cur / 1000000000u);
+            rem = cur % 1000000000u;
+        }
+        ch[nch++] = (uint32_t)rem;
+        while (len > 0 && w[len - 1] == 0) len--;
+    }
+    /* the top chunk without leading zeros, every other chunk as nine digits */
+    char top[10];
+    int lead = 0;
+    for (uint32_t v = ch[nch - 1]; v; v /= 10) top[lead++] = (char)('0' + v % 10);
+    uint64_t total = (uint64_t)lead + 9 * (nch - 1);
+    if (total > cap) {
+        free(w);
+        free(ch);
+        return UINT64_MAX;
+    }
+    uint64_t pos = 0;
+    for (int i = lead - 1; i >= 0; i--) out[pos++] = top[i];
+    for (uint64_t c = nch - 1; c-- > 0;) {
+        uint32_t v = ch[c];
+        for (int d = 8; d >= 0; d--) {
+            out[pos + d] = (char)('0' + v % 10);
+            v /= 10;
+        }
+        pos += 9;
+    }
+    free(w);
+    free(ch);
+    return total;
+}

@@ -23,6 +23,8 @@ KINDS = {"catalan": CAT_CATALAN, "central_binomial": CAT_CENTRAL_BINOMIAL,
 
 STATUS = {0: "CAT_OK", -1: "CAT_EINVAL", -2: "CAT_ENOMEM", -3: "CAT_ERANGE",
           -4: "CAT_ENOTINTEGRAL", -5: "CAT_ETIMEOUT", -6: "CAT_ECUDA", -7: "CAT_EBUSY"}
+CAT_OK, CAT_EINVAL, CAT_ENOMEM, CAT_ERANGE = 0, -1, -2, -3
+CAT_ENOTINTEGRAL, CAT_ETIMEOUT, CAT_ECUDA, CAT_EBUSY = -4, -5, -6, -7
 
 EXPORTED = ["cat_ctx_create", "cat_ctx_destroy", "cat_last_error", "cat_ctx_memory",
             "cat_ctx_set_profiling", "cat_ctx_profile",
@@ -32,7 +34,7 @@ EXPORTED = ["cat_ctx_create", "cat_ctx_destroy", "cat_last_error", "cat_ctx_memo
             "catalan_exact", "cat_exact_host", "cat_batch_bound", "cat_exact_batch",
             "cat_server_create", "cat_server_submit", "cat_server_poll", "cat_server_wait",
             "cat_server_fetch", "cat_server_release", "cat_server_pending",
-            "cat_server_destroy"]
+            "cat_server_destroy", "cat_decimal_bound", "to_decimal"]
 
 
 class CatError(RuntimeError):
@@ -100,6 +102,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.bigint_mul.restype = i32
     L.bigint_mul_noalloc.argtypes = [vp, sz, vp, sz, vp, sz, szp, vp]
     L.bigint_mul_noalloc.restype = i32
+    L.cat_decimal_bound.argtypes = [sz]
+    L.cat_decimal_bound.restype = sz
+    L.to_decimal.argtypes = [vp, vp, sz, vp, sz, szp, vp]
+    L.to_decimal.restype = i32
     L.bigint_pow.argtypes = [vp, vp, sz, u64, vp, sz, szp, vp]
     L.bigint_pow.restype = i32
     L.product_tree.argtypes = [vp, vp, sz, vp, sz, szp, vp]
@@ -235,6 +241,27 @@ def bigint_mul(ctx: Context, a, b, stream=None):
     n = ctypes.c_size_t()
     ctx.check(load().bigint_mul(ctx.handle, _ptr(ta), ta.numel(), _ptr(tb), tb.numel(),
                                 _ptr(out), cap, ctypes.byref(n), _stream(stream)))
+    return out[:n.value]
+
+
+def cat_decimal_bound(n_limbs: int) -> int:
+    """Upper bound on the decimal digit count of an n-limb number."""
+    return load().cat_decimal_bound(n_limbs)
+
+
+def to_decimal(ctx: Context, limbs, out=None, stream=None):
+    """Decimal digits of a little-endian uint32 number (device tensor or numpy
+    array) through to_decimal: a uint8 device tensor of ASCII digits, most
+    significant first ("0" for zero).  `out` may be a preallocated uint8
+    device tensor of at least cat_decimal_bound(len(limbs)) bytes."""
+    import torch
+    dev = f"cuda:{ctx.device}"
+    t = _limbs_tensor(limbs, dev)
+    if out is None:
+        out = torch.empty(max(cat_decimal_bound(t.numel()), 1), dtype=torch.uint8, device=dev)
+    n = ctypes.c_size_t()
+    ctx.check(load().to_decimal(ctx.handle, _ptr(t), t.numel(), _ptr(out), out.numel(),
+                                ctypes.byref(n), _stream(stream)))
     return out[:n.value]
 
 

@@ -276,4 +276,17 @@ int cat_exact_host(cat_ctx *ctx, int kind, uint64_t n, uint32_t *host_out, size_
     });
 }
 
+size_t cat_decimal_bound(size_t n) { return cat::decimal_bound(n); }
+
+int to_decimal(cat_ctx *ctx, const uint32_t *limbs, size_t n, char *out, size_t cap,
+               size_t *out_len, void *stream)
+{
+    if (!ctx || !out_len || (n && !limbs) || (cap && !out)) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        const int rc =
+            cat::to_decimal_dev(ctx->c, limbs, n, out, cap, out_len, as_stream(stream));
+        if (rc == CAT_ERANGE) cat::fail(CAT_ERANGE, "output capacity too small");
+    });
+}
+
 }  // extern "C"

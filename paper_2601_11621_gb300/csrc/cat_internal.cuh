@@ -364,6 +364,7 @@ struct Ctx {
     uint2 *twiddles = nullptr;  // [set][prime][dir][kTwPerDir] multiplier pairs
     int num_sms = 0;
     size_t comba_max_slot = 128;  // tree levels with slots up to this use schoolbook
+    int max_log = kLogMaxNtt;     // longest single transform; longer products go by pieces
     bool profiling = false;
     std::vector<ProfEntry> prof;
     std::vector<ProfPending> pending;
@@ -376,6 +377,25 @@ struct Ctx {
 int prof_begin(Ctx &c, const char *name, cudaStream_t s);
 void prof_end(Ctx &c, int token, cudaStream_t s, double bytes, double ops = 0);
 void prof_resolve(Ctx &c);
+
+// Where the limbs of a batch of products go: product k at out + k *
+// out_tstride, out_len limbs, in base 2^32 or (dec) in base 10^9; with `add`,
+// the limbs add + k * add_tstride (add_len of them, zero beyond) are added in
+// before the carries (the sum must fit out_len limbs).
+struct Sink {
+    uint32_t *out;
+    size_t out_tstride, out_len;
+    bool dec;
+    const uint32_t *add;
+    size_t add_tstride, add_len;
+};
+
+constexpr uint32_t kDecBase = 1000000000u;
+
+inline Sink plain_sink(uint32_t *out, size_t out_tstride, size_t out_len)
+{
+    return Sink{out, out_tstride, out_len, false, nullptr, 0, 0};
+}
 
 // Fills h[kTwTotal] with the twiddle tables of all sets (host side).
 constexpr size_t kTwTotal = (size_t)kNumSets * kNumPrimes * 2 * kTwPerDir;
@@ -466,6 +486,22 @@ void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> 
 // out[0 .. na+nb) = a * b (exact, zero-padded).  out must hold na + nb limbs.
 void mul_into(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
               uint32_t *out, cudaStream_t s);
+// nprod products x_k y (x_k at x + k xstride, xlen limbs; one y of ylen
+// limbs, transformed once) into `sink`; xlen + ylen <= 2^27.
+void mul_broadcast(Ctx &c, const uint32_t *x, size_t xstride, size_t xlen, size_t nprod,
+                   const uint32_t *y, size_t ylen, const Sink &sink, cudaStream_t s);
+// acc[0 .. R) += t[0 .. tn), base 2^32 or (dec) 10^9, carries through acc.
+void add_into(Ctx &c, uint32_t *acc, size_t R, const uint32_t *t, size_t tn, bool dec,
+              cudaStream_t s);
+// acc[0 .. R) += x y for any lengths (pieces of <= 2^26 limbs when long).
+void mul_acc(Ctx &c, const uint32_t *x, size_t xlen, const uint32_t *y, size_t ylen,
+             uint32_t *acc, size_t R, bool dec, cudaStream_t s);
+// Decimal digits of x[0..n) into out (device, no sign, no terminator, "0"
+// for zero); returns the digit count.  Fails with CAT_ERANGE (and the count
+// in *needed) when cap is too small.
+size_t decimal_bound(size_t n);
+int to_decimal_dev(Ctx &c, const uint32_t *x, size_t n, char *out, size_t cap, size_t *needed,
+                   cudaStream_t s);
 // Normalised length of x[0..n) (reads the device array).
 size_t normalized_length(Ctx &c, const uint32_t *x, size_t n, cudaStream_t s);
 // Product of count 32-bit values (balanced tree).  Returns the result.

@@ -226,6 +226,12 @@ void ctx_init(Ctx &c, int device, size_t budget)
     c.budget = budget;
     CAT_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device));
     if (const char *e = getenv("CAT_COMBA_MAX_SLOT")) c.comba_max_slot = strtoull(e, nullptr, 10);
+    // a lower single-transform limit sends shorter products through the piece
+    // path (used to exercise it at small sizes)
+    if (const char *e = getenv("CAT_MAX_TRANSFORM_LOG")) {
+        const long v = strtol(e, nullptr, 10);
+        if (v >= 13 && v <= kLogMaxNtt) c.max_log = (int)v;
+    }
     pool_for(device);
     build_twiddles(c);
 }

@@ -236,15 +236,38 @@ __device__ __forceinline__ void run_halo(const CoefRun &r, uint32_t first1, uint
     }
 }
 
+// The exact coefficient c = w2 2^64 + w1 2^32 + w0 < 10^26 as three base-10^9
+// digits (c < min(na, nb) (10^9 - 1)^2 < 2^26 10^18 for digit operands and
+// transforms of at most 2^27 points, so the top digit is below 10^8).
+__device__ __forceinline__ void words_to_dec(uint32_t &w0, uint32_t &w1, uint32_t &w2)
+{
+    const uint64_t hi = ((uint64_t)w2 << 32) | w1;
+    const uint64_t qh = hi / kDecBase;
+    const uint32_t rh = (uint32_t)(hi - qh * kDecBase);
+    const uint64_t lo = ((uint64_t)rh << 32) | w0;
+    const uint64_t ql = lo / kDecBase;
+    const uint64_t q = (qh << 32) + ql;  // floor(c / 10^9) < 10^17
+    const uint64_t q2 = q / kDecBase;
+    w0 = (uint32_t)(lo - ql * kDecBase);
+    w1 = (uint32_t)(q - q2 * kDecBase);
+    w2 = (uint32_t)q2;
+}
+
 // Limb sums and carries for one tile of coefficient runs, one run per thread
 // (run j0 = kLimbsPerThread * threadIdx.x; coefficients at or past tile_len
-// are zero).  Writes limbs j < min(tile_len, out_count) to out and returns the
-// tile's carry map in *tile_map (valid in every thread).  The tile's own
+// are zero), in base 2^32 or (dec) 10^9, plus the addend limbs add[j] for
+// j < add_count.  In both bases a limb sums two full words, the coefficient's
+// top word or digit (below 2^26 or 10^8: coefficients stay below 2^90, or
+// 10^26 for digit operands), the addend and a carry <= 3, so carries stay in
+// {0, 1, 2, 3}.  Writes limbs j < min(tile_len, out_count) to out and returns
+// the tile's carry map in *tile_map (valid in every thread).  The tile's own
 // carry-in is assumed 0.
 __device__ void tile_carry(const CoefRun &r, uint32_t h1, uint32_t h2a, uint32_t h2b, int tile_len,
-                           uint32_t *out, long out_count, uint32_t *wsm, uint32_t *tile_map)
+                           uint32_t *out, long out_count, bool dec, const uint32_t *add,
+                           long add_count, uint32_t *wsm, uint32_t *tile_map)
 {
     const int j0 = threadIdx.x * kLimbsPerThread;
+    const uint32_t top = dec ? kDecBase - 1 : 0xffffffffu;  // largest limb
     uint32_t limb[kLimbsPerThread];
     uint32_t carry = 0;
     uint32_t f = kMapId;
@@ -253,17 +276,24 @@ __device__ void tile_carry(const CoefRun &r, uint32_t h1, uint32_t h2a, uint32_t
         for (int i = 0; i < kLimbsPerThread; i++) {
             const uint32_t m1 = i >= 1 ? r.c1[i - 1] : h1;
             const uint32_t m2 = i >= 2 ? r.c2[i - 2] : (i == 0 ? h2a : h2b);
-            const uint64_t v = (uint64_t)r.c0[i] + m1 + m2 + carry;
-            limb[i] = (uint32_t)v;
-            carry = (uint32_t)(v >> 32);
+            const uint32_t ad = (add && j0 + i < add_count) ? add[j0 + i] : 0u;
+            const uint64_t v = (uint64_t)r.c0[i] + m1 + m2 + ad + carry;
+            if (dec) {
+                const uint32_t v32 = (uint32_t)v;  // < 3.1 10^9 + 3 < 2^32
+                carry = (v32 >= kDecBase) + (v32 >= 2 * kDecBase) + (v32 >= 3 * kDecBase);
+                limb[i] = v32 - carry * kDecBase;
+            } else {
+                limb[i] = (uint32_t)v;
+                carry = (uint32_t)(v >> 32);
+            }
         }
         bool ones = true;
 #pragma unroll
-        for (int i = 1; i < kLimbsPerThread; i++) ones = ones && limb[i] == 0xffffffffu;
+        for (int i = 1; i < kLimbsPerThread; i++) ones = ones && limb[i] == top;
         f = 0;
 #pragma unroll
         for (uint32_t c = 0; c < 4; c++) {
-            const uint32_t o = carry + ((c > 0 && ones && limb[0] >= 0u - c) ? 1u : 0u);
+            const uint32_t o = carry + ((c > 0 && ones && limb[0] >= top + 1 - c) ? 1u : 0u);
             f |= o << (2 * c);
         }
     }
@@ -275,8 +305,8 @@ __device__ void tile_carry(const CoefRun &r, uint32_t h1, uint32_t h2a, uint32_t
 #pragma unroll
         for (int i = 0; i < kLimbsPerThread; i++) {
             const uint64_t v = (uint64_t)limb[i] + c;
-            limb[i] = (uint32_t)v;
-            c = (uint32_t)(v >> 32);
+            c = dec ? (uint32_t)(v >= kDecBase) : (uint32_t)(v >> 32);
+            limb[i] = dec ? (uint32_t)(v - (uint64_t)c * kDecBase) : (uint32_t)v;
         }
 #pragma unroll
         for (int i = 0; i < kLimbsPerThread; i++)
@@ -291,9 +321,7 @@ struct CrtArgs {
     const uint32_t *G;  // inverse-transformed residues [prime][product][L]
     size_t gpstride;
     int n;              // log2 L
-    uint32_t *out;      // product k at out + k * out_tstride
-    size_t out_tstride;
-    size_t out_len;     // limbs written per product (<= L)
+    Sink sink;          // product k's limbs (out_len <= L)
     uint8_t *tile_maps; // [product][tiles]
 };
 
@@ -311,6 +339,7 @@ __global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
     const size_t jt = t * kTile;
     const uint32_t *g0 = a.G + (k << a.n) + jt;
     const int j0 = threadIdx.x * kLimbsPerThread;
+    const bool dec = a.sink.dec;
     uint32_t r[3][kLimbsPerThread];
 #pragma unroll
     for (int p = 0; p < 3; p++) {
@@ -321,20 +350,27 @@ __global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
     }
     CoefRun run;
 #pragma unroll
-    for (int i = 0; i < kLimbsPerThread; i++)
+    for (int i = 0; i < kLimbsPerThread; i++) {
         crt3<PS>(r[0][i], r[1][i], r[2][i], run.c0[i], run.c1[i], run.c2[i]);
+        if (dec) words_to_dec(run.c0[i], run.c1[i], run.c2[i]);
+    }
     // the tile's predecessor: coefficients jt - 2 and jt - 1 (none for tile 0)
     uint32_t f1 = 0, f2a = 0, f2b = 0;
     if (threadIdx.x == 0 && t > 0) {
-        uint32_t d0, d1, e0, e1;
+        uint32_t d0, d1, e0;
         crt3<PS>(g0[-2], g0[a.gpstride - 2], g0[2 * a.gpstride - 2], d0, d1, f2a);
+        if (dec) words_to_dec(d0, d1, f2a);
         crt3<PS>(g0[-1], g0[a.gpstride - 1], g0[2 * a.gpstride - 1], e0, f1, f2b);
+        if (dec) words_to_dec(e0, f1, f2b);
     }
     uint32_t h1, h2a, h2b;
     run_halo(run, f1, f2a, f2b, hsm, h1, h2a, h2b);
-    const long remaining = (long)a.out_len - (long)jt;
+    const Sink &o = a.sink;
+    const long remaining = (long)o.out_len - (long)jt;
+    const uint32_t *add = o.add ? o.add + k * o.add_tstride + jt : nullptr;
     uint32_t map;
-    tile_carry(run, h1, h2a, h2b, kTile, a.out + k * a.out_tstride + jt, remaining, wsm, &map);
+    tile_carry(run, h1, h2a, h2b, kTile, o.out + k * o.out_tstride + jt, remaining, dec, add,
+               (long)o.add_len - (long)jt, wsm, &map);
     if (threadIdx.x == 0) a.tile_maps[blockIdx.x] = (uint8_t)map;
 }
 
@@ -356,9 +392,10 @@ __global__ void __launch_bounds__(1024) carry_tile_scan(uint8_t *tile_maps, size
     }
 }
 
-// Add each tile's carry-in to its first limbs (rarely more than one).
+// Add each tile's carry-in to its first limbs (rarely more than one), in
+// base 2^32 or (dec) 10^9.
 __global__ void carry_fix(const uint8_t *tile_cin, size_t tiles_total, size_t tiles, int n,
-                          uint32_t *out, size_t out_tstride, size_t out_len)
+                          uint32_t *out, size_t out_tstride, size_t out_len, bool dec)
 {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= tiles_total) return;
@@ -370,8 +407,13 @@ __global__ void carry_fix(const uint8_t *tile_cin, size_t tiles_total, size_t ti
     const size_t end = std::min(j + kTile, out_len);
     for (; c && j < end; j++) {
         const uint64_t v = (uint64_t)o[j] + c;
-        o[j] = (uint32_t)v;
-        c = (uint32_t)(v >> 32);
+        if (dec) {
+            c = v >= kDecBase ? 1u : 0u;
+            o[j] = (uint32_t)(v - (uint64_t)c * kDecBase);
+        } else {
+            o[j] = (uint32_t)v;
+            c = (uint32_t)(v >> 32);
+        }
     }
 }
 
@@ -382,10 +424,9 @@ __global__ void carry_fix(const uint8_t *tile_cin, size_t tiles_total, size_t ti
 struct FusedArgs {
     const uint32_t *A;
     size_t a_tstride, a_len;
-    const uint32_t *B;  // null: square A
+    const uint32_t *B;  // null: square A; b_tstride 0: the same B for every product
     size_t b_tstride, b_len;
-    uint32_t *out;
-    size_t out_tstride, out_len;
+    Sink sink;
     const uint2 *tw;
     Scale scale;
 };
@@ -450,9 +491,14 @@ __global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
             crt3<0>(Rr[0][j], Rr[1][j], Rr[2][j], run.c0[i], run.c1[i], run.c2[i]);
         }
     }
+    const Sink &o = a.sink;
+    if (o.dec)
+#pragma unroll
+        for (int i = 0; i < kLimbsPerThread; i++) words_to_dec(run.c0[i], run.c1[i], run.c2[i]);
     uint32_t h1, h2a, h2b, map;
     run_halo(run, 0u, 0u, 0u, hsm, h1, h2a, h2b);
-    tile_carry(run, h1, h2a, h2b, L, a.out + k * a.out_tstride, (long)a.out_len, wsm, &map);
+    tile_carry(run, h1, h2a, h2b, L, o.out + k * o.out_tstride, (long)o.out_len, o.dec,
+               o.add ? o.add + k * o.add_tstride : nullptr, (long)o.add_len, wsm, &map);
 }
 
 // ------------------------------------------------------------ host side
@@ -603,24 +649,31 @@ struct Operand {
 };
 
 // Batched products through the multi-pass transform, L = 2^n > 2^12.
-//  mode PAIR_ADJACENT: nprod products of transforms (2k, 2k+1) of `x`
-//                      (2 nprod transforms, tstride apart);
+//  mode PAIR_ADJACENT:  nprod products of transforms (2k, 2k+1) of `x`
+//                       (2 nprod transforms, tstride apart);
 //  mode PAIR_FIRST_TWO: one product of x and y;
-//  mode PAIR_SQUARE:   nprod squares of x's transforms.
+//  mode PAIR_SQUARE:    nprod squares of x's transforms;
+//  mode PAIR_BROADCAST: nprod products of x's transforms (tstride apart) with
+//                       one y, whose transform is computed once.
 static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, Operand y,
-                              uint32_t *out, size_t out_tstride, size_t out_len,
-                              cudaStream_t s)
+                              const Sink &sink, cudaStream_t s)
 {
     const NttPlan P = make_plan(n);
     const int PS = set_for(n);
     const size_t L = (size_t)1 << n;
-    const size_t ntf = mode == PAIR_ADJACENT ? 2 * nprod : (mode == PAIR_SQUARE ? nprod : 2);
+    const size_t ntf = mode == PAIR_ADJACENT ? 2 * nprod
+                       : mode == PAIR_SQUARE ? nprod
+                       : mode == PAIR_BROADCAST ? nprod + 1
+                                                : 2;
     const size_t fp = ntf * L;
     DevBuf<uint32_t> F(c, fp * kNumPrimes, s);
     // forward column passes
     if (mode == PAIR_FIRST_TWO) {
         col_pass(c, PS, true, F.get(), fp, L, n, P.rcol[0], x.p, 0, x.len, s);
         col_pass(c, PS, true, F.get() + L, fp, L, n, P.rcol[0], y.p, 0, y.len, s);
+    } else if (mode == PAIR_BROADCAST) {
+        col_pass(c, PS, true, F.get(), fp, nprod * L, n, P.rcol[0], x.p, x.tstride, x.len, s);
+        col_pass(c, PS, true, F.get() + nprod * L, fp, L, n, P.rcol[0], y.p, 0, y.len, s);
     } else {
         col_pass(c, PS, true, F.get(), fp, fp, n, P.rcol[0], x.p, x.tstride, x.len, s);
     }
@@ -659,9 +712,7 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     ca.G = G.get();
     ca.gpstride = gp;
     ca.n = n;
-    ca.out = out;
-    ca.out_tstride = out_tstride;
-    ca.out_len = out_len;
+    ca.sink = sink;
     ca.tile_maps = maps.get();
     tok = prof_begin(c, "crt_carry_tiles", s);
     if (PS == 0)
@@ -671,7 +722,7 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     else
         crt_carry_tiles<2><<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
     CAT_LAUNCH("crt_carry_tiles");
-    prof_end(c, tok, s, 12.0 * (double)gp + 4.0 * (double)nprod * (double)out_len,
+    prof_end(c, tok, s, 12.0 * (double)gp + 4.0 * (double)nprod * (double)sink.out_len,
              40.0 * (double)gp);
     tok = prof_begin(c, "carry_tile_scan", s);
     carry_tile_scan<<<(unsigned)nprod, 1024, 0, s>>>(maps.get(), tiles);
@@ -679,8 +730,9 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     prof_end(c, tok, s, 2.0 * (double)(nprod * tiles));
     const size_t tt = nprod * tiles;
     tok = prof_begin(c, "carry_fix", s);
-    carry_fix<<<(unsigned)((tt + 255) / 256), 256, 0, s>>>(maps.get(), tt, tiles, n, out,
-                                                             out_tstride, out_len);
+    carry_fix<<<(unsigned)((tt + 255) / 256), 256, 0, s>>>(maps.get(), tt, tiles, n, sink.out,
+                                                             sink.out_tstride, sink.out_len,
+                                                             sink.dec);
     CAT_LAUNCH("carry_fix");
     prof_end(c, tok, s, (double)tt);
 }
@@ -695,7 +747,7 @@ static void launch_fused(unsigned grid, cudaStream_t s, const FusedArgs &a)
 }
 
 static void ntt_mul_small(Ctx &c, int n, size_t nprod, Operand x, Operand y, bool square,
-                          uint32_t *out, size_t out_tstride, size_t out_len, cudaStream_t s)
+                          const Sink &sink, cudaStream_t s)
 {
     FusedArgs a;
     a.A = x.p;
@@ -704,9 +756,7 @@ static void ntt_mul_small(Ctx &c, int n, size_t nprod, Operand x, Operand y, boo
     a.B = square ? nullptr : y.p;
     a.b_tstride = y.tstride;
     a.b_len = y.len;
-    a.out = out;
-    a.out_tstride = out_tstride;
-    a.out_len = out_len;
+    a.sink = sink;
     a.tw = c.twiddles;
     a.scale = make_scale(0, n);
     const unsigned grid = (unsigned)nprod;
@@ -728,7 +778,8 @@ static void ntt_mul_small(Ctx &c, int n, size_t nprod, Operand x, Operand y, boo
     }
     CAT_LAUNCH("ntt_mul_fused");
     const double Lf = (double)(1u << n);
-    prof_end(c, tok, s, 4.0 * (double)nprod * (double)(x.len + (square ? 0 : y.len) + out_len),
+    prof_end(c, tok, s,
+             4.0 * (double)nprod * (double)(x.len + (square ? 0 : y.len) + sink.out_len),
              (double)nprod * ((square ? 36.0 : 54.0) * Lf * n + 36.0 * Lf + 40.0 * Lf));
 }
 
@@ -746,11 +797,20 @@ void ntt_level(Ctx &c, const uint32_t *level, size_t slot, size_t nprod, uint32_
 {
     const int n = ceil_log2(2 * slot);
     Operand x{level, slot, slot};
+    if (n > c.max_log) {  // longer than one transform: each pair by pieces
+        for (size_t k = 0; k < nprod; k++) {
+            uint32_t *o = out + 2 * k * slot;
+            CAT_CUDA(cudaMemsetAsync(o, 0, 8 * slot, s));
+            mul_acc(c, level + 2 * k * slot, slot, level + (2 * k + 1) * slot, slot, o, 2 * slot,
+                    false, s);
+        }
+        return;
+    }
     if (n <= kFusedMaxLog) {
         Operand a{level, 2 * slot, slot}, b{level + slot, 2 * slot, slot};
-        ntt_mul_small(c, n, nprod, a, b, false, out, 2 * slot, 2 * slot, s);
+        ntt_mul_small(c, n, nprod, a, b, false, plain_sink(out, 2 * slot, 2 * slot), s);
     } else {
-        ntt_mul_multipass(c, n, PAIR_ADJACENT, nprod, x, x, out, 2 * slot, 2 * slot, s);
+        ntt_mul_multipass(c, n, PAIR_ADJACENT, nprod, x, x, plain_sink(out, 2 * slot, 2 * slot), s);
     }
 }
 
@@ -764,12 +824,90 @@ void ntt_mul(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
     const bool square = (a == b && na == nb);
     Operand x{a, 0, na}, y{b, 0, nb};
     if (n <= kFusedMaxLog) {
-        ntt_mul_small(c, n, 1, x, y, square, out, 0, len, s);
+        ntt_mul_small(c, n, 1, x, y, square, plain_sink(out, 0, len), s);
     } else if (square) {
-        ntt_mul_multipass(c, n, PAIR_SQUARE, 1, x, x, out, 0, len, s);
+        ntt_mul_multipass(c, n, PAIR_SQUARE, 1, x, x, plain_sink(out, 0, len), s);
     } else {
-        ntt_mul_multipass(c, n, PAIR_FIRST_TWO, 1, x, y, out, 0, len, s);
+        ntt_mul_multipass(c, n, PAIR_FIRST_TWO, 1, x, y, plain_sink(out, 0, len), s);
     }
+}
+
+// nprod products x_k y, x_k at x + k xstride (xlen limbs each), one y (ylen
+// limbs), into `sink`; xlen + ylen <= 2^27.  y is transformed once.
+void mul_broadcast(Ctx &c, const uint32_t *x, size_t xstride, size_t xlen, size_t nprod,
+                   const uint32_t *y, size_t ylen, const Sink &sink, cudaStream_t s)
+{
+    if (nprod == 0) return;
+    const int n = std::max(1, ceil_log2(xlen + ylen));
+    if (n > kLogMaxNtt) fail(CAT_EINVAL, "operands too long for one transform");
+    Operand ox{x, xstride, xlen}, oy{y, 0, ylen};
+    if (n <= kFusedMaxLog)
+        ntt_mul_small(c, n, nprod, ox, oy, false, sink, s);
+    else
+        ntt_mul_multipass(c, n, PAIR_BROADCAST, nprod, ox, oy, sink, s);
+}
+
+// ------------------------------------------------ long products by pieces
+
+// acc[j] += t[j] (t zero past tn) over one tile of 2048 limbs, carries within
+// the tile; the tile's carry map goes to tile_maps.
+__global__ void __launch_bounds__(kTileThreads) add_tiles(uint32_t *acc, size_t R,
+                                                          const uint32_t *t, size_t tn, bool dec,
+                                                          uint8_t *tile_maps)
+{
+    __shared__ uint32_t wsm[32];
+    const size_t jt = (size_t)blockIdx.x * kTile;
+    const int j0 = threadIdx.x * kLimbsPerThread;
+    CoefRun run;
+#pragma unroll
+    for (int i = 0; i < kLimbsPerThread; i++) {
+        const size_t j = jt + j0 + i;
+        run.c0[i] = j < tn ? t[j] : 0u;
+        run.c1[i] = run.c2[i] = 0u;
+    }
+    const int tile_len = (int)(R - jt < (size_t)kTile ? R - jt : (size_t)kTile);
+    uint32_t map;
+    tile_carry(run, 0u, 0u, 0u, tile_len, acc + jt, tile_len, dec, acc + jt, tile_len, wsm, &map);
+    if (threadIdx.x == 0) tile_maps[blockIdx.x] = (uint8_t)map;
+}
+
+// acc[0 .. R) += t[0 .. tn) in base 2^32 or (dec) 10^9, the carries carried
+// through all of acc (the sum must fit R limbs; limbs of t past R are zero).
+void add_into(Ctx &c, uint32_t *acc, size_t R, const uint32_t *t, size_t tn, bool dec,
+              cudaStream_t s)
+{
+    if (R == 0 || tn == 0) return;
+    const size_t tiles = (R + kTile - 1) / kTile;
+    if (tiles > 0x7fffffffu) fail(CAT_EINVAL, "addition too long");
+    DevBuf<uint8_t> maps(c, tiles, s);
+    const int tok = prof_begin(c, "add_tiles", s);
+    add_tiles<<<(unsigned)tiles, kTileThreads, 0, s>>>(acc, R, t, tn, dec, maps.get());
+    CAT_LAUNCH("add_tiles");
+    carry_tile_scan<<<1, 1024, 0, s>>>(maps.get(), tiles);
+    CAT_LAUNCH("carry_tile_scan");
+    carry_fix<<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(maps.get(), tiles, tiles, 0, acc, 0,
+                                                              R, dec);
+    CAT_LAUNCH("carry_fix");
+    prof_end(c, tok, s, 8.0 * (double)R + 4.0 * (double)tn);
+}
+
+// acc[0 .. R) += x y for operands of any length: pieces of at most 2^26
+// limbs (2^(max_log - 1)), so that every piece product fits one transform of
+// at most 2^27 points, each added in at its offset (the sum must fit R limbs).
+void mul_acc(Ctx &c, const uint32_t *x, size_t xlen, const uint32_t *y, size_t ylen,
+             uint32_t *acc, size_t R, bool dec, cudaStream_t s)
+{
+    if (xlen == 0 || ylen == 0) return;
+    const size_t M = (size_t)1 << (c.max_log - 1);
+    for (size_t i = 0; i < xlen; i += M)
+        for (size_t j = 0; j < ylen; j += M) {
+            if (i + j >= R) continue;
+            const size_t lx = std::min(M, xlen - i), ly = std::min(M, ylen - j);
+            DevBuf<uint32_t> t(c, lx + ly, s);
+            mul_broadcast(c, x + i, 0, lx, 1, y + j, ly,
+                          Sink{t.get(), 0, lx + ly, dec, nullptr, 0, 0}, s);
+            add_into(c, acc + i + j, R - (i + j), t.get(), lx + ly, dec, s);
+        }
 }
 
 // --------------------------------------- multiplication without allocation
@@ -853,7 +991,7 @@ static void noalloc_mul(const NoAllocDevice &d, const uint32_t *a, size_t na, co
     const int n = std::max(1, ceil_log2(len));
     Operand x{a, 0, na}, y{b, 0, nb};
     if (n <= kFusedMaxLog) {
-        ntt_mul_small(local, n, 1, x, y, false, out, 0, len, s);
+        ntt_mul_small(local, n, 1, x, y, false, plain_sink(out, 0, len), s);
         return;
     }
     const NttPlan P = make_plan(n);
@@ -889,15 +1027,14 @@ static void noalloc_mul(const NoAllocDevice &d, const uint32_t *a, size_t na, co
     ca.G = G;
     ca.gpstride = gp;
     ca.n = n;
-    ca.out = out;
-    ca.out_tstride = 0;
-    ca.out_len = len;
+    ca.sink = plain_sink(out, 0, len);
     ca.tile_maps = maps;
     crt_carry_tiles<0><<<(unsigned)tiles, kTileThreads, 0, s>>>(ca);
     CAT_LAUNCH("crt_carry_tiles");
     carry_tile_scan<<<1, 1024, 0, s>>>(maps, tiles);
     CAT_LAUNCH("carry_tile_scan");
-    carry_fix<<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(maps, tiles, tiles, n, out, 0, len);
+    carry_fix<<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(maps, tiles, tiles, n, out, 0, len,
+                                                            false);
     CAT_LAUNCH("carry_fix");
 }
 

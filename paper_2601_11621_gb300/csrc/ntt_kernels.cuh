@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
 
 // ------------------------------------------------------------ row pass
 
-enum { PAIR_ADJACENT = 0, PAIR_SQUARE = 1, PAIR_FIRST_TWO = 2 };
+enum { PAIR_ADJACENT = 0, PAIR_SQUARE = 1, PAIR_FIRST_TWO = 2, PAIR_BROADCAST = 3 };
 
 constexpr int kRowThreads = 256;
 constexpr int kRowMaxLog = 12;
@@ -482,6 +482,7 @@ __global__ void __launch_bounds__(kRowThreads) ntt_row_mul(RowArgs a)
     size_t ta, tb;
     if (a.mode == PAIR_ADJACENT) { ta = 2 * k; tb = 2 * k + 1; }
     else if (a.mode == PAIR_SQUARE) { ta = k; tb = k; }
+    else if (a.mode == PAIR_BROADCAST) { ta = k; tb = gridDim.x / blocks; }  // y after the x's
     else { ta = 0; tb = 1; }
     const uint32_t *fa = a.F + p * a.fpstride + (ta << a.n) + off;
     const uint32_t *fb = a.F + p * a.fpstride + (tb << a.n) + off;

@@ -29,7 +29,6 @@ void ntt_mul(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
              uint32_t *out, cudaStream_t s);
 
 constexpr size_t kLeafSlot = 8;
-constexpr size_t kMaxProductLimbs = (size_t)1 << kLogMaxNtt;
 
 static Big make_one(Ctx &c, cudaStream_t s)
 {
@@ -63,9 +62,13 @@ void mul_into(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb
         if (na + nb) CAT_CUDA(cudaMemsetAsync(out, 0, 4 * (na + nb), s));
         return;
     }
-    if (na + nb > kMaxProductLimbs)
-        fail(CAT_EINVAL, "product longer than 2^27 limbs is not supported");
-    ntt_mul(c, a, na, b, nb, out, s);
+    if (na + nb <= ((size_t)1 << c.max_log)) {
+        ntt_mul(c, a, na, b, nb, out, s);
+        return;
+    }
+    // longer than one transform: pieces of at most 2^26 limbs, accumulated
+    CAT_CUDA(cudaMemsetAsync(out, 0, 4 * (na + nb), s));
+    mul_acc(c, a, na, b, nb, out, na + nb, false, s);
 }
 
 Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s)

@@ -14,14 +14,15 @@ HEADER = os.path.join(ROOT, "include", "catalan.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:int|void|const\s+char\s*\*)\s*\*?\s*(\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:int|void|size_t|const\s+char\s*\*)\s*\*?\s*(\w+)\s*\(", text,
+                       flags=re.M)
     return sorted(set(names))
 
 
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("catalan_factor", "bigint_mul", "bigint_pow", "product_tree",
-                 "catalan_exact", "cat_bound_limbs", "cat_exact"):
+                 "catalan_exact", "cat_bound_limbs", "cat_exact", "to_decimal"):
         assert must in names
 
 

@@ -364,3 +364,41 @@ def test_sieve_range_is_a_slice_of_the_sieve(orc):
                    ((1 << 24) - 50, (1 << 24) + 50), (2_999_000, 3_000_000)]:
         want = full[(full >= lo) & (full <= hi)]
         assert (orc.sieve_range(lo, hi) == want).all(), (lo, hi)
+
+
+# ------------------------------------------------- decimal output (Sec. 3.2)
+
+def _dec_special_values():
+    vals = [0, 1, 9, 10, 999_999_999, 1_000_000_000, 2**32 - 1, 2**32, 2**64 - 1]
+    for k in (9, 10, 17, 18, 19, 81, 154, 155, 1000):
+        vals += [10**k - 1, 10**k, 10**k + 1]
+    for w in (1, 2, 15, 16, 17, 100):
+        vals += [2 ** (32 * w) - 1, 2 ** (32 * w)]
+    return vals
+
+
+def test_to_decimal_vs_cpython(orc):
+    # the digits are unique; CPython's int -> str is an independent routine
+    import sys
+    if hasattr(sys, "set_int_max_str_digits"):
+        sys.set_int_max_str_digits(0)
+    rnd = random.Random(20260101)
+    vals = _dec_special_values()
+    for nl in (1, 2, 3, 7, 16, 33, 257, 2049):
+        vals.append(rnd.getrandbits(32 * nl) | 1 << (32 * nl - 1))
+    for v in vals:
+        assert orc.to_decimal(orc.int_to_limbs(v)) == str(v).encode(), v
+    # leading zero limbs are ignored
+    limbs = np.concatenate([orc.int_to_limbs(12345), np.zeros(5, np.uint32)])
+    assert orc.to_decimal(limbs) == b"12345"
+
+
+def test_to_decimal_catalan_digit_count(orc):
+    # C(10^5) has 60,199 digits (floor(log10 C) + 1 from log-gamma)
+    d = orc.to_decimal(orc.catalan(10**5))
+    assert len(d) == 60199
+    lg = math.lgamma(2e5 + 1) - math.lgamma(1e5 + 1) - math.lgamma(1e5 + 2)
+    assert len(d) == int(lg / math.log(10)) + 1
+    # leading digits from the fractional part of log10 C
+    frac = lg / math.log(10) - int(lg / math.log(10))
+    assert d[:6] == str(int(10 ** (frac + 5))).encode()
