@@ -145,7 +145,7 @@ int bigint_mul(cat_ctx *ctx, const uint32_t *a, size_t na, const uint32_t *b,
  * service that must not meet an out-of-memory failure in the middle of a
  * request.  There is no context: the
  * transform scratch and the twiddle tables live in fixed-size __device__
- * arrays of the library (about 2.4 MB of scratch and 0.5 MB of tables),
+ * arrays of the library (about 2.4 MB of scratch and 1.4 MB of tables),
  * which every GPU that loads the library holds until the process exits.
  *   - Limit: na + nb <= 65,536 limbs; larger products return CAT_ENOMEM.
  *   - out must have room for na + nb limbs (cap >= na + nb, else
