@@ -227,6 +227,28 @@ int cat_batch_bound(const cat_request *reqs, size_t count, size_t *total);
 int cat_exact_batch(cat_ctx *ctx, const cat_request *reqs, size_t count, uint32_t *out,
                     size_t cap, uint64_t *offsets, uint64_t *lengths, void *stream);
 
+/* -------------------------------------------------------- factorial ratios
+ * N = prod_{i<ka} a_i! / prod_{j<kb} b_j! (Sec. 6.3): binomials C(n, k) =
+ * n!/(k!(n-k)!), multinomials, and any other ratio of factorial products.
+ * Phase 1 sieves the primes up to the largest term and sums Legendre's
+ * formula over the terms, v_p(N) = sum_i v_p(a_i!) - sum_j v_p(b_j!); Phase 2
+ * is the same reconstruction as for C(n).  a and b are HOST arrays.
+ * Limits: 0 <= ka, kb <= 16; every term below 2^32; the a_i sum to less than
+ * 2^32 (so every exponent fits 32 bits).  An empty product is 1.
+ *
+ * cat_ratio_bound_limbs: an upper bound on N's limb count (log-gamma, two
+ * spare limbs).  cat_ratio_factor: the grouped factorisation, as
+ * catalan_factor (free with cat_factor_free).  cat_ratio_exact: N into the
+ * device buffer out of cap limbs, *out_len its normalised length.
+ * Errors: CAT_EINVAL (limits above, null pointers), CAT_ENOTINTEGRAL (some
+ * v_p(N) < 0: N is not an integer), CAT_ERANGE (cap too small), CAT_ENOMEM,
+ * CAT_ECUDA. */
+int cat_ratio_bound_limbs(const uint64_t *a, int ka, const uint64_t *b, int kb, size_t *limbs);
+int cat_ratio_factor(cat_ctx *ctx, const uint64_t *a, int ka, const uint64_t *b, int kb,
+                     cat_factorization *out, void *stream);
+int cat_ratio_exact(cat_ctx *ctx, const uint64_t *a, int ka, const uint64_t *b, int kb,
+                    uint32_t *out, size_t cap, size_t *out_len, void *stream);
+
 /* ----------------------------------------------------------- decimal output
  * The optional decimal text output of the reconstructed number (Sec. 3.2;
  * Table 1 of Sec. 5 states 1,234,567,890 digits for C(2,050,572,903)).

@@ -299,6 +299,22 @@ def catalan(n: int) -> np.ndarray:
     return exact(CATALAN, n)
 
 
+def ratio_exact(a: list[int], b: list[int]) -> np.ndarray:
+    """prod a_i! / prod b_j! (Sec. 6.3) by the same two phases: sieve to the
+    largest term, exponents by the ratio form of Legendre's formula, grouping,
+    Algorithm 2.  Raises ValueError when some exponent is negative (the ratio
+    is not an integer)."""
+    limit = max(list(a) + list(b) + [0])
+    primes = sieve(limit) if limit >= 2 else np.zeros(0, dtype=np.uint32)
+    e = ratio_exponents(a, b, primes)
+    if (e < 0).any():
+        raise ValueError("not integral")
+    exps, offs, gp = group(primes, e)
+    # bits: sum e_p * bitlen(p)
+    bits = int(sum(int(x) * int(p).bit_length() for x, p in zip(e, primes) if x > 0))
+    return reconstruct(exps, offs, gp, bits // 32 + 2)
+
+
 # ---------------------------------------------------------------- checks
 
 def exact_mod(kind: int, n: int, q: int) -> int:

@@ -34,7 +34,8 @@ EXPORTED = ["cat_ctx_create", "cat_ctx_destroy", "cat_last_error", "cat_ctx_memo
             "catalan_exact", "cat_exact_host", "cat_batch_bound", "cat_exact_batch",
             "cat_server_create", "cat_server_submit", "cat_server_poll", "cat_server_wait",
             "cat_server_fetch", "cat_server_release", "cat_server_pending",
-            "cat_server_destroy", "cat_decimal_bound", "to_decimal"]
+            "cat_server_destroy", "cat_decimal_bound", "to_decimal",
+            "cat_ratio_bound_limbs", "cat_ratio_factor", "cat_ratio_exact"]
 
 
 class CatError(RuntimeError):
@@ -102,6 +103,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.bigint_mul.restype = i32
     L.bigint_mul_noalloc.argtypes = [vp, sz, vp, sz, vp, sz, szp, vp]
     L.bigint_mul_noalloc.restype = i32
+    u64a = ctypes.POINTER(ctypes.c_uint64)
+    L.cat_ratio_bound_limbs.argtypes = [u64a, i32, u64a, i32, szp]
+    L.cat_ratio_bound_limbs.restype = i32
+    L.cat_ratio_factor.argtypes = [vp, u64a, i32, u64a, i32, ctypes.POINTER(Factorization), vp]
+    L.cat_ratio_factor.restype = i32
+    L.cat_ratio_exact.argtypes = [vp, u64a, i32, u64a, i32, vp, sz, szp, vp]
+    L.cat_ratio_exact.restype = i32
     L.cat_decimal_bound.argtypes = [sz]
     L.cat_decimal_bound.restype = sz
     L.to_decimal.argtypes = [vp, vp, sz, vp, sz, szp, vp]
@@ -241,6 +249,43 @@ def bigint_mul(ctx: Context, a, b, stream=None):
     n = ctypes.c_size_t()
     ctx.check(load().bigint_mul(ctx.handle, _ptr(ta), ta.numel(), _ptr(tb), tb.numel(),
                                 _ptr(out), cap, ctypes.byref(n), _stream(stream)))
+    return out[:n.value]
+
+
+def _u64_array(v):
+    arr = (ctypes.c_uint64 * max(len(v), 1))(*[int(x) for x in v])
+    return arr, len(v)
+
+
+def cat_ratio_bound_limbs(a, b) -> int:
+    """Limb bound of prod a_i! / prod b_j! (Sec. 6.3)."""
+    (pa, ka), (pb, kb) = _u64_array(a), _u64_array(b)
+    out = ctypes.c_size_t()
+    rc = load().cat_ratio_bound_limbs(pa, ka, pb, kb, ctypes.byref(out))
+    if rc != 0:
+        raise CatError(rc, "cat_ratio_bound_limbs")
+    return out.value
+
+
+def cat_ratio_factor(ctx: Context, a, b, stream=None) -> "FactorResult":
+    """Grouped factorisation of prod a_i! / prod b_j! (device arrays)."""
+    (pa, ka), (pb, kb) = _u64_array(a), _u64_array(b)
+    f = Factorization()
+    ctx.check(load().cat_ratio_factor(ctx.handle, pa, ka, pb, kb, ctypes.byref(f),
+                                      _stream(stream)))
+    return FactorResult(ctx, f)
+
+
+def cat_ratio_exact(ctx: Context, a, b, out=None, stream=None):
+    """prod a_i! / prod b_j! as a device limb tensor (CAT_ENOTINTEGRAL when it is
+    not an integer)."""
+    dev = f"cuda:{ctx.device}"
+    (pa, ka), (pb, kb) = _u64_array(a), _u64_array(b)
+    if out is None:
+        out = _empty(cat_ratio_bound_limbs(a, b), dev)
+    n = ctypes.c_size_t()
+    ctx.check(load().cat_ratio_exact(ctx.handle, pa, ka, pb, kb, _ptr(out), out.numel(),
+                                     ctypes.byref(n), _stream(stream)))
     return out[:n.value]
 
 

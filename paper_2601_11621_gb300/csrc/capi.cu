@@ -49,6 +49,30 @@ int guarded(cat_ctx *ctx, F &&body)
 
 inline cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 
+// A factorial ratio from the ABI's arrays; false if the arguments are out of
+// range (term count, a term >= 2^32, numerator sum >= 2^32, null arrays).
+bool make_ratio(const uint64_t *a, int ka, const uint64_t *b, int kb, cat::Ratio *r)
+{
+    if (ka < 0 || kb < 0 || ka > cat::kMaxRatioTerms || kb > cat::kMaxRatioTerms) return false;
+    if ((ka && !a) || (kb && !b)) return false;
+    *r = cat::Ratio{};
+    r->kind = cat::kRatioKind;
+    r->ka = ka;
+    r->kb = kb;
+    uint64_t sum = 0;
+    for (int i = 0; i < ka; i++) {
+        if (a[i] >= (1ull << 32)) return false;
+        sum += a[i];
+        r->a[i] = (uint32_t)a[i];
+    }
+    if (sum >= (1ull << 32)) return false;
+    for (int j = 0; j < kb; j++) {
+        if (b[j] >= (1ull << 32)) return false;
+        r->b[j] = (uint32_t)b[j];
+    }
+    return true;
+}
+
 void copy_out(cat::Ctx &c, const cat::Big &r, uint32_t *out, size_t cap, size_t *out_len,
               cudaStream_t s)
 {
@@ -214,6 +238,42 @@ int cat_exact(cat_ctx *ctx, int kind, uint64_t n, uint32_t *out, size_t cap,
         cudaStream_t s = as_stream(stream);
         cat_factorization f{};
         cat::factor(ctx->c, n, kind, &f, s);
+        try {
+            cat::Big r = cat::reconstruct(ctx->c, &f, s);
+            cat::factor_free(ctx->c, &f);
+            copy_out(ctx->c, r, out, cap, out_len, s);
+        } catch (...) {
+            cat::factor_free(ctx->c, &f);
+            throw;
+        }
+    });
+}
+
+int cat_ratio_bound_limbs(const uint64_t *a, int ka, const uint64_t *b, int kb, size_t *limbs)
+{
+    cat::Ratio r;
+    if (!limbs || !make_ratio(a, ka, b, kb, &r)) return CAT_EINVAL;
+    *limbs = cat::ratio_bound_limbs(r);
+    return CAT_OK;
+}
+
+int cat_ratio_factor(cat_ctx *ctx, const uint64_t *a, int ka, const uint64_t *b, int kb,
+                     cat_factorization *out, void *stream)
+{
+    cat::Ratio r;
+    if (!ctx || !out || !make_ratio(a, ka, b, kb, &r)) return CAT_EINVAL;
+    return guarded(ctx, [&] { cat::factor_ratio(ctx->c, r, out, as_stream(stream)); });
+}
+
+int cat_ratio_exact(cat_ctx *ctx, const uint64_t *a, int ka, const uint64_t *b, int kb,
+                    uint32_t *out, size_t cap, size_t *out_len, void *stream)
+{
+    cat::Ratio q;
+    if (!ctx || !out_len || (cap && !out) || !make_ratio(a, ka, b, kb, &q)) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        cudaStream_t s = as_stream(stream);
+        cat_factorization f{};
+        cat::factor_ratio(ctx->c, q, &f, s);
         try {
             cat::Big r = cat::reconstruct(ctx->c, &f, s);
             cat::factor_free(ctx->c, &f);

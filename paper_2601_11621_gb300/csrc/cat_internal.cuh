@@ -508,13 +508,29 @@ size_t normalized_length(Ctx &c, const uint32_t *x, size_t n, cudaStream_t s);
 Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s);
 // a^e.
 Big power(Ctx &c, const uint32_t *a, size_t na, uint64_t e, cudaStream_t s);
+// Factorial ratios (Sec. 6.3): N = prod_i a_i! / prod_j b_j!.  A Ratio also
+// describes the three kinds (kind < kRatioKind: the quantity of n).  Every
+// term is below 2^32 and the a_i sum to less than 2^32, so every exponent
+// fits 32 bits.
+constexpr int kRatioKind = 3;
+constexpr int kMaxRatioTerms = 16;
+
+struct Ratio {
+    int kind;
+    uint32_t n;
+    int ka, kb;
+    uint32_t a[kMaxRatioTerms], b[kMaxRatioTerms];
+};
+
 // Phase 1 on the device.  The arrays of *out come from the context's pool
 // and are released by factor_free.
 void factor(Ctx &c, uint64_t n, int kind, cat_factorization *out, cudaStream_t s);
+void factor_ratio(Ctx &c, const Ratio &r, cat_factorization *out, cudaStream_t s);
 void factor_free(Ctx &c, cat_factorization *f);
 // Algorithm 2 on a factorisation; returns the result (normalised length).
 Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s);
 
 size_t bound_limbs(uint64_t n, int kind);
+size_t ratio_bound_limbs(const Ratio &r);
 
 }  // namespace cat

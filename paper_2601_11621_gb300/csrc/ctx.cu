@@ -264,4 +264,15 @@ size_t bound_limbs(uint64_t n, int kind)
     return (size_t)(bits / 32.0) + 2;
 }
 
+// The same for a factorial ratio: sum_i ln a_i! - sum_j ln b_j!, each term's
+// lgamma error far below the two spare limbs.
+size_t ratio_bound_limbs(const Ratio &r)
+{
+    double ln = 0;
+    for (int i = 0; i < r.ka; i++) ln += lgamma((double)r.a[i] + 1.0);
+    for (int j = 0; j < r.kb; j++) ln -= lgamma((double)r.b[j] + 1.0);
+    if (ln < 0) ln = 0;
+    return (size_t)(ln / log(2.0) / 32.0) + 2;
+}
+
 }  // namespace cat

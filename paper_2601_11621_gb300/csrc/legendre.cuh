@@ -42,4 +42,14 @@ __device__ __forceinline__ int64_t exponent_of(uint32_t p, uint32_t n, int kind)
     return e;
 }
 
+// v_p of a Ratio (Sec. 6.3: v_p(N) = sum_i v_p(a_i!) - sum_j v_p(b_j!)).
+__device__ __forceinline__ int64_t exponent_of(uint32_t p, const Ratio &r)
+{
+    if (r.kind != kRatioKind) return exponent_of(p, r.n, r.kind);
+    int64_t e = 0;
+    for (int i = 0; i < r.ka; i++) e += legendre32(r.a[i], p);
+    for (int j = 0; j < r.kb; j++) e -= legendre32(r.b[j], p);
+    return e;
+}
+
 }  // namespace cat

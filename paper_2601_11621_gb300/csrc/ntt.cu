@@ -2,8 +2,8 @@
 // transform (NTT), Chinese remaindering and carry propagation.
 //
 // This is the multiplication the reconstruction phase spends its time in
-// (Sec. 3.2 and Sec. 6.1: "large-integer multiplications ... consume the
-// majority of the runtime"; Sec. 6.3 names FFT-based multiplication).  The
+// (Sec. 3.2; Sec. 6 reports that the big products dominate the run time, and
+// Sec. 6.3 assumes an FFT-based multiplication for large operands).  The
 // method is the classical one: the limbs of a and b are the coefficients of
 // two polynomials; their cyclic convolution of length L = 2^n >= na + nb is
 // computed modulo three primes q_i (forward transforms, pointwise product,

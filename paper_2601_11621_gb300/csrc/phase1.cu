@@ -168,8 +168,7 @@ __global__ void __launch_bounds__(kSieveThreads) sieve_segments(SieveArgs a)
 struct ExpandArgs {
     const uint32_t *bits;
     const uint32_t *seg_offsets;  // exclusive scan of the per-segment counts
-    uint32_t n;
-    int kind;
+    Ratio r;                      // the quantity (a kind of n, or a factorial ratio)
     int has_two;                  // limit >= 2: item 0 is the prime 2
     uint64_t *items;              // out: (e << 32) | p, all primes ascending
     unsigned int *max_e;
@@ -209,7 +208,7 @@ __global__ void __launch_bounds__(kSieveThreads) expand_exponents(ExpandArgs a)
             const int b = __ffs(v) - 1;
             v &= v - 1;
             const uint32_t p = 2 * (ibase + 32 * k + b) + 1;
-            const int64_t e = exponent_of(p, a.n, a.kind);
+            const int64_t e = exponent_of(p, a.r);
             if (e < 0) neg = 1;
             const uint32_t eu = e < 0 ? 0u : (uint32_t)e;
             emax = max(emax, eu);
@@ -217,7 +216,7 @@ __global__ void __launch_bounds__(kSieveThreads) expand_exponents(ExpandArgs a)
         }
     }
     if (seg == 0 && threadIdx.x == 0 && a.has_two) {
-        const int64_t e = exponent_of(2, a.n, a.kind);
+        const int64_t e = exponent_of(2, a.r);
         if (e < 0) neg = 1;
         const uint32_t eu = e < 0 ? 0u : (uint32_t)e;
         emax = max(emax, eu);
@@ -416,8 +415,25 @@ void factor(Ctx &c, uint64_t n, int kind, cat_factorization *out, cudaStream_t s
 {
     if (n >= (1ull << 31)) fail(CAT_EINVAL, "n must be below 2^31");
     if (kind < CAT_CATALAN || kind > CAT_FACTORIAL) fail(CAT_EINVAL, "unknown kind");
+    Ratio r{};
+    r.kind = kind;
+    r.n = (uint32_t)n;
+    factor_ratio(c, r, out, s);
+}
+
+// Phase 1 for any Ratio: primes up to the largest factorial argument (2n for
+// the binomial kinds, n for n!, the largest term of a ratio).
+void factor_ratio(Ctx &c, const Ratio &r, cat_factorization *out, cudaStream_t s)
+{
     *out = cat_factorization{};
-    const uint64_t limit = kind == CAT_FACTORIAL ? n : 2 * n;
+    const int kind = r.kind;
+    const uint64_t n = r.n;
+    uint64_t limit = kind == CAT_FACTORIAL ? n : 2 * n;
+    if (kind == kRatioKind) {
+        limit = 0;
+        for (int i = 0; i < r.ka; i++) limit = std::max<uint64_t>(limit, r.a[i]);
+        for (int j = 0; j < r.kb; j++) limit = std::max<uint64_t>(limit, r.b[j]);
+    }
     std::vector<uint64_t> h_exps, h_offs{0};
     DevBuf<uint32_t> primes_out;
     uint64_t sieved = 0, npos = 0;
@@ -432,8 +448,7 @@ void factor(Ctx &c, uint64_t n, int kind, cat_factorization *out, cudaStream_t s
         DevBuf<uint64_t> items(c, sieved, s);
         DevBuf<unsigned int> flags(c, 2, s);
         CAT_CUDA(cudaMemsetAsync(flags.get(), 0, 8, s));
-        ExpandArgs ea{bits.get(), counts.get(), (uint32_t)n, kind, 1, items.get(),
-                      flags.get(), flags.get() + 1};
+        ExpandArgs ea{bits.get(), counts.get(), r, 1, items.get(), flags.get(), flags.get() + 1};
         tok = prof_begin(c, "expand_exponents", s);
         expand_exponents<<<nsegs, kSieveThreads, 0, s>>>(ea);
         CAT_LAUNCH("expand_exponents");

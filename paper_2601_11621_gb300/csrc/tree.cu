@@ -117,7 +117,7 @@ static Big mul_big(Ctx &c, const Big &x, const Big &y, cudaStream_t s)
     return r;
 }
 
-// a^e, left-to-right binary ("fast pow" of Algorithm 2).  Squarings reuse
+// a^e, left-to-right binary (the powering step of Algorithm 2).  Squarings reuse
 // one forward transform.
 Big power(Ctx &c, const uint32_t *a, size_t na, uint64_t e, cudaStream_t s)
 {

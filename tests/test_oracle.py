@@ -402,3 +402,30 @@ def test_to_decimal_catalan_digit_count(orc):
     # leading digits from the fractional part of log10 C
     frac = lg / math.log(10) - int(lg / math.log(10))
     assert d[:6] == str(int(10 ** (frac + 5))).encode()
+
+
+# --------------------------------------- factorial ratios (Sec. 6.3)
+
+def test_ratio_exact_vs_cpython(orc):
+    f = math.factorial
+    cases = [([10], [3, 7]), ([1000], [400, 600]), ([30], [10, 10, 10]),
+             ([2 * 500], [500, 501]), ([200, 7], [100, 100]), ([12], [12]), ([], []),
+             ([5000], [4999]), ([0], []), ([1, 1], [0])]
+    for a, b in cases:
+        want = 1
+        for x in a:
+            want *= f(x)
+        for y in b:
+            assert want % f(y) == 0
+            want //= f(y)
+        assert orc.limbs_to_int(orc.ratio_exact(a, b)) == want, (a, b)
+    # C(n) through the ratio form equals Algorithm 1 (kind = Catalan)
+    assert (orc.ratio_exact([2 * 3000], [3000, 3001]) == orc.catalan(3000)).all()
+
+
+def test_ratio_not_integral(orc):
+    # 5!/(3! 3!) = 10/3; 3!/4!; 7!/(2! 2! 2! 2!) = 315 is integral
+    for a, b in [([5], [3, 3]), ([3], [4]), ([10], [11])]:
+        with pytest.raises(ValueError):
+            orc.ratio_exact(a, b)
+    assert orc.limbs_to_int(orc.ratio_exact([7], [2, 2, 2, 2])) == 315
