@@ -249,6 +249,27 @@ int cat_ratio_factor(cat_ctx *ctx, const uint64_t *a, int ka, const uint64_t *b,
 int cat_ratio_exact(cat_ctx *ctx, const uint64_t *a, int ka, const uint64_t *b, int kb,
                     uint32_t *out, size_t cap, size_t *out_len, void *stream);
 
+/* ---------------------------------------------------------------- artifacts
+ * cat_factor_text: the grouped factorisation f in the text layout of Sec. 3.1,
+ * as ASCII into the device buffer out of cap bytes:
+ *     # Prime factorization of <name>
+ *     # exponent=E count=K            (one block per group, ascending E)
+ *     p1 p2 ... pK                    (its primes, ascending, one line)
+ * Lines end with '\n'; no terminator.  *out_len = the byte count (the exact
+ * size is returned with CAT_ERANGE when cap is short).  At most 390,000,000
+ * primes.  Errors: CAT_EINVAL, CAT_ERANGE, CAT_ENOMEM, CAT_ECUDA.
+ *
+ * cat_binary: the result file of Algorithm 2's last step: the bytes 01 01
+ * followed by the magnitude of limbs[0..n) in little-endian byte order, its
+ * minimal length ceil(bits / 8) (the layout whose SHA-256 is the one Table 1
+ * prints for C(2,050,572,903); the paper states the magnitude's size,
+ * 512,643,220 bytes), into the device buffer out of cap bytes.  Zero is the
+ * two header bytes alone.  Errors: CAT_EINVAL, CAT_ERANGE, CAT_ECUDA. */
+int cat_factor_text(cat_ctx *ctx, const cat_factorization *f, const char *name, char *out,
+                    size_t cap, size_t *out_len, void *stream);
+int cat_binary(cat_ctx *ctx, const uint32_t *limbs, size_t n, uint8_t *out, size_t cap,
+               size_t *out_len, void *stream);
+
 /* ----------------------------------------------------------- decimal output
  * The optional decimal text output of the reconstructed number (Sec. 3.2;
  * Table 1 of Sec. 5 states 1,234,567,890 digits for C(2,050,572,903)).

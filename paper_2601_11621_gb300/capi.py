@@ -35,7 +35,8 @@ EXPORTED = ["cat_ctx_create", "cat_ctx_destroy", "cat_last_error", "cat_ctx_memo
             "cat_server_create", "cat_server_submit", "cat_server_poll", "cat_server_wait",
             "cat_server_fetch", "cat_server_release", "cat_server_pending",
             "cat_server_destroy", "cat_decimal_bound", "to_decimal",
-            "cat_ratio_bound_limbs", "cat_ratio_factor", "cat_ratio_exact"]
+            "cat_ratio_bound_limbs", "cat_ratio_factor", "cat_ratio_exact",
+            "cat_factor_text", "cat_binary"]
 
 
 class CatError(RuntimeError):
@@ -110,6 +111,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cat_ratio_factor.restype = i32
     L.cat_ratio_exact.argtypes = [vp, u64a, i32, u64a, i32, vp, sz, szp, vp]
     L.cat_ratio_exact.restype = i32
+    L.cat_factor_text.argtypes = [vp, ctypes.POINTER(Factorization), ctypes.c_char_p, vp, sz,
+                                  szp, vp]
+    L.cat_factor_text.restype = i32
+    L.cat_binary.argtypes = [vp, vp, sz, vp, sz, szp, vp]
+    L.cat_binary.restype = i32
     L.cat_decimal_bound.argtypes = [sz]
     L.cat_decimal_bound.restype = sz
     L.to_decimal.argtypes = [vp, vp, sz, vp, sz, szp, vp]
@@ -286,6 +292,34 @@ def cat_ratio_exact(ctx: Context, a, b, out=None, stream=None):
     n = ctypes.c_size_t()
     ctx.check(load().cat_ratio_exact(ctx.handle, pa, ka, pb, kb, _ptr(out), out.numel(),
                                      ctypes.byref(n), _stream(stream)))
+    return out[:n.value]
+
+
+def cat_factor_text(ctx: Context, fr: "FactorResult", name: str, stream=None):
+    """The factorisation in the text layout of Sec. 3.1 (uint8 device tensor)."""
+    import torch
+    dev = f"cuda:{ctx.device}"
+    n = ctypes.c_size_t()
+    rc = load().cat_factor_text(ctx.handle, ctypes.byref(fr.f), name.encode(), None, 0,
+                                ctypes.byref(n), _stream(stream))
+    if rc not in (0, CAT_ERANGE):
+        ctx.check(rc)
+    out = torch.empty(max(n.value, 1), dtype=torch.uint8, device=dev)
+    ctx.check(load().cat_factor_text(ctx.handle, ctypes.byref(fr.f), name.encode(), _ptr(out),
+                                     out.numel(), ctypes.byref(n), _stream(stream)))
+    return out[:n.value]
+
+
+def cat_binary(ctx: Context, limbs, stream=None):
+    """The result file bytes (01 01, then the little-endian magnitude) as a
+    uint8 device tensor."""
+    import torch
+    dev = f"cuda:{ctx.device}"
+    t = _limbs_tensor(limbs, dev)
+    out = torch.empty(4 * t.numel() + 2, dtype=torch.uint8, device=dev)
+    n = ctypes.c_size_t()
+    ctx.check(load().cat_binary(ctx.handle, _ptr(t), t.numel(), _ptr(out), out.numel(),
+                                ctypes.byref(n), _stream(stream)))
     return out[:n.value]
 
 

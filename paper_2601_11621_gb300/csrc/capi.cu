@@ -336,6 +336,26 @@ int cat_exact_host(cat_ctx *ctx, int kind, uint64_t n, uint32_t *host_out, size_
     });
 }
 
+int cat_factor_text(cat_ctx *ctx, const cat_factorization *f, const char *name, char *out,
+                    size_t cap, size_t *out_len, void *stream)
+{
+    if (!ctx || !f || !name || !out_len || (cap && !out)) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        if (cat::factor_text(ctx->c, f, name, out, cap, out_len, as_stream(stream)) != CAT_OK)
+            cat::fail(CAT_ERANGE, "output capacity too small");
+    });
+}
+
+int cat_binary(cat_ctx *ctx, const uint32_t *limbs, size_t n, uint8_t *out, size_t cap,
+               size_t *out_len, void *stream)
+{
+    if (!ctx || !out_len || (n && !limbs) || (cap && !out)) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        if (cat::binary_file(ctx->c, limbs, n, out, cap, out_len, as_stream(stream)) != CAT_OK)
+            cat::fail(CAT_ERANGE, "output capacity too small");
+    });
+}
+
 size_t cat_decimal_bound(size_t n) { return cat::decimal_bound(n); }
 
 int to_decimal(cat_ctx *ctx, const uint32_t *limbs, size_t n, char *out, size_t cap,

@@ -530,6 +530,14 @@ void factor_free(Ctx &c, cat_factorization *f);
 // Algorithm 2 on a factorisation; returns the result (normalised length).
 Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s);
 
+// The factorisation as the paper's text layout (Sec. 3.1) into out (device),
+// titled `name`; the binary result file (bytes 01 01, then the magnitude
+// little-endian).  Both fail with CAT_ERANGE when cap is short (*needed set).
+int factor_text(Ctx &c, const cat_factorization *f, const char *name, char *out, size_t cap,
+                size_t *needed, cudaStream_t s);
+int binary_file(Ctx &c, const uint32_t *x, size_t n, uint8_t *out, size_t cap, size_t *needed,
+                cudaStream_t s);
+
 size_t bound_limbs(uint64_t n, int kind);
 size_t ratio_bound_limbs(const Ratio &r);
 
