@@ -493,6 +493,10 @@ void mul_broadcast(Ctx &c, const uint32_t *x, size_t xstride, size_t xlen, size_
 // acc[0 .. R) += t[0 .. tn), base 2^32 or (dec) 10^9, carries through acc.
 void add_into(Ctx &c, uint32_t *acc, size_t R, const uint32_t *t, size_t tn, bool dec,
               cudaStream_t s);
+// out[0 .. nx + ny) = x y for ny <= 2^k - ny: chunks of 2^k - ny limbs of x
+// times y in one batch (y transformed once), overlap-added.
+void mul_chunked(Ctx &c, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny, int k,
+                 uint32_t *out, cudaStream_t s);
 // acc[0 .. R) += x y for any lengths (pieces of <= 2^26 limbs when long).
 void mul_acc(Ctx &c, const uint32_t *x, size_t xlen, const uint32_t *y, size_t ylen,
              uint32_t *acc, size_t R, bool dec, cudaStream_t s);

@@ -910,6 +910,85 @@ void mul_acc(Ctx &c, const uint32_t *x, size_t xlen, const uint32_t *y, size_t y
         }
 }
 
+// ------------------------------------------- unbalanced products by chunks
+
+// The product of a long x (nx limbs) and a short y (ny limbs) from chunk
+// products: chunk i = x[iM, iM + M) times y lies in slot i of T (M + ny
+// words), and belongs at offset iM, so it overlaps the next chunk's product by
+// ny limbs.  Limb j of the result sums t1 = slot k's word j - kM (k = j / M,
+// the last slot also covers its tail) and t2 = slot k-1's word M + (j - kM)
+// when j - kM < ny.  Per tile: run words c0[i] = t1(j0 + i) and c1[i] =
+// t2(j0 + i + 1), so tile_carry's c1[j - 1] term adds t2(j) to limb j.
+__device__ __forceinline__ void overlap_terms(const uint32_t *T, size_t M, size_t ny,
+                                              size_t chunks, size_t j, uint32_t &t1,
+                                              uint32_t &t2)
+{
+    size_t k = j / M;
+    const bool past = k >= chunks;
+    if (past) k = chunks - 1;
+    const size_t r = j - k * M;
+    t1 = r < M + ny ? T[k * (M + ny) + r] : 0u;
+    t2 = (!past && k >= 1 && r < ny) ? T[(k - 1) * (M + ny) + M + r] : 0u;
+}
+
+__global__ void __launch_bounds__(kTileThreads) overlap_tiles(const uint32_t *T, size_t M,
+                                                              size_t ny, size_t chunks,
+                                                              uint32_t *out, size_t R,
+                                                              uint8_t *tile_maps)
+{
+    __shared__ uint32_t wsm[32];
+    __shared__ uint32_t hsm[96];
+    const size_t jt = (size_t)blockIdx.x * kTile;
+    const size_t j0 = jt + threadIdx.x * kLimbsPerThread;
+    CoefRun run;
+#pragma unroll
+    for (int i = 0; i < kLimbsPerThread; i++) {
+        uint32_t a = 0, b = 0, dummy = 0;
+        if (j0 + i < R) overlap_terms(T, M, ny, chunks, j0 + i, a, dummy);
+        if (j0 + i + 1 < R) overlap_terms(T, M, ny, chunks, j0 + i + 1, dummy, b);
+        run.c0[i] = a;
+        run.c1[i] = b;
+        run.c2[i] = 0u;
+    }
+    uint32_t first1 = 0, dummy = 0;
+    if (threadIdx.x == 0 && jt < R) overlap_terms(T, M, ny, chunks, jt, dummy, first1);
+    uint32_t h1, h2a, h2b;
+    run_halo(run, first1, 0u, 0u, hsm, h1, h2a, h2b);
+    const int tile_len = (int)(R - jt < (size_t)kTile ? R - jt : (size_t)kTile);
+    uint32_t map;
+    tile_carry(run, h1, 0u, 0u, tile_len, out + jt, tile_len, false, nullptr, 0, wsm, &map);
+    if (threadIdx.x == 0) tile_maps[blockIdx.x] = (uint8_t)map;
+}
+
+// out[0 .. nx + ny) = x y by chunks of M = 2^k - ny >= ny limbs of x, each
+// multiplied by y in one batch (y transformed once).
+void mul_chunked(Ctx &c, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny, int k,
+                 uint32_t *out, cudaStream_t s)
+{
+    const size_t L = (size_t)1 << k, M = L - ny, slot = L;
+    if (ny == 0 || M < ny) fail(CAT_EINVAL, "chunk size below the short operand");
+    const size_t full = nx / M, rem = nx - full * M, chunks = full + (rem ? 1 : 0);
+    DevBuf<uint32_t> T(c, chunks * slot, s);
+    if (full) mul_broadcast(c, x, M, M, full, y, ny, plain_sink(T.get(), slot, slot), s);
+    if (rem) {
+        uint32_t *last = T.get() + full * slot;
+        CAT_CUDA(cudaMemsetAsync(last, 0, 4 * slot, s));
+        mul_broadcast(c, x + full * M, 0, rem, 1, y, ny, plain_sink(last, 0, rem + ny), s);
+    }
+    const size_t R = nx + ny, tiles = (R + kTile - 1) / kTile;
+    DevBuf<uint8_t> maps(c, tiles, s);
+    const int tok = prof_begin(c, "overlap_tiles", s);
+    overlap_tiles<<<(unsigned)tiles, kTileThreads, 0, s>>>(T.get(), M, ny, chunks, out, R,
+                                                            maps.get());
+    CAT_LAUNCH("overlap_tiles");
+    carry_tile_scan<<<1, 1024, 0, s>>>(maps.get(), tiles);
+    CAT_LAUNCH("carry_tile_scan");
+    carry_fix<<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(maps.get(), tiles, tiles, 0, out, 0,
+                                                              R, false);
+    CAT_LAUNCH("carry_fix");
+    prof_end(c, tok, s, 4.0 * (double)(chunks * slot) + 4.0 * (double)R);
+}
+
 // --------------------------------------- multiplication without allocation
 //
 // For callers that must not allocate device memory: code running where
