@@ -440,8 +440,10 @@ constexpr int kFusedThreads = 512;
 // space (it is last read before R2 is written), raw B [3L,4L), transform pair
 // XY [4L,6L).  Every thread owns a run of eight coefficients for the carries
 // (L <= 8 x threads).
+// Two blocks per SM (64 registers; a small spill in the remaindering phase):
+// measured faster than one block per SM without the spill.
 template <int LR>
-__global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
+__global__ void __launch_bounds__(kFusedThreads, 2) ntt_mul_fused(FusedArgs a)
 {
     extern __shared__ uint32_t sm[];
     __shared__ uint32_t wsm[32];
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(kFusedThreads) ntt_mul_fused(FusedArgs a)
             Y[swz(i)] = reduce_in<0>(gb ? rawB[i] : rawA[i], q, wp1);
         }
         __syncthreads();
-        dif_smem<LR, 2, 0>(X, T, q);
+        dif_smem<LR, 2, 0>(X, T, q);  // X and Y as two arrays
         uint32_t *Z = Rr[p];
         // elementwise in the swizzled space: Z, X, Y share the permutation
         for (int i = threadIdx.x; i < L; i += blockDim.x) Z[i] = pmul<0>(X[i], Y[i], sc, q, qinv);

@@ -172,38 +172,40 @@ struct SmemIO {
     }
 };
 
-// All-shared-memory transforms (used by the one-block multiply).  Caller
+// All-shared-memory transforms (used by the one-block multiply) of C arrays
+// of 2^LR words each, back to back (swizzled); every group holds one array's
+// points, so a round has C 2^(LR - E) groups for the block's threads.  Caller
 // synchronises before; these return synchronised.
-template <int LR, int NA, int PS>
+template <int LR, int C, int PS>
 __device__ __forceinline__ void dif_smem(uint32_t *s, const uint2 *T, uint32_t q)
 {
     constexpr int NR = rounds_of(LR);
-    SmemIO<LR, 1, true> S{s};
-    round_io<LR, 1, dif_base(LR, 0), round_size(LR, 0), true, NA, true, PS>(S, S, T, q);
+    SmemIO<LR, C, false> S{s};
+    round_io<LR, C, dif_base(LR, 0), round_size(LR, 0), true, 1, false, PS>(S, S, T, q);
     __syncthreads();
     if constexpr (NR >= 2) {
-        round_io<LR, 1, dif_base(LR, 1), round_size(LR, 1), true, NA, true, PS>(S, S, T, q);
+        round_io<LR, C, dif_base(LR, 1), round_size(LR, 1), true, 1, false, PS>(S, S, T, q);
         __syncthreads();
     }
     if constexpr (NR >= 3) {
-        round_io<LR, 1, dif_base(LR, 2), round_size(LR, 2), true, NA, true, PS>(S, S, T, q);
+        round_io<LR, C, dif_base(LR, 2), round_size(LR, 2), true, 1, false, PS>(S, S, T, q);
         __syncthreads();
     }
 }
 
-template <int LR, int NA, int PS>
+template <int LR, int C, int PS>
 __device__ __forceinline__ void dit_smem(uint32_t *s, const uint2 *Ti, uint32_t q)
 {
     constexpr int NR = rounds_of(LR);
-    SmemIO<LR, 1, true> S{s};
-    round_io<LR, 1, dit_base(LR, 0), dit_size(LR, 0), false, NA, true, PS>(S, S, Ti, q);
+    SmemIO<LR, C, false> S{s};
+    round_io<LR, C, dit_base(LR, 0), dit_size(LR, 0), false, 1, false, PS>(S, S, Ti, q);
     __syncthreads();
     if constexpr (NR >= 2) {
-        round_io<LR, 1, dit_base(LR, 1), dit_size(LR, 1), false, NA, true, PS>(S, S, Ti, q);
+        round_io<LR, C, dit_base(LR, 1), dit_size(LR, 1), false, 1, false, PS>(S, S, Ti, q);
         __syncthreads();
     }
     if constexpr (NR >= 3) {
-        round_io<LR, 1, dit_base(LR, 2), dit_size(LR, 2), false, NA, true, PS>(S, S, Ti, q);
+        round_io<LR, C, dit_base(LR, 2), dit_size(LR, 2), false, 1, false, PS>(S, S, Ti, q);
         __syncthreads();
     }
 }
