@@ -298,7 +298,11 @@ int to_decimal(cat_ctx *ctx, const uint32_t *limbs, size_t n, char *out, size_t 
  * admits the queued requests in arrival order while their estimated device
  * footprint fits its share of hbm_budget_bytes (0 = no cap; at least one
  * request is always admitted) and at most max_batch of them (0 = 4096), and
- * computes them together with cat_exact_batch.  Requests that arrive while
+ * computes them together with cat_exact_batch.  The footprint estimate is
+ * 256 bytes per limb of the result bound (cat_bound_limbs); cat_server_submit
+ * denies (CAT_ENOMEM) a request whose estimate alone exceeds the budget, and
+ * every worker's context is capped at the budget, so a batch that still
+ * outgrows it fails with CAT_ENOMEM for its tickets.  Requests that arrive while
  * batches are running are admitted by the next idle worker, so batches
  * overlap on the GPU.  Results stay in device memory until released.
  * All functions are thread-safe. */
@@ -319,7 +323,8 @@ typedef struct {
 int cat_server_create(int device, size_t hbm_budget_bytes, int workers, size_t max_batch,
                       cat_server **out);
 
-/* Queues one request; *ticket identifies it.  Errors: CAT_EINVAL. */
+/* Queues one request; *ticket identifies it.  Errors: CAT_EINVAL, CAT_ENOMEM
+ * (estimated footprint above the whole budget). */
 int cat_server_submit(cat_server *sv, int kind, uint64_t n, uint64_t *ticket);
 
 /* CAT_EBUSY while queued or running; CAT_OK with *res filled when done; the

@@ -383,6 +383,7 @@ constexpr uint64_t kBatchFactorialMax = 64;
 void exact_batch(Ctx &c, const cat_request *reqs, size_t count, uint32_t *out, size_t cap,
                  uint64_t *offsets, uint64_t *lengths, cudaStream_t s)
 {
+    NvtxRange range("batch");
     if (count == 0) return;
     uint64_t total_cap = 0;
     for (size_t r = 0; r < count; r++) {

@@ -15,6 +15,8 @@
 
 #include "catalan.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace cat {
 
 // ----------------------------------------------------------------- errors
@@ -396,6 +398,15 @@ inline Sink plain_sink(uint32_t *out, size_t out_tstride, size_t out_len)
 {
     return Sink{out, out_tstride, out_len, false, nullptr, 0, 0};
 }
+
+// An NVTX range over a scope (phases and tree levels show up by name in
+// profilers; no cost without one attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Fills h[kTwTotal] with the twiddle tables of all sets (host side).
 constexpr size_t kTwTotal = (size_t)kNumSets * kNumPrimes * 2 * kTwPerDir;

@@ -109,6 +109,7 @@ static std::vector<uint32_t> leaf_power()
 int to_decimal_dev(Ctx &c, const uint32_t *x, size_t n, char *out, size_t cap, size_t *needed,
                    cudaStream_t s)
 {
+    NvtxRange range("to_decimal");
     n = n ? normalized_length(c, x, n, s) : 0;
     if (n == 0) {
         *needed = 1;

@@ -425,6 +425,7 @@ void factor(Ctx &c, uint64_t n, int kind, cat_factorization *out, cudaStream_t s
 // the binomial kinds, n for n!, the largest term of a ratio).
 void factor_ratio(Ctx &c, const Ratio &r, cat_factorization *out, cudaStream_t s)
 {
+    NvtxRange range("phase1: sieve, exponents, grouping");
     *out = cat_factorization{};
     const int kind = r.kind;
     const uint64_t n = r.n;

@@ -195,7 +195,7 @@ int cat_server_create(int device, size_t hbm_budget_bytes, int workers, size_t m
     try {
         for (int i = 0; i < workers; i++) {
             auto w = std::make_unique<Worker>();
-            cat::ctx_init(w->ctx, device, 0);
+            cat::ctx_init(w->ctx, device, hbm_budget_bytes);  // hard cap per worker
             cat::check_cuda(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking),
                             "cudaStreamCreateWithFlags");
             sv->workers.push_back(std::move(w));
@@ -217,6 +217,10 @@ int cat_server_submit(cat_server *sv, int kind, uint64_t n, uint64_t *ticket)
 {
     if (!sv || !ticket || n >= (1ull << 31) || kind < CAT_CATALAN || kind > CAT_FACTORIAL)
         return CAT_EINVAL;
+    // admission denial: a request whose estimated footprint alone exceeds the
+    // whole budget is never queued
+    if (sv->budget && cat::bound_limbs(n, kind) * kFootprintPerLimb > sv->budget)
+        return CAT_ENOMEM;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (sv->stop) return CAT_EINVAL;

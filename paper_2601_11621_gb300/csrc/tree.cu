@@ -117,12 +117,14 @@ void mul_into(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb
 
 Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s)
 {
+    NvtxRange range("product tree");
     if (count == 0) return make_one(c, s);
     size_t slot = kLeafSlot;
     size_t nodes = (count + kLeafSlot - 1) / kLeafSlot;
     DevBuf<uint32_t> cur(c, nodes * slot, s);
     leaf_level(c, values, count, cur.get(), nodes, s);
     while (nodes > 1) {
+        NvtxRange level("tree level");
         const size_t nprod = nodes / 2, odd = nodes & 1, nn = nprod + odd, ns = 2 * slot;
         DevBuf<uint32_t> nxt(c, nn * ns, s);
         if (slot > c.comba_max_slot || !comba_level(c, cur.get(), slot, nprod, nxt.get(), s))
@@ -165,6 +167,7 @@ static Big mul_big(Ctx &c, const Big &x, const Big &y, cudaStream_t s)
 // one forward transform.
 Big power(Ctx &c, const uint32_t *a, size_t na, uint64_t e, cudaStream_t s)
 {
+    NvtxRange range("power");
     na = normalized_length(c, a, na, s);
     if (e == 0) return make_one(c, s);
     if (na == 0) return copy_big(c, a, 0, s);
@@ -232,6 +235,7 @@ static Big reconstruct_bits(Ctx &c, const cat_factorization *f, cudaStream_t s)
 // first, so intermediates stay as short as possible).
 Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s)
 {
+    NvtxRange range("phase2: reconstruction");
     if (f->num_groups > kManyGroups) return reconstruct_bits(c, f, s);
     std::vector<Big> P;
     for (uint64_t g = 0; g < f->num_groups; g++) {
