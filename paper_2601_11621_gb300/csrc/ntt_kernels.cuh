@@ -16,34 +16,42 @@
 
 __host__ __device__ constexpr int rounds_of(int lr) { return (lr + 3) / 4; }
 
-// size of DIF round rd (counted from the top stage bits); when the stages do
-// not split evenly the last rounds take the extra ones, so that the round at
-// stage bits [0, E) (which carries the column twiddles) is the largest
+// size of DIF round rd of nr rounds (counted from the top stage bits); when
+// the stages do not split evenly the last rounds take the extra ones, so that
+// the round at stage bits [0, E) (which carries the column twiddles) is the
+// largest
+__host__ __device__ constexpr int round_size(int lr, int rd, int nr)
+{
+    return lr / nr + (rd >= nr - lr % nr ? 1 : 0);
+}
 __host__ __device__ constexpr int round_size(int lr, int rd)
 {
-    return lr / rounds_of(lr) + (rd >= rounds_of(lr) - lr % rounds_of(lr) ? 1 : 0);
+    return round_size(lr, rd, rounds_of(lr));
 }
 
 // lowest stage bit of DIF round rd
-__host__ __device__ constexpr int dif_base(int lr, int rd)
+__host__ __device__ constexpr int dif_base(int lr, int rd, int nr)
 {
     int b = lr;
-    for (int j = 0; j <= rd; j++) b -= round_size(lr, j);
+    for (int j = 0; j <= rd; j++) b -= round_size(lr, j, nr);
     return b;
 }
+__host__ __device__ constexpr int dif_base(int lr, int rd) { return dif_base(lr, rd, rounds_of(lr)); }
 
 // DIT round rd (counted from the bottom) mirrors DIF round NR-1-rd
-__host__ __device__ constexpr int dit_size(int lr, int rd)
+__host__ __device__ constexpr int dit_size(int lr, int rd, int nr)
 {
-    return round_size(lr, rounds_of(lr) - 1 - rd);
+    return round_size(lr, nr - 1 - rd, nr);
 }
+__host__ __device__ constexpr int dit_size(int lr, int rd) { return dit_size(lr, rd, rounds_of(lr)); }
 
-__host__ __device__ constexpr int dit_base(int lr, int rd)
+__host__ __device__ constexpr int dit_base(int lr, int rd, int nr)
 {
     int b = 0;
-    for (int j = 0; j < rd; j++) b += dit_size(lr, j);
+    for (int j = 0; j < rd; j++) b += dit_size(lr, j, nr);
     return b;
 }
+__host__ __device__ constexpr int dit_base(int lr, int rd) { return dit_base(lr, rd, rounds_of(lr)); }
 
 // Shared-memory address swizzle: the bank bits of address a are XORed with a
 // GF(2)-linear image f(t) of its row-of-32 index t = (a >> 5) mod 32, f
@@ -266,13 +274,13 @@ __host__ __device__ constexpr int bitrev_c(int j, int bits)
 // W0 U^bitrev_E(k), W0 = w^(col bitrev_LR(base)), U = w^(col 2^(LR - E)) (in
 // units of the root order, hence the shift), so a group takes two table
 // products and one Montgomery product per point to step through the powers.
-template <int LR, int PS>
+template <int LR, int PS, int NR = rounds_of(LR)>
 struct ColTw {
     const uint2 *T;
     uint32_t q, qinv;
     int shift;   // log2(root order) - m
     uint32_t u;  // U of this thread's column, when it has one column
-    static constexpr int E = round_size(LR, rounds_of(LR) - 1);
+    static constexpr int E = round_size(LR, NR - 1, NR);
     static constexpr bool kOneColumn = (1 << col_log_c(LR)) <= kColThreads;
     __device__ __forceinline__ uint32_t step_of(uint32_t gcol) const
     {
@@ -317,11 +325,11 @@ struct ColOutTw {
 };
 
 // Inverse pass input: element (row, col) times w_M^-(col * bitrev(row)).
-template <int LR, int PS>
+template <int LR, int PS, int NR = rounds_of(LR)>
 struct ColInTw {
     const uint32_t *p;
     uint32_t S, col0;
-    ColTw<LR, PS> tw;
+    ColTw<LR, PS, NR> tw;
     template <int E, int B, int NA>
     __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
@@ -388,7 +396,9 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
 {
     extern __shared__ uint32_t sm[];
     constexpr int LC = col_log_c(LR), C = 1 << LC;
-    constexpr int NR = rounds_of(LR);
+    // 2^4-point columns in two rounds of two stages: a single 16-value round
+    // kept a 512-thread block at one per SM (measured faster split)
+    constexpr int NR = LR == 4 ? 2 : rounds_of(LR);
     const int p = blockIdx.y;
     const uint32_t q = c_q[PS][p];
     const size_t Sr = (size_t)1 << (a.m - LR);
@@ -397,22 +407,23 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
     const size_t col0 = (blockIdx.x % groups) << LC;
     uint32_t *base = a.data + p * a.pstride + (blk << a.m);
     const uint2 *Ti = tw_table(a.tw, PS, p, 1);
-    ColTw<LR, PS> tw{Ti, q, c_qinv[PS][p], set_log_root(PS) - a.m, 0u};
+    ColTw<LR, PS, NR> tw{Ti, q, c_qinv[PS][p], set_log_root(PS) - a.m, 0u};
     tw.init((uint32_t)col0);
-    const ColInTw<LR, PS> in{base, (uint32_t)Sr, (uint32_t)col0, tw};
+    const ColInTw<LR, PS, NR> in{base, (uint32_t)Sr, (uint32_t)col0, tw};
     const ColOut out{base, (uint32_t)Sr, (uint32_t)col0};
     if constexpr (NR == 1) {
         round_io<LR, C, 0, LR, false, 1, true, PS>(in, out, Ti, q);
     } else {
         const SmemIO<LR, C, true> sio{sm};
-        round_io<LR, C, 0, dit_size(LR, 0), false, 1, true, PS>(in, sio, Ti, q);
+        round_io<LR, C, 0, dit_size(LR, 0, NR), false, 1, true, PS>(in, sio, Ti, q);
         __syncthreads();
         if constexpr (NR == 3) {
-            round_io<LR, C, dit_base(LR, 1), dit_size(LR, 1), false, 1, true, PS>(sio, sio, Ti, q);
+            round_io<LR, C, dit_base(LR, 1, NR), dit_size(LR, 1, NR), false, 1, true, PS>(
+                sio, sio, Ti, q);
             __syncthreads();
         }
-        round_io<LR, C, dit_base(LR, NR - 1), dit_size(LR, NR - 1), false, 1, true, PS>(sio, out,
-                                                                                        Ti, q);
+        round_io<LR, C, dit_base(LR, NR - 1, NR), dit_size(LR, NR - 1, NR), false, 1, true, PS>(
+            sio, out, Ti, q);
     }
 }
 
