@@ -434,8 +434,25 @@ struct FusedArgs {
 constexpr int kFusedMaxLog = 12;
 constexpr int kFusedThreads = 512;
 
-// One product per block: three forward/pointwise/inverse rounds (one per
-// prime) in shared memory, then remaindering and carries over one tile.
+// The one-block multiply's first forward round input: raw limbs (shared
+// memory, unswizzled) reduced into the forward range; column 0 is operand a,
+// column 1 operand b (a again when squaring).
+struct RawIn {
+    const uint32_t *a, *b;
+    uint32_t q, wp1;
+    template <int E, int B, int NA>
+    __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
+    {
+        const uint32_t *r = c ? b : a;
+#pragma unroll
+        for (int k = 0; k < (1 << E); k++) x[0][k] = reduce_in<0>(r[base + (k << B)], q, wp1);
+    }
+};
+
+// One product per block: per prime the forward transforms of both operands,
+// the pointwise product and the inverse transform in shared memory (register
+// rounds, the middle one fused as in the row pass), then remaindering and
+// carries over one tile.
 // Layout (words): residues R0 [0,L) R1 [L,2L) R2 [2L,3L); raw A shares R2's
 // space (it is last read before R2 is written), raw B [3L,4L), transform pair
 // XY [4L,6L).  Every thread owns a run of eight coefficients for the carries
@@ -461,23 +478,66 @@ __global__ void __launch_bounds__(kFusedThreads, 2) ntt_mul_fused(FusedArgs a)
         rawB[i] = (gb && (size_t)i < a.b_len) ? gb[i] : 0u;
     }
     __syncthreads();
+    constexpr int NR = rounds_of(LR);
 #pragma unroll 1
     for (int p = 0; p < kNumPrimes; p++) {
         const uint32_t q = c_q[0][p], qinv = c_qinv[0][p], wp1 = c_wp1[0][p];
         const uint2 *T = tw_table(a.tw, 0, p, 0);
         const uint2 *Ti = tw_table(a.tw, 0, p, 1);
         const uint2 sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
-        for (int i = threadIdx.x; i < L; i += blockDim.x) {
-            X[swz(i)] = reduce_in<0>(rawA[i], q, wp1);
-            Y[swz(i)] = reduce_in<0>(gb ? rawB[i] : rawA[i], q, wp1);
-        }
-        __syncthreads();
-        dif_smem<LR, 2, 0>(X, T, q);  // X and Y as two arrays
         uint32_t *Z = Rr[p];
-        // elementwise in the swizzled space: Z, X, Y share the permutation
-        for (int i = threadIdx.x; i < L; i += blockDim.x) Z[i] = pmul<0>(X[i], Y[i], sc, q, qinv);
-        __syncthreads();
-        dit_smem<LR, 1, 0>(Z, Ti, q);
+        if constexpr (NR == 1) {
+            // up to 16 points: reduce, transform both, multiply, transform back
+            for (int i = threadIdx.x; i < L; i += blockDim.x) {
+                X[swz(i)] = reduce_in<0>(rawA[i], q, wp1);
+                Y[swz(i)] = reduce_in<0>(gb ? rawB[i] : rawA[i], q, wp1);
+            }
+            __syncthreads();
+            dif_smem<LR, 2, 0>(X, T, q);  // X and Y as two arrays
+            // elementwise in the swizzled space: Z, X, Y share the permutation
+            for (int i = threadIdx.x; i < L; i += blockDim.x)
+                Z[i] = pmul<0>(X[i], Y[i], sc, q, qinv);
+            __syncthreads();
+            dit_smem<LR, 1, 0>(Z, Ti, q);
+        } else {
+            // The first forward round reads the raw limbs and reduces them; X and
+            // Y are two arrays of the round (twice the groups of one pair).
+            const SmemIO<LR, 2, false> xy{X};
+            const RawIn ri{rawA, gb ? rawB : rawA, q, wp1};
+            round_io<LR, 2, dif_base(LR, 0), round_size(LR, 0), true, 1, false, 0>(ri, xy, T, q);
+            __syncthreads();
+            if constexpr (NR == 3) {
+                round_io<LR, 2, dif_base(LR, 1), round_size(LR, 1), true, 1, false, 0>(xy, xy, T,
+                                                                                      q);
+                __syncthreads();
+            }
+            // The last forward round of both operands, the pointwise product and
+            // the first inverse round share one register round (their stage bits
+            // coincide), as in the row pass.
+            constexpr int EL = round_size(LR, NR - 1);
+            static_assert(EL == dit_size(LR, 0), "mirrored rounds");
+            const SmemIO<LR, 1, false> pair{X};  // NA = 2: X and Y = X + L
+            const SmemIO<LR, 1, false> zs{Z};
+            for (int g = threadIdx.x; g < (L >> EL); g += blockDim.x) {
+                const int base = g << EL;
+                uint32_t x[2][1 << EL];
+                pair.template load<EL, 0, 2>(x, base, 0);
+                dif_stages<EL, 0, 2, 0>(x, 0, T, q);
+                uint32_t zz[1][1 << EL];
+#pragma unroll
+                for (int j = 0; j < (1 << EL); j++) zz[0][j] = pmul<0>(x[0][j], x[1][j], sc, q, qinv);
+                dit_stages<EL, 0, 1, 0>(zz, 0, Ti, q);
+                zs.template store<EL, 0, 1>(zz, base, 0);
+            }
+            __syncthreads();
+            round_io<LR, 1, dit_base(LR, 1), dit_size(LR, 1), false, 1, false, 0>(zs, zs, Ti, q);
+            __syncthreads();
+            if constexpr (NR == 3) {
+                round_io<LR, 1, dit_base(LR, 2), dit_size(LR, 2), false, 1, false, 0>(zs, zs, Ti,
+                                                                                      q);
+                __syncthreads();
+            }
+        }
     }
     // each thread remainders its run of eight coefficients straight from the
     // swizzled residues (for a fixed i the lanes' words 8 t + i fall in
