@@ -56,6 +56,11 @@ struct Garner {
     static constexpr uint32_t inv_q0q1_mod_q2 =
         to_mont_c(powmod_u32(mulmod_u64(q0, q1, q2), q2 - 2, q2), q2);
     static_assert(q0 < q1 && q1 < q2, "Garner order assumes q0 < q1 < q2");
+    // the same three factors as plain residues with Shoup's companions
+    static constexpr uint32_t s1 = powmod_u32(q0 % q1, q1 - 2, q1), s1p = shoup_c(s1, q1);
+    static constexpr uint32_t s2 = q0 % q2, s2p = shoup_c(s2, q2);
+    static constexpr uint32_t s3 = powmod_u32(mulmod_u64(q0, q1, q2), q2 - 2, q2),
+                              s3p = shoup_c(s3, q2);
 };
 
 // Pointwise scale 2^-n folded into the product's second factor: 2^32 2^-n mod
@@ -135,15 +140,32 @@ __device__ __forceinline__ void crt3(uint32_t r0, uint32_t r1, uint32_t r2, uint
                                      uint32_t &c1, uint32_t &c2)
 {
     using G = Garner<PS>;
-    constexpr bool S = G::q2 < (1u << 31);
-    r0 = final_red<PS>(r0, G::q0);
-    r1 = final_red<PS>(r1, G::q1);
-    r2 = final_red<PS>(r2, G::q2);
-    const uint32_t x0 = r0;  // < q0 < q1 < q2
-    const uint32_t x1 = mont<S>(sub_m<S>(r1, x0, G::q1), G::inv_q0_mod_q1, G::q1, G::qinv1);
-    uint32_t t = sub_m<S>(r2, x0, G::q2);
-    t = sub_m<S>(t, mont<S>(x1, G::q0_mod_q2, G::q2, G::qinv2), G::q2);
-    const uint32_t x2 = mont<S>(t, G::inv_q0q1_mod_q2, G::q2, G::qinv2);
+    uint32_t x0, x1, x2;
+    if constexpr (PS == 2) {
+        x0 = r0;  // < q0 < q1 < q2
+        x1 = mont_mul(sub_mod(r1, x0, G::q1), G::inv_q0_mod_q1, G::q1, G::qinv1);
+        uint32_t t = sub_mod(r2, x0, G::q2);
+        t = sub_mod(t, mont_mul(x1, G::q0_mod_q2, G::q2, G::qinv2), G::q2);
+        x2 = mont_mul(t, G::inv_q0q1_mod_q2, G::q2, G::qinv2);
+    } else {
+        // Shoup products take any 32-bit input, so the differences go in
+        // unreduced: set 0's lazy residues need only r0 fully reduced (it is
+        // the exact low digit) and r1, r2 below 2q; set 1's are below q.
+        x0 = final_red<PS>(r0, G::q0);
+        if constexpr (PS == 0) {
+            r1 = csub(r1, 2 * G::q1);  // [0, 2 q1)
+            r2 = csub(r2, 2 * G::q2);  // [0, 2 q2)
+        }
+        // (r1 - x0) / q0 mod q1, the input in (0, 3 q1)
+        x1 = csub(shoup(r1 - x0 + G::q1, G::s1, G::s1p, G::q1), G::q1);
+        const uint32_t u = csub(shoup(x1, G::s2, G::s2p, G::q2), G::q2);  // x1 q0 mod q2
+        uint32_t t;
+        if constexpr (PS == 0)
+            t = r2 - x0 - u + 2 * G::q2;  // (0, 4 q2), below 2^32 as 4 q2 < 2^32
+        else
+            t = sub_m<true>(r2, x0, G::q2) - u + G::q2;  // (0, 2 q2)
+        x2 = csub(shoup(t, G::s3, G::s3p, G::q2), G::q2);
+    }
     const uint64_t y = (uint64_t)G::q1 * x2 + x1;                 // < q1 q2
     const uint64_t lo = (uint64_t)G::q0 * (uint32_t)y + x0;
     const uint64_t hi = (uint64_t)G::q0 * (uint32_t)(y >> 32) + (lo >> 32);
