@@ -19,6 +19,12 @@
 // Grouping.  (e, p) pairs are sorted stably by e (least-significant-digit
 // radix sort, pairs with e = 0 dropped in the first pass), so primes stay
 // ascending within each group; group starts are then collected.
+//
+// Binomial kinds.  For C(n) and C(2n, n) every prime above sqrt(2n) has
+// exponent 0 or 1 (one base-p carry), found with one division inside the
+// sieve; the sieve keeps only the primes with exponent 1 and they are written
+// in order straight into the e = 1 group.  Only the seed primes (below
+// sqrt(2n) <= 65536) go through Legendre's formula and the radix grouping.
 #include "cat_internal.cuh"
 #include "legendre.cuh"
 
@@ -85,6 +91,12 @@ struct SieveArgs {
     uint32_t imax;          // largest odd index i with 2i+1 <= limit
     uint32_t *bits;         // out: per segment, bit set = prime
     uint32_t *counts;       // out: primes per segment
+    // unit_kind >= 0: keep only the primes p > root (p^2 > 2 unit_n) whose
+    // exponent in the quantity of that kind is 1 (all others are 0 there);
+    // counts then count the kept primes, and *total gets every odd prime.
+    int unit_kind;
+    uint32_t unit_n, root;
+    unsigned int *total;
 };
 
 __constant__ uint32_t c_small_primes[10] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
@@ -92,7 +104,7 @@ __constant__ uint32_t c_small_primes[10] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31}
 __global__ void __launch_bounds__(kSieveThreads) sieve_segments(SieveArgs a)
 {
     __shared__ uint32_t bm[kSegWords];
-    __shared__ uint32_t red[kSieveThreads / 32];
+    __shared__ uint32_t red[kSieveThreads / 32], red_all[kSieveThreads / 32];
     const uint32_t seg = blockIdx.x;
     const uint32_t ibase = seg * (uint32_t)kSegBits;  // odd index of bit 0
     // primes 3..31: bit b of word w is odd number x = 2(ibase + 32 w + b) + 1;
@@ -143,23 +155,43 @@ __global__ void __launch_bounds__(kSieveThreads) sieve_segments(SieveArgs a)
         bm[0] = w0;
     }
     __syncthreads();
-    uint32_t cnt = 0;
+    uint32_t cnt = 0, all = 0;
     uint32_t *out = a.bits + (size_t)seg * kSegWords;
     for (int w = threadIdx.x; w < kSegWords; w += blockDim.x) {
         uint32_t v = ~bm[w];
         const uint64_t i0 = (uint64_t)ibase + 32u * w;
         if (i0 > a.imax) v = 0;
         else if (i0 + 31 > a.imax) v &= (uint32_t)((2ull << (a.imax - i0)) - 1);
+        if (a.unit_kind >= 0) {
+            all += __popc(v);
+            uint32_t keep = 0;
+            for (uint32_t m = v; m; m &= m - 1) {
+                const int b = __ffs(m) - 1;
+                const uint32_t p = (uint32_t)(2 * (i0 + b) + 1);
+                if (p > a.root && unit_exponent(p, a.unit_n, a.unit_kind)) keep |= 1u << b;
+            }
+            v = keep;
+        }
         out[w] = v;
         cnt += __popc(v);
     }
-    for (int off = 16; off; off >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, off);
-    if (lane == 0) red[wid] = cnt;
+    for (int off = 16; off; off >>= 1) {
+        cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+        all += __shfl_down_sync(0xffffffffu, all, off);
+    }
+    if (lane == 0) {
+        red[wid] = cnt;
+        red_all[wid] = all;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int k = 0; k < nw; k++) t += red[k];
+        uint32_t t = 0, ta = 0;
+        for (int k = 0; k < nw; k++) {
+            t += red[k];
+            ta += red_all[k];
+        }
         a.counts[seg] = t;
+        if (a.unit_kind >= 0) atomicAdd(a.total, ta);
     }
 }
 
@@ -347,6 +379,74 @@ __global__ void group_starts(const uint64_t *items, size_t count, uint64_t *star
     }
 }
 
+// One block per segment: the primes of its bitmap in ascending order, written
+// to primes[first + seg_offsets[seg] + ...]; with_two also puts 2 at primes[0].
+// Each warp owns 1024 consecutive words and takes them 32 at a time (one word
+// a lane): a warp scan of the bit counts places each lane's primes in a
+// per-warp shared stage, which the warp then copies out contiguously.
+constexpr int kExpandThreads = 256;
+constexpr int kExpandWarps = kExpandThreads / 32;
+constexpr int kWordsPerWarp = kSegWords / kExpandWarps;  // 1024
+constexpr int kExpandIters = kWordsPerWarp / 32;          // 32
+
+__global__ void __launch_bounds__(kExpandThreads) expand_primes(const uint32_t *bits,
+                                                               const uint32_t *seg_offsets,
+                                                               uint32_t *primes, uint32_t first,
+                                                               int with_two)
+{
+    __shared__ uint32_t stage[kExpandWarps][32 * 32];
+    __shared__ uint32_t wsum[kExpandWarps];
+    const uint32_t seg = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t word0 = (uint32_t)wid * kWordsPerWarp;
+    const uint32_t *b = bits + (size_t)seg * kSegWords + word0;
+    uint32_t w[kExpandIters];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int it = 0; it < kExpandIters; it++) {
+        w[it] = b[it * 32 + lane];
+        cnt += __popc(w[it]);
+    }
+    for (int off = 16; off; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if (lane == 0) wsum[wid] = cnt;
+    __syncthreads();
+    size_t pos = (size_t)seg_offsets[seg] + first;
+    for (int k = 0; k < wid; k++) pos += wsum[k];
+    uint32_t *st = stage[wid];
+#pragma unroll
+    for (int it = 0; it < kExpandIters; it++) {
+        const uint32_t c = __popc(w[it]);
+        uint32_t incl = c;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t at = incl - c;
+        const uint32_t ibase = seg * (uint32_t)kSegBits + 32u * (word0 + it * 32 + lane);
+        for (uint32_t m = w[it]; m; m &= m - 1) st[at++] = 2 * (ibase + __ffs(m) - 1) + 1;
+        __syncwarp();
+        for (uint32_t k = lane; k < tot; k += 32) primes[pos + k] = st[k];
+        pos += tot;
+        __syncwarp();
+    }
+    if (with_two && seg == 0 && threadIdx.x == 0) primes[0] = 2;
+}
+
+// The exponents of the seed primes (all primes <= sqrt(2n)), one thread each.
+__global__ void seed_items(const uint32_t *seeds, uint32_t ns, Ratio r, uint64_t *items,
+                           unsigned int *max_e, unsigned int *negative)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const uint32_t p = seeds[i];
+    const int64_t e = exponent_of(p, r);
+    if (e < 0) atomicOr(negative, 1u);
+    const uint32_t eu = e < 0 ? 0u : (uint32_t)e;
+    atomicMax(max_e, eu);
+    items[i] = ((uint64_t)eu << 32) | p;
+}
+
 // ------------------------------------------------------------ host side
 
 static uint64_t isqrt64(uint64_t x)
@@ -359,23 +459,30 @@ static uint64_t isqrt64(uint64_t x)
 
 // The segmented sieve up to `limit` (>= 2): per-segment bitmaps of the odd
 // primes and the exclusive scan of their counts.  sieved = pi(limit).
+// With unit_kind >= 0 (a binomial kind of n, limit = 2n) the bitmaps keep only
+// the primes above sqrt(2n) with exponent 1, the offsets scan their counts
+// (kept in total), and the seeds are exactly the primes up to sqrt(2n).
 struct SieveOut {
-    DevBuf<uint32_t> bits, offsets;
-    uint32_t nsegs = 0;
-    uint64_t sieved = 0;
+    DevBuf<uint32_t> bits, offsets, seeds;
+    uint32_t nsegs = 0, nseeds = 0;
+    uint64_t sieved = 0, kept = 0;
 };
 
-static SieveOut run_sieve(Ctx &c, uint64_t limit, cudaStream_t s)
+static SieveOut run_sieve(Ctx &c, uint64_t limit, cudaStream_t s, int unit_kind = -1,
+                          uint32_t unit_n = 0)
 {
     SieveOut o;
     const uint64_t root = isqrt64(limit);
-    DevBuf<uint32_t> seeds(c, 8192, s);
-    DevBuf<uint32_t> nseeds(c, 1, s);
+    o.seeds = DevBuf<uint32_t>(c, 8192, s);
+    DevBuf<uint32_t> &seeds = o.seeds;
+    DevBuf<uint32_t> nseeds(c, 2, s);
+    CAT_CUDA(cudaMemsetAsync(nseeds.get(), 0, 8, s));
     seed_sieve<<<1, 1024, 0, s>>>((uint32_t)root, seeds.get(), nseeds.get());
     CAT_LAUNCH("seed_sieve");
     uint32_t ns = 0;
     CAT_CUDA(cudaMemcpyAsync(&ns, nseeds.get(), 4, cudaMemcpyDeviceToHost, s));
     CAT_CUDA(cudaStreamSynchronize(s));
+    o.nseeds = ns;
     std::vector<uint32_t> hs(ns);
     if (ns)
         CAT_CUDA(cudaMemcpyAsync(hs.data(), seeds.get(), 4 * ns, cudaMemcpyDeviceToHost, s));
@@ -394,7 +501,8 @@ static SieveOut run_sieve(Ctx &c, uint64_t limit, cudaStream_t s)
     o.nsegs = imax / kSegBits + 1;
     o.bits = DevBuf<uint32_t>(c, (size_t)o.nsegs * kSegWords, s);
     o.offsets = DevBuf<uint32_t>(c, o.nsegs, s);
-    SieveArgs sa{odd, i_med, i_large, nodd, imax, o.bits.get(), o.offsets.get()};
+    SieveArgs sa{odd, i_med, i_large, nodd, imax, o.bits.get(), o.offsets.get(),
+                 unit_kind, unit_n, (uint32_t)root, nseeds.get() + 1};
     const int tok = prof_begin(c, "sieve_segments", s);
     sieve_segments<<<o.nsegs, kSieveThreads, 0, s>>>(sa);
     CAT_LAUNCH("sieve_segments");
@@ -403,11 +511,13 @@ static SieveOut run_sieve(Ctx &c, uint64_t limit, cudaStream_t s)
     CAT_CUDA(cudaMemcpyAsync(&last_count, o.offsets.get() + o.nsegs - 1, 4,
                              cudaMemcpyDeviceToHost, s));
     exclusive_scan_u32(c, o.offsets.get(), o.nsegs, s);
-    uint32_t last_off = 0;
+    uint32_t last_off = 0, total = 0;
     CAT_CUDA(cudaMemcpyAsync(&last_off, o.offsets.get() + o.nsegs - 1, 4,
                              cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaMemcpyAsync(&total, nseeds.get() + 1, 4, cudaMemcpyDeviceToHost, s));
     CAT_CUDA(cudaStreamSynchronize(s));
-    o.sieved = (uint64_t)last_off + last_count + 1;  // plus the prime 2
+    o.kept = (uint64_t)last_off + last_count;
+    o.sieved = (unit_kind >= 0 ? (uint64_t)total : o.kept) + 1;  // plus the prime 2
     return o;
 }
 
@@ -419,6 +529,138 @@ void factor(Ctx &c, uint64_t n, int kind, cat_factorization *out, cudaStream_t s
     r.kind = kind;
     r.n = (uint32_t)n;
     factor_ratio(c, r, out, s);
+}
+
+// (e, p) items with e = 0 dropped, grouped by e: primes ascending within each
+// group, groups by ascending e, offs[k] = start of group k (offs has one more
+// entry than exps, ending in count).
+struct Grouped {
+    DevBuf<uint32_t> primes;
+    std::vector<uint64_t> exps, offs{0};
+    uint64_t count = 0;
+};
+
+static Grouped group_items(Ctx &c, DevBuf<uint64_t> &items, size_t count, uint32_t max_e,
+                           cudaStream_t s)
+{
+    Grouped g;
+    // stable radix sort by e, dropping e = 0
+    int ebits = 0;
+    while (ebits < 32 && (max_e >> ebits)) ebits++;
+    DevBuf<uint64_t> alt(c, std::max<size_t>(count, 1), s);
+    uint64_t *src = items.get(), *dst = alt.get();
+    int tok;
+    for (int shift = 0, pass = 0; pass == 0 || shift < ebits; pass++) {
+        const int bitsd = std::max(1, std::min(8, ebits - shift));
+        const size_t tiles = (count + kRsTile - 1) / kRsTile;
+        if (tiles == 0) break;
+        const size_t nbins = (size_t)1 << bitsd;
+        DevBuf<uint32_t> cnt(c, nbins * tiles, s);
+        RsArgs ra{src, dst, count, shift, bitsd, pass == 0 ? 1 : 0, cnt.get(), tiles};
+        tok = prof_begin(c, "rs_histogram", s);
+        rs_histogram<<<(unsigned)tiles, kRsThreads, 0, s>>>(ra);
+        CAT_LAUNCH("rs_histogram");
+        prof_end(c, tok, s, 8.0 * (double)count);
+        uint32_t lastc = 0, lasto = 0;
+        CAT_CUDA(cudaMemcpyAsync(&lastc, cnt.get() + nbins * tiles - 1, 4,
+                                 cudaMemcpyDeviceToHost, s));
+        exclusive_scan_u32(c, cnt.get(), nbins * tiles, s);
+        CAT_CUDA(cudaMemcpyAsync(&lasto, cnt.get() + nbins * tiles - 1, 4,
+                                 cudaMemcpyDeviceToHost, s));
+        tok = prof_begin(c, "rs_scatter", s);
+        rs_scatter<<<(unsigned)tiles, kRsThreads, 0, s>>>(ra);
+        CAT_LAUNCH("rs_scatter");
+        prof_end(c, tok, s, 16.0 * (double)count);
+        CAT_CUDA(cudaStreamSynchronize(s));
+        count = (size_t)lasto + lastc;
+        std::swap(src, dst);
+        shift += bitsd;
+        if (ebits == 0) break;
+    }
+    g.count = count;
+    if (count == 0) return g;
+    g.primes = DevBuf<uint32_t>(c, count, s);
+    DevBuf<uint64_t> starts(c, 2 * count, s);
+    DevBuf<unsigned int> nst(c, 1, s);
+    CAT_CUDA(cudaMemsetAsync(nst.get(), 0, 4, s));
+    group_starts<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(src, count, starts.get(),
+                                                                  nst.get(), g.primes.get());
+    CAT_LAUNCH("group_starts");
+    unsigned int ng = 0;
+    CAT_CUDA(cudaMemcpyAsync(&ng, nst.get(), 4, cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    std::vector<uint64_t> hst(2 * (size_t)ng);
+    CAT_CUDA(cudaMemcpyAsync(hst.data(), starts.get(), 16 * (size_t)ng, cudaMemcpyDeviceToHost,
+                             s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    std::vector<std::pair<uint64_t, uint64_t>> gs(ng);
+    for (size_t k = 0; k < ng; k++) gs[k] = {hst[2 * k], hst[2 * k + 1]};
+    std::sort(gs.begin(), gs.end());
+    g.offs.clear();
+    for (auto &x : gs) {
+        g.exps.push_back(x.first);
+        g.offs.push_back(x.second);
+    }
+    g.offs.push_back(count);
+    return g;
+}
+
+// Catalan or central binomial kinds with n >= 2.  Every prime above sqrt(2n)
+// has exponent 0 or 1; the sieve keeps those with 1 and they are written in
+// order straight into the e = 1 group, after the seed primes with e = 1.  The
+// seed primes (<= sqrt(2n), fewer than 6600) take Legendre's formula and the
+// radix grouping; their groups with e >= 2 follow.
+static void factor_unit(Ctx &c, const Ratio &r, uint64_t limit, DevBuf<uint32_t> &primes_out,
+                        std::vector<uint64_t> &h_exps, std::vector<uint64_t> &h_offs,
+                        uint64_t &sieved, uint64_t &npos, cudaStream_t s)
+{
+    SieveOut sv = run_sieve(c, limit, s, r.kind, r.n);
+    sieved = sv.sieved;
+    const uint32_t ns = sv.nseeds;
+    DevBuf<uint64_t> items(c, std::max<uint32_t>(ns, 1), s);
+    DevBuf<unsigned int> flags(c, 2, s);
+    CAT_CUDA(cudaMemsetAsync(flags.get(), 0, 8, s));
+    if (ns) {
+        seed_items<<<(ns + 255) / 256, 256, 0, s>>>(sv.seeds.get(), ns, r, items.get(),
+                                                    flags.get(), flags.get() + 1);
+        CAT_LAUNCH("seed_items");
+    }
+    unsigned int hf[2];
+    CAT_CUDA(cudaMemcpyAsync(hf, flags.get(), 8, cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaStreamSynchronize(s));
+    if (hf[1]) fail(CAT_ENOTINTEGRAL, "a prime exponent is negative");
+    Grouped g = group_items(c, items, ns, hf[0], s);
+    const uint64_t nl = sv.kept;
+    const uint64_t n1 = (!g.exps.empty() && g.exps[0] == 1) ? g.offs[1] : 0;
+    npos = g.count + nl;
+    h_exps.clear();
+    h_offs.assign(1, 0);
+    if (npos == 0) return;
+    primes_out = DevBuf<uint32_t>(c, npos, s);
+    uint32_t *d = primes_out.get();
+    if (n1)
+        CAT_CUDA(cudaMemcpyAsync(d, g.primes.get(), 4 * n1, cudaMemcpyDeviceToDevice, s));
+    if (nl) {
+        const int tok = prof_begin(c, "expand_primes", s);
+        expand_primes<<<sv.nsegs, kExpandThreads, 0, s>>>(sv.bits.get(), sv.offsets.get(),
+                                                           d + n1, 0, 0);
+        CAT_LAUNCH("expand_primes");
+        prof_end(c, tok, s, 4.0 * (double)sv.nsegs * kSegWords + 4.0 * (double)nl);
+    }
+    if (g.count > n1)
+        CAT_CUDA(cudaMemcpyAsync(d + n1 + nl, g.primes.get() + n1, 4 * (g.count - n1),
+                                 cudaMemcpyDeviceToDevice, s));
+    h_offs.clear();
+    if (n1 + nl) {
+        h_exps.push_back(1);
+        h_offs.push_back(0);
+    }
+    for (size_t k = n1 ? 1 : 0; k < g.exps.size(); k++) {
+        h_exps.push_back(g.exps[k]);
+        h_offs.push_back(g.offs[k] + nl);
+    }
+    h_offs.push_back(npos);
+    CAT_CUDA(cudaStreamSynchronize(s));  // the copies read g.primes before it is freed
 }
 
 // Phase 1 for any Ratio: primes up to the largest factorial argument (2n for
@@ -438,88 +680,34 @@ void factor_ratio(Ctx &c, const Ratio &r, cat_factorization *out, cudaStream_t s
     std::vector<uint64_t> h_exps, h_offs{0};
     DevBuf<uint32_t> primes_out;
     uint64_t sieved = 0, npos = 0;
-    if (limit >= 2) {
+    if ((kind == CAT_CATALAN || kind == CAT_CENTRAL_BINOMIAL) && n >= 2) {
+        factor_unit(c, r, limit, primes_out, h_exps, h_offs, sieved, npos, s);
+    } else if (limit >= 2) {
         SieveOut sv = run_sieve(c, limit, s);
         const uint32_t nsegs = sv.nsegs;
         sieved = sv.sieved;
-        DevBuf<uint32_t> &bits = sv.bits;
-        DevBuf<uint32_t> &counts = sv.offsets;
-        int tok;
         // exponents
         DevBuf<uint64_t> items(c, sieved, s);
         DevBuf<unsigned int> flags(c, 2, s);
         CAT_CUDA(cudaMemsetAsync(flags.get(), 0, 8, s));
-        ExpandArgs ea{bits.get(), counts.get(), r, 1, items.get(), flags.get(), flags.get() + 1};
-        tok = prof_begin(c, "expand_exponents", s);
+        ExpandArgs ea{sv.bits.get(), sv.offsets.get(), r, 1, items.get(), flags.get(),
+                      flags.get() + 1};
+        const int tok = prof_begin(c, "expand_exponents", s);
         expand_exponents<<<nsegs, kSieveThreads, 0, s>>>(ea);
         CAT_LAUNCH("expand_exponents");
         prof_end(c, tok, s, 4.0 * (double)nsegs * kSegWords + 8.0 * (double)sieved);
-        bits.reset();
-        counts.reset();
+        sv.bits.reset();
+        sv.offsets.reset();
+        sv.seeds.reset();
         unsigned int hf[2];
         CAT_CUDA(cudaMemcpyAsync(hf, flags.get(), 8, cudaMemcpyDeviceToHost, s));
         CAT_CUDA(cudaStreamSynchronize(s));
         if (hf[1]) fail(CAT_ENOTINTEGRAL, "a prime exponent is negative");
-        const uint32_t max_e = hf[0];
-        // stable radix sort by e, dropping e = 0
-        int ebits = 0;
-        while (ebits < 32 && (max_e >> ebits)) ebits++;
-        DevBuf<uint64_t> alt(c, sieved, s);
-        uint64_t *src = items.get(), *dst = alt.get();
-        size_t count = sieved;
-        for (int shift = 0, pass = 0; pass == 0 || shift < ebits; pass++) {
-            const int bitsd = std::max(1, std::min(8, ebits - shift));
-            const size_t tiles = (count + kRsTile - 1) / kRsTile;
-            if (tiles == 0) break;
-            const size_t nbins = (size_t)1 << bitsd;
-            DevBuf<uint32_t> cnt(c, nbins * tiles, s);
-            RsArgs ra{src, dst, count, shift, bitsd, pass == 0 ? 1 : 0, cnt.get(), tiles};
-            tok = prof_begin(c, "rs_histogram", s);
-            rs_histogram<<<(unsigned)tiles, kRsThreads, 0, s>>>(ra);
-            CAT_LAUNCH("rs_histogram");
-            prof_end(c, tok, s, 8.0 * (double)count);
-            uint32_t lastc = 0, lasto = 0;
-            CAT_CUDA(cudaMemcpyAsync(&lastc, cnt.get() + nbins * tiles - 1, 4,
-                                     cudaMemcpyDeviceToHost, s));
-            exclusive_scan_u32(c, cnt.get(), nbins * tiles, s);
-            CAT_CUDA(cudaMemcpyAsync(&lasto, cnt.get() + nbins * tiles - 1, 4,
-                                     cudaMemcpyDeviceToHost, s));
-            tok = prof_begin(c, "rs_scatter", s);
-            rs_scatter<<<(unsigned)tiles, kRsThreads, 0, s>>>(ra);
-            CAT_LAUNCH("rs_scatter");
-            prof_end(c, tok, s, 16.0 * (double)count);
-            CAT_CUDA(cudaStreamSynchronize(s));
-            count = (size_t)lasto + lastc;
-            std::swap(src, dst);
-            shift += bitsd;
-            if (ebits == 0) break;
-        }
-        npos = count;
-        if (npos > 0) {
-            primes_out = DevBuf<uint32_t>(c, npos, s);
-            DevBuf<uint64_t> starts(c, 2 * npos, s);
-            DevBuf<unsigned int> nst(c, 1, s);
-            CAT_CUDA(cudaMemsetAsync(nst.get(), 0, 4, s));
-            group_starts<<<(unsigned)((npos + 255) / 256), 256, 0, s>>>(
-                src, npos, starts.get(), nst.get(), primes_out.get());
-            CAT_LAUNCH("group_starts");
-            unsigned int ng = 0;
-            CAT_CUDA(cudaMemcpyAsync(&ng, nst.get(), 4, cudaMemcpyDeviceToHost, s));
-            CAT_CUDA(cudaStreamSynchronize(s));
-            std::vector<uint64_t> hst(2 * (size_t)ng);
-            CAT_CUDA(cudaMemcpyAsync(hst.data(), starts.get(), 16 * (size_t)ng,
-                                     cudaMemcpyDeviceToHost, s));
-            CAT_CUDA(cudaStreamSynchronize(s));
-            std::vector<std::pair<uint64_t, uint64_t>> g(ng);
-            for (size_t k = 0; k < ng; k++) g[k] = {hst[2 * k], hst[2 * k + 1]};
-            std::sort(g.begin(), g.end());
-            h_offs.clear();
-            for (auto &x : g) {
-                h_exps.push_back(x.first);
-                h_offs.push_back(x.second);
-            }
-            h_offs.push_back(npos);
-        }
+        Grouped g = group_items(c, items, sieved, hf[0], s);
+        npos = g.count;
+        primes_out = std::move(g.primes);
+        h_exps = std::move(g.exps);
+        h_offs = std::move(g.offs);
     }
     const size_t ng = h_exps.size();
     DevBuf<uint64_t> d_exps(c, ng + 1, s), d_offs(c, ng + 1, s);
@@ -542,44 +730,6 @@ void factor_ratio(Ctx &c, const Ratio &r, cat_factorization *out, cudaStream_t s
     out->primes = primes_out.release();
 }
 
-// One block per segment: its primes in order (no exponents).
-__global__ void __launch_bounds__(kSieveThreads) expand_primes(const uint32_t *bits,
-                                                              const uint32_t *seg_offsets,
-                                                              uint32_t *primes)
-{
-    __shared__ uint32_t pre[kSieveThreads];
-    constexpr int kWordsPerThread = kSegWords / kSieveThreads;
-    const uint32_t seg = blockIdx.x;
-    const uint32_t *b = bits + (size_t)seg * kSegWords + threadIdx.x * kWordsPerThread;
-    uint32_t w[kWordsPerThread];
-    uint32_t cnt = 0;
-#pragma unroll
-    for (int k = 0; k < kWordsPerThread; k++) {
-        w[k] = b[k];
-        cnt += __popc(w[k]);
-    }
-    pre[threadIdx.x] = cnt;
-    __syncthreads();
-    for (int off = 1; off < kSieveThreads; off <<= 1) {
-        const uint32_t v = threadIdx.x >= (unsigned)off ? pre[threadIdx.x - off] : 0;
-        __syncthreads();
-        pre[threadIdx.x] += v;
-        __syncthreads();
-    }
-    size_t pos = (size_t)seg_offsets[seg] + pre[threadIdx.x] - cnt + 1;  // after the prime 2
-    const uint32_t ibase = seg * (uint32_t)kSegBits + threadIdx.x * kWordsPerThread * 32;
-#pragma unroll
-    for (int k = 0; k < kWordsPerThread; k++) {
-        uint32_t v = w[k];
-        while (v) {
-            const int bb = __ffs(v) - 1;
-            v &= v - 1;
-            primes[pos++] = 2 * (ibase + 32 * k + bb) + 1;
-        }
-    }
-    if (seg == 0 && threadIdx.x == 0) primes[0] = 2;
-}
-
 DevBuf<uint32_t> sieve_primes(Ctx &c, uint64_t limit, uint64_t *count, cudaStream_t s)
 {
     *count = 0;
@@ -587,8 +737,8 @@ DevBuf<uint32_t> sieve_primes(Ctx &c, uint64_t limit, uint64_t *count, cudaStrea
     SieveOut sv = run_sieve(c, limit, s);
     DevBuf<uint32_t> primes(c, sv.sieved, s);
     const int tok = prof_begin(c, "expand_primes", s);
-    expand_primes<<<sv.nsegs, kSieveThreads, 0, s>>>(sv.bits.get(), sv.offsets.get(),
-                                                      primes.get());
+    expand_primes<<<sv.nsegs, kExpandThreads, 0, s>>>(sv.bits.get(), sv.offsets.get(),
+                                                       primes.get(), 1, 1);
     CAT_LAUNCH("expand_primes");
     prof_end(c, tok, s, 4.0 * (double)sv.nsegs * kSegWords + 4.0 * (double)sv.sieved);
     *count = sv.sieved;

@@ -66,6 +66,47 @@ def test_factor_matches_oracle(ctx, cat_lib, orc, kind, n):
         f.free()
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_factor_small_sweep_binomial(ctx, cat_lib, orc, kind):
+    # every n up to 300: n + 1 prime (Catalan exponent 0 above sqrt(2n)),
+    # sqrt(2n) crossing a prime, the smallest cases of the binomial kinds
+    for n in range(1, 301):
+        f = cat_lib.catalan_factor(ctx, n, kind)
+        try:
+            exps, offs, gp = orc.factor(kind, n)
+            assert f.exps.tolist() == exps.tolist(), n
+            assert f.offsets.tolist() == offs.tolist(), n
+            assert (host(f.primes()) == gp).all(), n
+            assert f.primes_sieved == orc.prime_count(2 * n), n
+        finally:
+            f.free()
+
+
+# (p^2 - 1)/2 for a prime p: sqrt(2n) lies just below p, so p is the smallest
+# prime handled by the one-division exponent; 2^31 - 1 is the largest n taken
+@pytest.mark.parametrize("n", [(1009**2 - 1) // 2, 12_345_679, 2**30 + 3,
+                               (65521**2 - 1) // 2, 2**31 - 1])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_factor_binomial_vs_ratio_path(ctx, cat_lib, kind, n):
+    # C(n) = (2n)!/(n! (n+1)!) and C(2n, n) = (2n)!/(n! n!) as factorial
+    # ratios take Legendre's formula for every prime and the radix grouping;
+    # the binomial kinds take the one-division exponent above sqrt(2n).
+    import torch
+    b = [n, n + 1] if kind == 0 else [n, n]
+    f = cat_lib.catalan_factor(ctx, n, kind)
+    g = cat_lib.cat_ratio_factor(ctx, [2 * n], b)
+    try:
+        assert f.primes_sieved == g.primes_sieved
+        assert f.num_primes == g.num_primes
+        assert f.exps.tolist() == g.exps.tolist()
+        assert f.offsets.tolist() == g.offsets.tolist()
+        assert torch.equal(f.primes(), g.primes())
+    finally:
+        f.free()
+        g.free()
+        torch.cuda.empty_cache()
+
+
 def test_factor_config1_counts(ctx, cat_lib):
     # n = 10^5: 17,984 primes <= 2n (pi(2*10^5), textbook value)
     f = cat_lib.catalan_factor(ctx, 100000, 0)
