@@ -196,7 +196,10 @@ int catalan_exact(cat_ctx *ctx, uint64_t n, uint32_t *out, size_t cap,
                   size_t *out_len, void *stream);
 
 /* cat_exact writing into a HOST buffer: the device result is copied back
- * before returning (the copy is part of the call). */
+ * before returning (the copy is part of the call).  When host_out lies in
+ * page-locked memory mapped for the device (cudaHostAlloc, cudaHostRegister),
+ * the copy is a kernel storing straight into it; for pageable memory it is a
+ * copy-engine transfer.  host_out must hold cap limbs in one buffer. */
 int cat_exact_host(cat_ctx *ctx, int kind, uint64_t n, uint32_t *host_out,
                    size_t cap, size_t *out_len, void *stream);
 

@@ -330,8 +330,7 @@ int cat_exact_host(cat_ctx *ctx, int kind, uint64_t n, uint32_t *host_out, size_
         cat::factor_free(ctx->c, &f);
         *out_len = r.n;
         if (r.n > cap) cat::fail(CAT_ERANGE, "output capacity too small");
-        if (r.n)
-            CAT_CUDA(cudaMemcpyAsync(host_out, r.buf.get(), 4 * r.n, cudaMemcpyDeviceToHost, s));
+        cat::copy_to_host(ctx->c, host_out, r.buf.get(), r.n, s);
         CAT_CUDA(cudaStreamSynchronize(s));
     });
 }

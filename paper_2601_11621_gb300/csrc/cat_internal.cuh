@@ -542,6 +542,11 @@ struct Ratio {
 void factor(Ctx &c, uint64_t n, int kind, cat_factorization *out, cudaStream_t s);
 void factor_ratio(Ctx &c, const Ratio &r, cat_factorization *out, cudaStream_t s);
 void factor_free(Ctx &c, cat_factorization *f);
+
+// n limbs from device memory into host memory, on stream s (not synchronised):
+// a store kernel when the host range is page-locked and mapped for the
+// device, a copy-engine transfer otherwise.
+void copy_to_host(Ctx &c, uint32_t *host, const uint32_t *dev, size_t n, cudaStream_t s);
 // Algorithm 2 on a factorisation; returns the result (normalised length).
 Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s);
 

@@ -152,6 +152,37 @@ def test_exact_host_buffer(ctx, cat_lib, orc):
     assert (got == orc.catalan(54321)).all()
 
 
+@pytest.mark.parametrize("shift", [0, 1, 2, 3])
+@pytest.mark.parametrize("kind,n", [(0, 54321), (1, 7), (2, 3000), (0, 2 * 10**6)])
+def test_exact_into_pinned_host(ctx, cat_lib, orc, shift, kind, n):
+    # page-locked destinations take the store kernel: 16-byte aligned (shift 0)
+    # or not (1..3 limbs in), lengths with and without a ragged last 1..3
+    # limbs; limbs around the result stay untouched
+    import torch
+    cap = cat_lib.cat_bound_limbs(n, kind)
+    pinned = torch.empty(cap + 8, dtype=torch.int32, pin_memory=True)
+    buf = pinned.numpy().view(np.uint32)
+    buf[:] = 0xDEADBEEF
+    got = cat_lib.cat_exact_host(ctx, kind, n, out=buf[shift:shift + cap])
+    want = cat_lib.to_numpy(cat_lib.cat_exact(ctx, kind, n))
+    assert (got == want).all()
+    if n <= 10**5:
+        assert (got == orc.exact(kind, n)).all()
+    assert (buf[:shift] == 0xDEADBEEF).all()
+    assert (buf[shift + got.size:] == 0xDEADBEEF).all()
+
+
+def test_exact_into_pageable_host(ctx, cat_lib):
+    # pageable memory takes the copy-engine transfer
+    n = 10**6
+    cap = cat_lib.cat_bound_limbs(n, 0)
+    buf = np.full(cap + 3, 0xDEADBEEF, dtype=np.uint32)
+    got = cat_lib.cat_exact_host(ctx, 0, n, out=buf[1:1 + cap])
+    want = cat_lib.to_numpy(cat_lib.catalan_exact(ctx, n))
+    assert (got == want).all()
+    assert buf[0] == 0xDEADBEEF and (buf[1 + got.size:] == 0xDEADBEEF).all()
+
+
 @pytest.mark.parametrize("kind,n", [("catalan", 10**6), ("central_binomial", 10**6),
                                     ("factorial", 10**6), ("catalan", 10**7),
                                     ("catalan", 50_000_000)])
