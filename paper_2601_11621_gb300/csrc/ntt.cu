@@ -223,6 +223,72 @@ __device__ uint32_t block_map_scan(uint32_t f, uint32_t *wsm, uint32_t *total)
     return map_compose(ex, before);
 }
 
+// The carry map of a run in compact form.  A run takes its carry-in c in
+// {0,1,2,3} into its lowest limb, and one more carry leaves it only if that
+// limb overflows and every other limb is the largest digit; so its map is
+// c -> b + [c >= t] with b the carry-out for c = 0 and t in {1,2,3} (or 4,
+// never).  Compositions keep the form, (f o g)(c) = b_f + [b_g + [c >= t_g]
+// >= t_f], with t = 0 for "always".  Packed as b << 4 | t; kUnitId (t = 15)
+// is the identity, for threads without limbs.
+constexpr uint32_t kUnitId = 15u;
+
+__device__ __forceinline__ uint32_t unit_eval(uint32_t m, uint32_t c)
+{
+    return m == kUnitId ? c : (m >> 4) + (c >= (m & 15u) ? 1u : 0u);
+}
+
+// f o g
+__device__ __forceinline__ uint32_t unit_compose(uint32_t f, uint32_t g)
+{
+    const uint32_t tf = f & 15u, bg = g >> 4, tg = g & 15u;
+    const uint32_t t = bg >= tf ? 0u : (bg + 1u == tf ? tg : 4u);
+    uint32_t r = (f & ~15u) | t;
+    r = g == kUnitId ? f : r;
+    return f == kUnitId ? g : r;
+}
+
+// table form (2 bits per carry-in) of a compact map
+__device__ __forceinline__ uint32_t unit_table(uint32_t m)
+{
+    uint32_t r = 0;
+#pragma unroll
+    for (uint32_t c = 0; c < 4; c++) r |= unit_eval(m, c) << (2 * c);
+    return r;
+}
+
+// Scan of compact run maps over the threads of the block, in thread order:
+// returns the carry into thread t's run for a tile carry-in of 0, and the
+// whole tile's map in table form through *tile_table.  wsm holds 32 words.
+// Synchronises internally.
+__device__ uint32_t block_carry_scan(uint32_t f, uint32_t *wsm, uint32_t *tile_table)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    uint32_t inc = f;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc = unit_compose(inc, o);
+    }
+    __syncthreads();
+    if (lane == 31) wsm[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < nw ? wsm[lane] : kUnitId;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w = unit_compose(w, o);
+        }
+        wsm[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t cin_warp = wid > 0 ? unit_eval(wsm[wid - 1], 0u) : 0u;
+    const uint32_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
+    *tile_table = unit_table(wsm[nw - 1]);
+    return lane > 0 ? unit_eval(ex, cin_warp) : cin_warp;
+}
+
 constexpr int kLimbsPerThread = 8;
 
 // Coefficient words of a thread's run of kLimbsPerThread consecutive
@@ -292,7 +358,7 @@ __device__ void tile_carry(const CoefRun &r, uint32_t h1, uint32_t h2a, uint32_t
     const uint32_t top = dec ? kDecBase - 1 : 0xffffffffu;  // largest limb
     uint32_t limb[kLimbsPerThread];
     uint32_t carry = 0;
-    uint32_t f = kMapId;
+    uint32_t f = kUnitId;
     if (j0 < tile_len) {
 #pragma unroll
         for (int i = 0; i < kLimbsPerThread; i++) {
@@ -312,18 +378,13 @@ __device__ void tile_carry(const CoefRun &r, uint32_t h1, uint32_t h2a, uint32_t
         bool ones = true;
 #pragma unroll
         for (int i = 1; i < kLimbsPerThread; i++) ones = ones && limb[i] == top;
-        f = 0;
-#pragma unroll
-        for (uint32_t c = 0; c < 4; c++) {
-            const uint32_t o = carry + ((c > 0 && ones && limb[0] >= top + 1 - c) ? 1u : 0u);
-            f |= o << (2 * c);
-        }
+        // a carry-in c leaves the run iff ones and limb[0] + c > top
+        const uint32_t t = (ones && limb[0] >= top - 2u) ? top + 1u - limb[0] : 4u;
+        f = (carry << 4) | t;
     }
-    uint32_t total;
-    const uint32_t ex = block_map_scan(f, wsm, &total);
-    *tile_map = total;
+    const uint32_t cin = block_carry_scan(f, wsm, tile_map);
     if (j0 < tile_len) {
-        uint32_t c = map_at(ex, 0);
+        uint32_t c = cin;
 #pragma unroll
         for (int i = 0; i < kLimbsPerThread; i++) {
             const uint64_t v = (uint64_t)limb[i] + c;
