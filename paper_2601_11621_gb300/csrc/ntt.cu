@@ -174,55 +174,6 @@ __device__ __forceinline__ void crt3(uint32_t r0, uint32_t r1, uint32_t r2, uint
     c2 = (uint32_t)(hi >> 32);
 }
 
-// Carry maps: for a run of limbs, the carry out as a function of the carry
-// in c in {0,1,2,3}, packed two bits per entry.  Composition is associative,
-// so runs combine by a parallel scan.
-constexpr uint32_t kMapId = 0xE4u;  // c -> c
-
-__device__ __forceinline__ uint32_t map_at(uint32_t m, uint32_t c) { return (m >> (2 * c)) & 3u; }
-
-// (f o g)(c) = f(g(c))
-__device__ __forceinline__ uint32_t map_compose(uint32_t f, uint32_t g)
-{
-    uint32_t r = 0;
-#pragma unroll
-    for (uint32_t c = 0; c < 4; c++) r |= map_at(f, map_at(g, c)) << (2 * c);
-    return r;
-}
-
-// Exclusive scan of maps over the threads of the block, in thread order:
-// returns f_{t-1} o ... o f_0 for thread t, and the whole block's composition
-// through *total.  wsm holds 32 words.  Synchronises internally.
-__device__ uint32_t block_map_scan(uint32_t f, uint32_t *wsm, uint32_t *total)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
-    uint32_t inc = f;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t o = __shfl_up_sync(0xffffffffu, inc, off);
-        if (lane >= off) inc = map_compose(inc, o);
-    }
-    __syncthreads();
-    if (lane == 31) wsm[wid] = inc;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t w = lane < nw ? wsm[lane] : kMapId;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t o = __shfl_up_sync(0xffffffffu, w, off);
-            if (lane >= off) w = map_compose(w, o);
-        }
-        wsm[lane] = w;
-    }
-    __syncthreads();
-    uint32_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
-    if (lane == 0) ex = kMapId;
-    const uint32_t before = wid > 0 ? wsm[wid - 1] : kMapId;
-    *total = wsm[nw - 1];
-    return map_compose(ex, before);
-}
-
 // The carry map of a run in compact form.  A run takes its carry-in c in
 // {0,1,2,3} into its lowest limb, and one more carry leaves it only if that
 // limb overflows and every other limb is the largest digit; so its map is
@@ -247,20 +198,11 @@ __device__ __forceinline__ uint32_t unit_compose(uint32_t f, uint32_t g)
     return f == kUnitId ? g : r;
 }
 
-// table form (2 bits per carry-in) of a compact map
-__device__ __forceinline__ uint32_t unit_table(uint32_t m)
-{
-    uint32_t r = 0;
-#pragma unroll
-    for (uint32_t c = 0; c < 4; c++) r |= unit_eval(m, c) << (2 * c);
-    return r;
-}
-
 // Scan of compact run maps over the threads of the block, in thread order:
-// returns the carry into thread t's run for a tile carry-in of 0, and the
-// whole tile's map in table form through *tile_table.  wsm holds 32 words.
-// Synchronises internally.
-__device__ uint32_t block_carry_scan(uint32_t f, uint32_t *wsm, uint32_t *tile_table)
+// returns the carry into thread t's run for a carry-in of 0 ahead of thread 0,
+// and the composition of all the block's maps through *total.  wsm holds 32
+// words.  Synchronises internally.
+__device__ uint32_t block_carry_scan(uint32_t f, uint32_t *wsm, uint32_t *total)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
@@ -285,7 +227,7 @@ __device__ uint32_t block_carry_scan(uint32_t f, uint32_t *wsm, uint32_t *tile_t
     __syncthreads();
     const uint32_t cin_warp = wid > 0 ? unit_eval(wsm[wid - 1], 0u) : 0u;
     const uint32_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
-    *tile_table = unit_table(wsm[nw - 1]);
+    *total = wsm[nw - 1];
     return lane > 0 ? unit_eval(ex, cin_warp) : cin_warp;
 }
 
@@ -348,8 +290,8 @@ __device__ __forceinline__ void words_to_dec(uint32_t &w0, uint32_t &w1, uint32_
 // top word or digit (below 2^26 or 10^8: coefficients stay below 2^90, or
 // 10^26 for digit operands), the addend and a carry <= 3, so carries stay in
 // {0, 1, 2, 3}.  Writes limbs j < min(tile_len, out_count) to out and returns
-// the tile's carry map in *tile_map (valid in every thread).  The tile's own
-// carry-in is assumed 0.
+// the tile's carry map in compact form in *tile_map (valid in every thread; it
+// fits a byte).  The tile's own carry-in is assumed 0.
 __device__ void tile_carry(const CoefRun &r, uint32_t h1, uint32_t h2a, uint32_t h2b, int tile_len,
                            uint32_t *out, long out_count, bool dec, const uint32_t *add,
                            long add_count, uint32_t *wsm, uint32_t *tile_map)
@@ -405,7 +347,7 @@ struct CrtArgs {
     size_t gpstride;
     int n;              // log2 L
     Sink sink;          // product k's limbs (out_len <= L)
-    uint8_t *tile_maps; // [product][tiles]
+    uint8_t *tile_maps; // [product][tiles], compact carry maps
 };
 
 // One tile of 2048 coefficients per block: each thread remainders its run of
@@ -457,21 +399,24 @@ __global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
     if (threadIdx.x == 0) a.tile_maps[blockIdx.x] = (uint8_t)map;
 }
 
-// Carry into each tile: a scan of the tile maps of one product (one block).
+// Carry into each tile of a product (one block per product), in place of the
+// tiles' compact maps: each thread folds the maps of its stretch of
+// consecutive tiles, a block scan carries between the stretches, and each
+// thread replays its stretch, writing every tile's carry-in.
 __global__ void __launch_bounds__(1024) carry_tile_scan(uint8_t *tile_maps, size_t tiles)
 {
     __shared__ uint32_t wsm[32];
     uint8_t *m = tile_maps + blockIdx.x * tiles;
-    uint32_t run = 0;  // carry into the current chunk
-    for (size_t base = 0; base < tiles; base += blockDim.x) {
-        const size_t i = base + threadIdx.x;
-        const uint32_t f = i < tiles ? m[i] : kMapId;
-        uint32_t total;
-        const uint32_t ex = block_map_scan(f, wsm, &total);
-        __syncthreads();
-        if (i < tiles) m[i] = (uint8_t)map_at(ex, run);  // now the tile's carry-in
-        run = map_at(total, run);
-        __syncthreads();
+    const size_t per = (tiles + blockDim.x - 1) / blockDim.x;
+    const size_t i0 = threadIdx.x * per, i1 = std::min(tiles, i0 + per);
+    uint32_t f = kUnitId;
+    for (size_t i = i0; i < i1; i++) f = unit_compose(m[i], f);
+    uint32_t total;
+    uint32_t c = block_carry_scan(f, wsm, &total);
+    for (size_t i = i0; i < i1; i++) {
+        const uint32_t g = m[i];
+        m[i] = (uint8_t)c;  // now the tile's carry-in
+        c = unit_eval(g, c);
     }
 }
 
