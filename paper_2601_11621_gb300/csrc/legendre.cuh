@@ -45,10 +45,11 @@ __device__ __forceinline__ int64_t exponent_of(uint32_t p, uint32_t n, int kind)
 // The same exponent for a prime with p^2 > 2n (Catalan or central binomial
 // kinds).  Then v_p((2n)!) = floor(2n/p) and v_p(n!) = floor(n/p), so with
 // r = n mod p the difference is floor(2r/p) in {0, 1} (one carry when n + n
-// is added in base p), and v_p(n+1) = [p | n+1] = [r = p-1].  One division.
+// is added in base p), and v_p(n+1) = [p | n+1] = [r = p-1].  One division,
+// none for p > n (r = n there: half of the primes up to 2n).
 __device__ __forceinline__ uint32_t unit_exponent(uint32_t p, uint32_t n, int kind)
 {
-    const uint32_t r = n % p;
+    const uint32_t r = p > n ? n : n % p;
     uint32_t e = 2 * r >= p ? 1u : 0u;  // 2r < 2^32: r <= n < 2^31
     if (kind == CAT_CATALAN && r == p - 1) e = 0;
     return e;

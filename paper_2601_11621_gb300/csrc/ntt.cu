@@ -373,19 +373,29 @@ __global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
         r[p][0] = x.x; r[p][1] = x.y; r[p][2] = x.z; r[p][3] = x.w;
         r[p][4] = y.x; r[p][5] = y.y; r[p][6] = y.z; r[p][7] = y.w;
     }
+    // the tile's predecessor: coefficients jt - 2 and jt - 1 (none for tile 0),
+    // loaded by thread 0 beside its run so that the latencies overlap
+    const bool pred = threadIdx.x == 0 && t > 0;
+    uint32_t pr[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    if (pred) {
+#pragma unroll
+        for (int p = 0; p < 3; p++) {
+            pr[p][0] = g0[p * a.gpstride - 2];
+            pr[p][1] = g0[p * a.gpstride - 1];
+        }
+    }
     CoefRun run;
 #pragma unroll
     for (int i = 0; i < kLimbsPerThread; i++) {
         crt3<PS>(r[0][i], r[1][i], r[2][i], run.c0[i], run.c1[i], run.c2[i]);
         if (dec) words_to_dec(run.c0[i], run.c1[i], run.c2[i]);
     }
-    // the tile's predecessor: coefficients jt - 2 and jt - 1 (none for tile 0)
     uint32_t f1 = 0, f2a = 0, f2b = 0;
-    if (threadIdx.x == 0 && t > 0) {
+    if (pred) {
         uint32_t d0, d1, e0;
-        crt3<PS>(g0[-2], g0[a.gpstride - 2], g0[2 * a.gpstride - 2], d0, d1, f2a);
+        crt3<PS>(pr[0][0], pr[1][0], pr[2][0], d0, d1, f2a);
         if (dec) words_to_dec(d0, d1, f2a);
-        crt3<PS>(g0[-1], g0[a.gpstride - 1], g0[2 * a.gpstride - 1], e0, f1, f2b);
+        crt3<PS>(pr[0][1], pr[1][1], pr[2][1], e0, f1, f2b);
         if (dec) words_to_dec(e0, f1, f2b);
     }
     uint32_t h1, h2a, h2b;
