@@ -59,9 +59,10 @@ __host__ __device__ constexpr int dit_base(int lr, int rd) { return dit_base(lr,
 // B < 5 the lanes of a warp differ in address bits [0, B) and in bits at and
 // above B + E; f is chosen so that those five bits always land on five
 // independent bank bits for the round shapes used here (E = 3 or 4 with
-// B = 0, 3 or 4 on contiguous rows; the group bit 7 of 16-column tiles), so
-// no round has a bank conflict.  Rounds with B >= 5 are conflict-free under
-// any such XOR.
+// B = 0, 3 or 4 on contiguous rows; the group bit 7 of 16-column tiles; in the
+// column passes' interleaved tiles every shape from E = 2 to 4 at the bases
+// they use, checked lane by lane), so no round has a bank conflict.  Rounds
+// with B >= 5 are conflict-free under any such XOR.
 __host__ __device__ constexpr int swz(int a)
 {
     const int t = (a >> 5) & 31;
@@ -227,6 +228,14 @@ __host__ __device__ constexpr int col_log_c(int lr) { return lr >= 10 ? 4 : 13 -
 constexpr int kColThreads = 512;
 constexpr int kColMinLog = 4;   // columns of at least 2^4 rows
 constexpr int kColMaxLog = 10;  // and at most 2^10
+// Most stages per register round in the forward and inverse column passes.
+// Rounds of at most three stages keep the passes at 32 to 36 registers, so
+// four 512-thread blocks share an SM instead of two at 64 registers with
+// four-stage rounds (measured per C(2,050,572,903): inverse passes 25.1 ->
+// 22.1 ms, forward passes 45.5 -> 45.1 ms).
+constexpr int kColFwdRoundMax = 3;
+constexpr int kColInvRoundMax = 3;
+__host__ __device__ constexpr int col_rounds(int lr, int most) { return (lr + most - 1) / most; }
 
 struct ColArgs {
     uint32_t *data;        // prime p's array at data + p * pstride
@@ -307,11 +316,11 @@ struct ColTw {
 };
 
 // Forward pass output: element (row, col) times w_M^(col * bitrev(row)).
-template <int LR, int PS>
+template <int LR, int PS, int NR = rounds_of(LR)>
 struct ColOutTw {
     uint32_t *p;
     uint32_t S, col0;
-    ColTw<LR, PS> tw;
+    ColTw<LR, PS, NR> tw;
     template <int E, int B, int NA>
     __device__ __forceinline__ void store(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
@@ -361,7 +370,9 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_fwd(ColArgs a)
 {
     extern __shared__ uint32_t sm[];
     constexpr int LC = col_log_c(LR), C = 1 << LC;
-    constexpr int NR = rounds_of(LR);
+    // 2^4-row columns in one round, straight from global to global memory
+    constexpr int NR = LR <= 4 ? 1 : col_rounds(LR, kColFwdRoundMax);
+    static_assert(NR <= 4, "at most four rounds");
     const int p = blockIdx.y;
     const uint32_t q = c_q[PS][p];
     const size_t Sr = (size_t)1 << (a.m - LR);
@@ -373,20 +384,27 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_fwd(ColArgs a)
     const ColIn<PS> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, (uint32_t)Sr,
                        (uint32_t)col0, (uint32_t)a.src_len,
                        q, c_wp1[PS][p]};
-    ColTw<LR, PS> tw{T, q, c_qinv[PS][p], set_log_root(PS) - a.m, 0u};
+    ColTw<LR, PS, NR> tw{T, q, c_qinv[PS][p], set_log_root(PS) - a.m, 0u};
     tw.init((uint32_t)col0);
-    const ColOutTw<LR, PS> out{base, (uint32_t)Sr, (uint32_t)col0, tw};
+    const ColOutTw<LR, PS, NR> out{base, (uint32_t)Sr, (uint32_t)col0, tw};
     if constexpr (NR == 1) {
         round_io<LR, C, 0, LR, true, 1, true, PS>(in, out, T, q);
     } else {
         const SmemIO<LR, C, true> sio{sm};
-        round_io<LR, C, dif_base(LR, 0), round_size(LR, 0), true, 1, true, PS>(in, sio, T, q);
+        round_io<LR, C, dif_base(LR, 0, NR), round_size(LR, 0, NR), true, 1, true, PS>(in, sio,
+                                                                                      T, q);
         __syncthreads();
-        if constexpr (NR == 3) {
-            round_io<LR, C, dif_base(LR, 1), round_size(LR, 1), true, 1, true, PS>(sio, sio, T, q);
+        if constexpr (NR >= 3) {
+            round_io<LR, C, dif_base(LR, 1, NR), round_size(LR, 1, NR), true, 1, true, PS>(
+                sio, sio, T, q);
             __syncthreads();
         }
-        round_io<LR, C, 0, round_size(LR, NR - 1), true, 1, true, PS>(sio, out, T, q);
+        if constexpr (NR >= 4) {
+            round_io<LR, C, dif_base(LR, 2, NR), round_size(LR, 2, NR), true, 1, true, PS>(
+                sio, sio, T, q);
+            __syncthreads();
+        }
+        round_io<LR, C, 0, round_size(LR, NR - 1, NR), true, 1, true, PS>(sio, out, T, q);
     }
 }
 
@@ -396,9 +414,8 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
 {
     extern __shared__ uint32_t sm[];
     constexpr int LC = col_log_c(LR), C = 1 << LC;
-    // 2^4-point columns in two rounds of two stages: a single 16-value round
-    // kept a 512-thread block at one per SM (measured faster split)
-    constexpr int NR = LR == 4 ? 2 : rounds_of(LR);
+    constexpr int NR = col_rounds(LR, kColInvRoundMax);
+    static_assert(NR <= 4, "at most four rounds");
     const int p = blockIdx.y;
     const uint32_t q = c_q[PS][p];
     const size_t Sr = (size_t)1 << (a.m - LR);
@@ -417,8 +434,13 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
         const SmemIO<LR, C, true> sio{sm};
         round_io<LR, C, 0, dit_size(LR, 0, NR), false, 1, true, PS>(in, sio, Ti, q);
         __syncthreads();
-        if constexpr (NR == 3) {
+        if constexpr (NR >= 3) {
             round_io<LR, C, dit_base(LR, 1, NR), dit_size(LR, 1, NR), false, 1, true, PS>(
+                sio, sio, Ti, q);
+            __syncthreads();
+        }
+        if constexpr (NR >= 4) {
+            round_io<LR, C, dit_base(LR, 2, NR), dit_size(LR, 2, NR), false, 1, true, PS>(
                 sio, sio, Ti, q);
             __syncthreads();
         }
