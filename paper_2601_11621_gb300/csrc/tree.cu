@@ -115,12 +115,40 @@ void mul_into(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb
     mul_acc(c, a, na, b, nb, out, na + nb, false, s);
 }
 
-Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s)
+static Big copy_big(Ctx &c, const uint32_t *a, size_t n, cudaStream_t s);
+static Big mul_big(Ctx &c, const Big &x, const Big &y, cudaStream_t s);
+
+// Levels above the leaves of a tree over `count` values.
+static int tree_depth(size_t count)
+{
+    size_t nodes = (count + kLeafSlot - 1) / kLeafSlot;
+    int d = 0;
+    for (; nodes > 1; d++) nodes = (nodes + 1) / 2;
+    return d;
+}
+
+// The product of values[0 .. count) (times *extra when given).  extra joins
+// the tree as one node: the count is padded with values 1 up to a multiple of
+// a slot size S >= extra's length, plus S more, so that at slot S the last
+// node is exactly 1 and extra takes its place.  Every node still fits its
+// slot, so the levels above are unchanged; only when the padding would add a
+// level is extra multiplied in at the end instead.
+Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s, const Big *extra)
 {
     NvtxRange range("product tree");
-    if (count == 0) return make_one(c, s);
+    if (count == 0) return extra ? copy_big(c, extra->buf.get(), extra->n, s) : make_one(c, s);
+    size_t total = count, inj_slot = 0;
+    if (extra) {
+        size_t S = 2 * kLeafSlot;
+        while (S < extra->n) S <<= 1;
+        const size_t padded = (count + S - 1) / S * S + S;
+        if (tree_depth(padded) == tree_depth(count)) {
+            total = padded;
+            inj_slot = S;
+        }
+    }
     size_t slot = kLeafSlot;
-    size_t nodes = (count + kLeafSlot - 1) / kLeafSlot;
+    size_t nodes = (total + kLeafSlot - 1) / kLeafSlot;
     DevBuf<uint32_t> cur(c, nodes * slot, s);
     leaf_level(c, values, count, cur.get(), nodes, s);
     while (nodes > 1) {
@@ -134,6 +162,15 @@ Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s)
                                      4 * slot, cudaMemcpyDeviceToDevice, s));
             CAT_CUDA(cudaMemsetAsync(nxt.get() + nprod * ns + slot, 0, 4 * slot, s));
         }
+        if (ns == inj_slot) {  // the last node covers only padding: replace its 1 by extra
+            uint32_t *last = nxt.get() + (nn - 1) * ns;
+            CAT_CUDA(cudaMemcpyAsync(last, extra->buf.get(), 4 * extra->n,
+                                     cudaMemcpyDeviceToDevice, s));
+            if (extra->n < ns)
+                CAT_CUDA(cudaMemsetAsync(last + extra->n, 0, 4 * (ns - extra->n), s));
+            inj_slot = 0;
+            extra = nullptr;
+        }
         cur = std::move(nxt);
         nodes = nn;
         slot = ns;
@@ -141,6 +178,7 @@ Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s)
     Big r;
     r.n = normalized_length(c, cur.get(), slot, s);
     r.buf = std::move(cur);
+    if (extra) return mul_big(c, r, *extra, s);
     return r;
 }
 
@@ -237,16 +275,20 @@ Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s)
 {
     NvtxRange range("phase2: reconstruction");
     if (f->num_groups > kManyGroups) return reconstruct_bits(c, f, s);
+    // P_e = Q_e^e for e >= 2 first, combined into R; then Q_1's tree takes R
+    // in as one of its nodes, so that the long P_1 needs no final product
+    // (the same integer: the final product of the P_e, re-associated).
     std::vector<Big> P;
+    int64_t g1 = -1;
     for (uint64_t g = 0; g < f->num_groups; g++) {
+        if (f->host_exps[g] == 1) {
+            g1 = (int64_t)g;
+            continue;
+        }
         const uint64_t off = f->host_offsets[g], cnt = f->host_offsets[g + 1] - off;
         Big Q = tree_product(c, f->primes + off, cnt, s);
-        if (f->host_exps[g] == 1)
-            P.push_back(std::move(Q));
-        else
-            P.push_back(power(c, Q.buf.get(), Q.n, f->host_exps[g], s));
+        P.push_back(power(c, Q.buf.get(), Q.n, f->host_exps[g], s));
     }
-    if (P.empty()) return make_one(c, s);
     while (P.size() > 1) {
         std::sort(P.begin(), P.end(), [](const Big &x, const Big &y) { return x.n > y.n; });
         Big x = std::move(P.back());
@@ -255,7 +297,9 @@ Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s)
         P.pop_back();
         P.push_back(mul_big(c, x, y, s));
     }
-    return std::move(P[0]);
+    if (g1 < 0) return P.empty() ? make_one(c, s) : std::move(P[0]);
+    const uint64_t off = f->host_offsets[g1], cnt = f->host_offsets[g1 + 1] - off;
+    return tree_product(c, f->primes + off, cnt, s, P.empty() ? nullptr : &P[0]);
 }
 
 }  // namespace cat
