@@ -520,11 +520,12 @@ int to_decimal_dev(Ctx &c, const uint32_t *x, size_t n, char *out, size_t cap, s
 // Normalised length of x[0..n) (reads the device array).
 size_t normalized_length(Ctx &c, const uint32_t *x, size_t n, cudaStream_t s);
 // Product of count 32-bit values (balanced tree).  Returns the result.
-// The product of values[0 .. count), times *extra when given (see tree.cu).
+// The product of values[0 .. count), times *extra when given; exact = false
+// returns a length bound (zero top limbs) without a host read-back (tree.cu).
 Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s,
-                 const Big *extra = nullptr);
+                 const Big *extra = nullptr, bool exact = true);
 // a^e.
-Big power(Ctx &c, const uint32_t *a, size_t na, uint64_t e, cudaStream_t s);
+Big power(Ctx &c, const uint32_t *a, size_t na, uint64_t e, cudaStream_t s, bool exact = true);
 // Factorial ratios (Sec. 6.3): N = prod_i a_i! / prod_j b_j!.  A Ratio also
 // describes the three kinds (kind < kRatioKind: the quantity of n).  Every
 // term is below 2^32 and the a_i sum to less than 2^32, so every exponent

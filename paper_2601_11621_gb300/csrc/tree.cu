@@ -116,7 +116,7 @@ void mul_into(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb
 }
 
 static Big copy_big(Ctx &c, const uint32_t *a, size_t n, cudaStream_t s);
-static Big mul_big(Ctx &c, const Big &x, const Big &y, cudaStream_t s);
+static Big mul_big(Ctx &c, const Big &x, const Big &y, cudaStream_t s, bool exact = true);
 
 // Levels above the leaves of a tree over `count` values.
 static int tree_depth(size_t count)
@@ -132,8 +132,11 @@ static int tree_depth(size_t count)
 // a slot size S >= extra's length, plus S more, so that at slot S the last
 // node is exactly 1 and extra takes its place.  Every node still fits its
 // slot, so the levels above are unchanged; only when the padding would add a
-// level is extra multiplied in at the end instead.
-Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s, const Big *extra)
+// level is extra multiplied in at the end instead.  exact = false returns the
+// top slot (zero-padded) as the length instead of reading the true length
+// back: no host synchronisation.
+Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s, const Big *extra,
+                 bool exact)
 {
     NvtxRange range("product tree");
     if (count == 0) return extra ? copy_big(c, extra->buf.get(), extra->n, s) : make_one(c, s);
@@ -176,9 +179,9 @@ Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s, c
         slot = ns;
     }
     Big r;
-    r.n = normalized_length(c, cur.get(), slot, s);
+    r.n = exact ? normalized_length(c, cur.get(), slot, s) : slot;
     r.buf = std::move(cur);
-    if (extra) return mul_big(c, r, *extra, s);
+    if (extra) return mul_big(c, r, *extra, s, exact);
     return r;
 }
 
@@ -191,22 +194,26 @@ static Big copy_big(Ctx &c, const uint32_t *a, size_t n, cudaStream_t s)
     return r;
 }
 
-static Big mul_big(Ctx &c, const Big &x, const Big &y, cudaStream_t s)
+// x y; exact = false keeps the bound x.n + y.n as the length (zero top limbs)
+// instead of reading the true length back.
+static Big mul_big(Ctx &c, const Big &x, const Big &y, cudaStream_t s, bool exact)
 {
     Big r;
     const size_t n = x.n + y.n;
     r.buf = DevBuf<uint32_t>(c, n ? n : 1, s);
     mul_into(c, x.buf.get(), x.n, y.buf.get(), y.n, r.buf.get(), s);
-    r.n = trim(c, r.buf.get(), n, s);
+    r.n = exact ? trim(c, r.buf.get(), n, s) : n;
     return r;
 }
 
 // a^e, left-to-right binary (the powering step of Algorithm 2).  Squarings reuse
-// one forward transform.
-Big power(Ctx &c, const uint32_t *a, size_t na, uint64_t e, cudaStream_t s)
+// one forward transform.  exact = false takes a (nonzero) as given, with zero
+// top limbs allowed, and returns a bound as the length: no host
+// synchronisation.
+Big power(Ctx &c, const uint32_t *a, size_t na, uint64_t e, cudaStream_t s, bool exact)
 {
     NvtxRange range("power");
-    na = normalized_length(c, a, na, s);
+    if (exact) na = normalized_length(c, a, na, s);
     if (e == 0) return make_one(c, s);
     if (na == 0) return copy_big(c, a, 0, s);
     Big base = copy_big(c, a, na, s);
@@ -214,8 +221,8 @@ Big power(Ctx &c, const uint32_t *a, size_t na, uint64_t e, cudaStream_t s)
     int top = 63;
     while (!((e >> top) & 1)) top--;
     for (int bit = top - 1; bit >= 0; bit--) {
-        r = mul_big(c, r, r, s);
-        if ((e >> bit) & 1) r = mul_big(c, r, base, s);
+        r = mul_big(c, r, r, s, exact);
+        if ((e >> bit) & 1) r = mul_big(c, r, base, s, exact);
     }
     return r;
 }
@@ -277,7 +284,10 @@ Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s)
     if (f->num_groups > kManyGroups) return reconstruct_bits(c, f, s);
     // P_e = Q_e^e for e >= 2 first, combined into R; then Q_1's tree takes R
     // in as one of its nodes, so that the long P_1 needs no final product
-    // (the same integer: the final product of the P_e, re-associated).
+    // (the same integer: the final product of the P_e, re-associated).  The
+    // small P_e and R carry length bounds (zero top limbs), so that none of
+    // their many short steps waits for a read-back; only the end result is
+    // normalised.
     std::vector<Big> P;
     int64_t g1 = -1;
     for (uint64_t g = 0; g < f->num_groups; g++) {
@@ -286,8 +296,8 @@ Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s)
             continue;
         }
         const uint64_t off = f->host_offsets[g], cnt = f->host_offsets[g + 1] - off;
-        Big Q = tree_product(c, f->primes + off, cnt, s);
-        P.push_back(power(c, Q.buf.get(), Q.n, f->host_exps[g], s));
+        Big Q = tree_product(c, f->primes + off, cnt, s, nullptr, false);
+        P.push_back(power(c, Q.buf.get(), Q.n, f->host_exps[g], s, false));
     }
     while (P.size() > 1) {
         std::sort(P.begin(), P.end(), [](const Big &x, const Big &y) { return x.n > y.n; });
@@ -295,9 +305,13 @@ Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s)
         P.pop_back();
         Big y = std::move(P.back());
         P.pop_back();
-        P.push_back(mul_big(c, x, y, s));
+        P.push_back(mul_big(c, x, y, s, false));
     }
-    if (g1 < 0) return P.empty() ? make_one(c, s) : std::move(P[0]);
+    if (g1 < 0) {
+        if (P.empty()) return make_one(c, s);
+        P[0].n = normalized_length(c, P[0].buf.get(), P[0].n, s);
+        return std::move(P[0]);
+    }
     const uint64_t off = f->host_offsets[g1], cnt = f->host_offsets[g1 + 1] - off;
     return tree_product(c, f->primes + off, cnt, s, P.empty() ? nullptr : &P[0]);
 }
