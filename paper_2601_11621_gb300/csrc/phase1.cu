@@ -6,7 +6,7 @@
 // Sieve.  Seed primes up to sqrt(limit) come from one thread block.  The odd
 // numbers up to the limit are cut into segments of 2^18 (one bit each, 32 KiB
 // of shared memory per block).  Primes 3..31 are struck word by word from
-// precomputed bit patterns; primes 37..2047 are struck by whole warps (one
+// precomputed bit patterns; primes 37..511 are struck by whole warps (one
 // multiple per lane); larger seed primes by one thread each.  Each segment's
 // bitmap and prime count go to global memory; an exclusive scan of the
 // counts gives every segment its first output position.
@@ -39,7 +39,7 @@ constexpr int kSegBits = 1 << 18;           // odd numbers per segment
 constexpr int kSegWords = kSegBits / 32;    // 8192 words
 constexpr int kSieveThreads = 512;
 constexpr uint32_t kMediumPrime = 37;       // first prime struck by atomics
-constexpr uint32_t kLargePrime = 2048;      // thread-per-prime from here
+constexpr uint32_t kLargePrime = 512;       // thread-per-prime from here (measured best)
 
 // ---------------------------------------------------------------- seeds
 
