@@ -40,6 +40,23 @@ NTT_SOURCES = ["paper_2601_11621_gb300/csrc/ntt.cu", "paper_2601_11621_gb300/csr
                "paper_2601_11621_gb300/csrc/cat_internal.cuh"]
 
 
+def slowest_rank(seconds: float, dist=None, device: str = "cpu") -> float:
+    """The largest of the ranks' timings, on every rank: the job takes as long
+    as its slowest rank (one all-reduce MAX; the local value when alone)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def per_unit(seconds: float, units_per_rank: int, world: int) -> float:
+    """Whole-job seconds per C(n): the slowest rank's time over the units that
+    all ranks processed (every rank computes units_per_rank replicas)."""
+    return seconds / (units_per_rank * world)
+
+
 def captured_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or
     None when there is none or the kernel sources changed since the capture."""
@@ -249,11 +266,8 @@ def main():
     clk = clocks.stop()
     prof = ctx.profile()
     ctx.set_profiling(False)
-    if dist:
-        t = torch.tensor([ms], device=f"cuda:{local_rank}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ms / 1000.0 / (args.steps * world)
+    ms = 1000.0 * slowest_rank(ms / 1000.0, dist, f"cuda:{local_rank}")
+    value = per_unit(ms / 1000.0, args.steps, world)
 
     # end to end through the C ABI into pinned host memory
     host = torch.empty(cap, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
@@ -267,11 +281,8 @@ def main():
         hres = capi.cat_exact_host(ctx, capi.CAT_CATALAN, n, out=host)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=f"cuda:{local_rank}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = e2e_s / (e2e_steps * world)
+    e2e_s = slowest_rank(e2e_s, dist, f"cuda:{local_rank}")
+    e2e_value = per_unit(e2e_s, e2e_steps, world)
 
     # dominant kernel by device time
     peak, peak_kind = read_peaks()
