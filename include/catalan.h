@@ -175,9 +175,11 @@ int product_tree(cat_ctx *ctx, const uint32_t *values, size_t count, uint32_t *o
                  size_t cap, size_t *out_len, void *stream);
 
 /* Algorithm 2 on a factorisation: out = prod_g (prod_{p in G_g} p)^exps[g].
- * The P_e are combined by always multiplying the two shortest, which keeps
- * every intermediate as short as possible (the aim Sec. 3.2 states for the
- * balanced tree). */
+ * The P_e with e >= 2 are combined by always multiplying the two shortest,
+ * which keeps every intermediate as short as possible (the aim Sec. 3.2
+ * states for the balanced tree); their product then joins the tree of Q_1
+ * as one node, so the longest factor needs no final multiplication (the same
+ * integer, re-associated). */
 int cat_reconstruct(cat_ctx *ctx, const cat_factorization *f, uint32_t *out,
                     size_t cap, size_t *out_len, void *stream);
 
