@@ -140,18 +140,20 @@ int bigint_mul(cat_ctx *ctx, const uint32_t *a, size_t na, const uint32_t *b,
 /* out = a * b without allocating any device memory.  The paper has no
  * counterpart: this is for callers that cannot call cudaMalloc, such as an
  * application whose own allocator already holds the device's memory (a new
- * allocation would fail or fragment it), or latency-critical code that must
- * not take cudaMalloc/cudaFree's implicit device-wide synchronisation, or a
- * service that must not meet an out-of-memory failure in the middle of a
- * request.  There is no context: the
+ * allocation would fail or fragment it), or code that must not take
+ * cudaMalloc/cudaFree's implicit synchronisation of the whole device (this
+ * call waits only for its own stream), or a service that must not meet an
+ * out-of-memory failure in the middle of a request.  There is no context: the
  * transform scratch and the twiddle tables live in fixed-size __device__
  * arrays of the library (about 2.4 MB of scratch and 1.4 MB of tables),
  * which every GPU that loads the library holds until the process exits.
- *   - Limit: na + nb <= 65,536 limbs; larger products return CAT_ENOMEM.
+ *   - Limit: na + nb <= 65,536 limbs; larger products return CAT_ENOMEM
+ *     (checked before any device work).
  *   - out must have room for na + nb limbs (cap >= na + nb, else
  *     CAT_ERANGE); *out_len = the normalised length.  a, b, out are device
- *     pointers; stream as elsewhere; the call returns after the result is
- *     complete.
+ *     pointers; stream as elsewhere.  Every call synchronises `stream` before
+ *     it returns (it reads the normalised length back), so the result is
+ *     complete on return.
  *   - Runs on the current CUDA device.  The first call on a device sets that
  *     device up (looks up the arrays' device addresses and uploads the
  *     twiddle table with a synchronous copy); make that first call before any

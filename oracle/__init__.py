@@ -33,13 +33,17 @@ _U64_MAX = (1 << 64) - 1
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` into ``liboracle.so`` with gcc (plain -O2)."""
+    """Compile ``oracle.c`` into ``liboracle.so`` with gcc (plain -O2; with
+    OpenMP when the compiler has it, which only ``exact_mt`` uses)."""
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC",
-                           "-o", tmp, _SRC, "-lm"])
+    base = ["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC]
+    try:
+        subprocess.check_call(base + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base + ["-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -61,8 +65,6 @@ def lib() -> ctypes.CDLL:
         L.orc_sieve_range.restype = u64
         L.orc_legendre.argtypes = [u64, u64]
         L.orc_legendre.restype = u64
-        L.orc_valuation.argtypes = [u64, u64]
-        L.orc_valuation.restype = u64
         L.orc_factor_trial.argtypes = [u64, u32p, u64, u64p, u64p, ctypes.c_int]
         L.orc_factor_trial.restype = ctypes.c_int
         L.orc_prime_limit.argtypes = [ctypes.c_int, u64]
@@ -86,6 +88,10 @@ def lib() -> ctypes.CDLL:
         L.orc_reconstruct.restype = u64
         L.orc_exact.argtypes = [ctypes.c_int, u64, u32p, u64]
         L.orc_exact.restype = u64
+        L.orc_exact_mt.argtypes = [ctypes.c_int, u64, u32p, u64, ctypes.c_int]
+        L.orc_exact_mt.restype = u64
+        L.orc_max_threads.argtypes = []
+        L.orc_max_threads.restype = ctypes.c_int
         L.orc_mulmod_plain.argtypes = [u64, u64, u64]
         L.orc_mulmod_plain.restype = u64
         L.orc_mulmod_mont.argtypes = [u64, u64, u64]
@@ -149,10 +155,6 @@ def prime_count(limit: int) -> int:
 def legendre(m: int, p: int) -> int:
     """v_p(m!) by Legendre's formula (Sec. 2)."""
     return int(lib().orc_legendre(m, p))
-
-
-def valuation(x: int, p: int) -> int:
-    return int(lib().orc_valuation(x, p))
 
 
 def factor_trial(m: int, primes: np.ndarray) -> list[tuple[int, int]]:
@@ -293,6 +295,25 @@ def exact(kind: int, n: int) -> np.ndarray:
     if m > cap:
         raise ValueError("cap too small")
     return out[:m].copy()
+
+
+def exact_mt(kind: int, n: int, threads: int | None = None) -> np.ndarray:
+    """``exact`` on several host threads (product-tree halves and large
+    Karatsuba sub-products as OpenMP tasks); the same integer."""
+    cap = bound_limbs(kind, n)
+    out = np.zeros(cap, dtype=np.uint32)
+    t = max_threads() if threads is None else int(threads)
+    m = lib().orc_exact_mt(kind, n, _p32(out), cap, t)
+    if m == _U64_MAX:
+        raise ValueError("not integral")
+    if m > cap:
+        raise ValueError("cap too small")
+    return out[:m].copy()
+
+
+def max_threads() -> int:
+    """Host threads ``exact_mt`` can use (1 when built without OpenMP)."""
+    return int(lib().orc_max_threads())
 
 
 def catalan(n: int) -> np.ndarray:

@@ -31,6 +31,17 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Multi-threaded runs (orc_exact_mt only): the two halves of a product tree
+ * and the three sub-products of a Karatsuba step become OpenMP tasks when they
+ * are at least this large.  Outside a parallel region a task runs at once in
+ * the calling thread, so every other entry point stays single-threaded and
+ * computes in exactly the order written. */
+#define ORC_TASK_MIN_LIMBS 2048
+#define ORC_TASK_MIN_VALUES 4096
 
 typedef uint32_t limb_t;
 typedef unsigned __int128 u128;
@@ -148,15 +159,6 @@ uint64_t orc_legendre(uint64_t m, uint64_t p)
         pk *= p;
     }
     return s;
-}
-
-/* p-adic valuation of a positive integer x. */
-uint64_t orc_valuation(uint64_t x, uint64_t p)
-{
-    uint64_t v = 0;
-    if (x == 0) return 0;
-    while (x % p == 0) { x /= p; v++; }
-    return v;
 }
 
 /* Algorithm 1 step 2: factor m = n+1 by trial division with the primes up to
@@ -375,10 +377,14 @@ static void mul_karatsuba(const limb_t *a, const limb_t *b, uint64_t n, limb_t *
     sa[hh] = add_into(sa, hh, a0, h);
     sb[hh] = add_into(sb, hh, b0, h);
     limb_t *z1 = calloc(2 * (hh + 1), sizeof(limb_t));
-    mul_karatsuba(sa, sb, hh + 1, z1);
     memset(out, 0, sizeof(limb_t) * 2 * n);
+    /* the three products are independent (disjoint outputs) */
+#pragma omp task if (n >= ORC_TASK_MIN_LIMBS)
+    mul_karatsuba(sa, sb, hh + 1, z1);
+#pragma omp task if (n >= ORC_TASK_MIN_LIMBS)
     mul_karatsuba(a0, b0, h, out);                 /* z0 -> out[0, 2h)     */
     mul_karatsuba(a1, b1, hh, out + 2 * h);        /* z2 -> out[2h, 2n)    */
+#pragma omp taskwait
     sub_from(z1, 2 * (hh + 1), out, 2 * h);         /* z1 -= z0             */
     sub_from(z1, 2 * (hh + 1), out + 2 * h, 2 * hh); /* z1 -= z2            */
     add_into(out + h, 2 * n - h, z1, norm_len(z1, 2 * (hh + 1)));
@@ -457,7 +463,11 @@ static big_t tree_u32(const uint32_t *v, uint64_t count)
     if (count == 0) return big_from_u64(1);
     if (count == 1) return big_from_u64(v[0]);
     uint64_t h = count / 2;
-    big_t l = tree_u32(v, h), r = tree_u32(v + h, count - h);
+    big_t l, r;
+#pragma omp task shared(l) if (count >= ORC_TASK_MIN_VALUES)
+    l = tree_u32(v, h);
+    r = tree_u32(v + h, count - h);
+#pragma omp taskwait
     big_t p = big_mul(l, r);
     free(l.d); free(r.d);
     return p;
@@ -472,7 +482,11 @@ static big_t tree_big(big_t *v, uint64_t count)
         return c;
     }
     uint64_t h = count / 2;
-    big_t l = tree_big(v, h), r = tree_big(v + h, count - h);
+    big_t l, r;
+#pragma omp task shared(l) if (count >= 4)
+    l = tree_big(v, h);
+    r = tree_big(v + h, count - h);
+#pragma omp taskwait
     big_t p = big_mul(l, r);
     free(l.d); free(r.d);
     return p;
@@ -563,6 +577,30 @@ uint64_t orc_exact(int kind, uint64_t n, limb_t *out, uint64_t cap)
     uint64_t len = orc_reconstruct(ng, exps, offs, gp, out, cap);
     free(pr); free(e); free(exps); free(offs); free(gp);
     return len;
+}
+
+/* orc_exact run by `threads` threads: the same steps and the same code, with
+ * the product tree's halves and the large Karatsuba sub-products executed as
+ * OpenMP tasks (the integer is the same; only the schedule changes).  Used to
+ * time the oracle on all host cores.  Without OpenMP it runs single-threaded. */
+uint64_t orc_exact_mt(int kind, uint64_t n, limb_t *out, uint64_t cap, int threads)
+{
+    uint64_t len = 0;
+    if (threads < 1) threads = 1;
+#pragma omp parallel num_threads(threads)
+#pragma omp single
+    len = orc_exact(kind, n, out, cap);
+    return len;
+}
+
+/* Threads orc_exact_mt can use: the processors OpenMP sees, or 1 without it. */
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_num_procs();
+#else
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------------ */

@@ -1224,7 +1224,8 @@ extern "C" int bigint_mul_noalloc(const uint32_t *a, size_t na, const uint32_t *
 {
     using namespace cat;
     if (!out_len || (na && !a) || (nb && !b) || (cap && !out)) return CAT_EINVAL;
-    if (na + nb > kNoAllocMaxLimbs) return CAT_ENOMEM;  // beyond the static scratch
+    // beyond the static scratch (written so that na + nb cannot wrap around)
+    if (na > kNoAllocMaxLimbs || nb > kNoAllocMaxLimbs - na) return CAT_ENOMEM;
     if (cap < na + nb) return CAT_ERANGE;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CAT_ECUDA;

@@ -175,5 +175,50 @@ def test_paper_scale_decimal(ctx):
     h = capi.to_numpy(r)
     x = int.from_bytes(h.astype("<u4").tobytes(), "little")
     assert tail == str(x % 10**18).zfill(18).encode()
+    # every digit: the decimal string mod four seeded 31-bit primes (plain
+    # torch integer arithmetic, independent of the conversion) against the
+    # oracle's residues of the binary limbs
+    for q in orc_check_primes(4):
+        assert _decimal_mod(d, q) == _orc().limbs_mod(h, q), q
     del d, r
     torch.cuda.empty_cache()
+
+
+def _orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def orc_check_primes(count):
+    return _orc().check_primes(seed=1234567890, count=count, lower=1 << 30, bits=31)
+
+
+def _decimal_mod(d, q: int) -> int:
+    """The value of the ASCII digit string d (a device tensor, most
+    significant digit first) mod q < 2^31: nine-digit chunks c_i (leading
+    zeros prepended so that the count divides by nine), then
+    sum_i c_i B^(m-1-i) mod q with B = 10^9, the powers B^j mod q built by
+    doubling (B^(j+k) = B^j B^k).  Every product is below 2^61 in int64."""
+    import torch
+    dev = d.device
+    nd = d.numel()
+    pad = (-nd) % 9
+    digits = torch.cat([torch.full((pad,), 48, dtype=torch.uint8, device=dev), d.view(-1)])
+    p10 = torch.tensor([10 ** (8 - k) for k in range(9)], dtype=torch.int64, device=dev)
+    m = digits.numel() // 9
+    chunks = torch.zeros(m, dtype=torch.int64, device=dev)
+    step = 1 << 24
+    for i in range(0, m, step):
+        part = digits[9 * i: 9 * min(m, i + step)].view(-1, 9).to(torch.int64) - 48
+        chunks[i: i + part.shape[0]] = (part * p10).sum(dim=1)
+    pw = torch.ones(1, dtype=torch.int64, device=dev)  # B^0
+    bk = 10 ** 9 % q                                    # B^k for k = len(pw)
+    while pw.numel() < m:
+        pw = torch.cat([pw, (pw * bk) % q])
+        bk = bk * bk % q
+    pw = pw[:m].flip(0)                                 # chunk i weighs B^(m-1-i)
+    acc = 0
+    for i in range(0, m, step):
+        acc += int((((chunks[i: i + step] % q) * pw[i: i + step]) % q).sum().item())
+    return acc % q

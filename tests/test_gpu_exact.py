@@ -231,3 +231,39 @@ def test_paper_scale(ctx, cat_lib, orc):
     assert have == want
     # Table 1's SHA-256 of the paper's own result file
     assert sha == t["sha256"]
+
+
+def read_groups(name):
+    """sieved / positive / sha256 rows and 'exponent count' rows of an
+    oracle-written Phase-1 golden file."""
+    head, groups = {}, []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        k, v = line.split()
+        if k in ("sieved", "positive", "sha256"):
+            head[k] = v
+        else:
+            groups.append((int(k), int(v)))
+    return head, groups
+
+
+@pytest.mark.slow
+def test_paper_scale_factor_vs_oracle_groups(ctx, cat_lib):
+    """Phase 1 at n = 2,050,572,903 (Algorithm 1 at Table 1's scale) against
+    the oracle's grouping: the number of primes <= 2n, the number with
+    e_p > 0, every group's exponent and size, and the SHA-256 of all grouped
+    primes in CSR order (tests/golden/make_oracle_golden.py --paper)."""
+    head, groups = read_groups("oracle_groups_catalan_2050572903.txt")
+    f = cat_lib.catalan_factor(ctx, 2_050_572_903, 0)
+    try:
+        assert f.primes_sieved == int(head["sieved"])
+        assert int(f.offsets[-1]) == int(head["positive"])
+        assert f.exps.tolist() == [e for e, _ in groups]
+        counts = np.diff(np.asarray(f.offsets.tolist(), dtype=np.int64)).tolist()
+        assert counts == [c for _, c in groups]
+        got = host(f.primes())
+        assert hashlib.sha256(got.astype("<u4").tobytes()).hexdigest() == head["sha256"]
+    finally:
+        f.free()

@@ -73,3 +73,20 @@ def test_batch_bound_is_the_sum_of_bounds(cat_lib):
     assert e.value.code == cat_lib.CAT_EINVAL
     with pytest.raises(cat_lib.CatError):
         cat_lib.cat_batch_bound([(3, 10)])                    # unknown kind
+
+
+def test_noalloc_size_check_on_the_host(cat_lib):
+    # bigint_mul_noalloc rejects sizes beyond its static scratch before any
+    # device work, including lengths whose sum would wrap around size_t (the
+    # pointers are never dereferenced, so no GPU is needed)
+    import ctypes
+    L = cat_lib.load()
+    n = ctypes.c_size_t()
+    fake = ctypes.c_void_p(16)
+    big = (1 << 64) - 1
+    for na, nb in [(big, 2), (2, big), (cat_lib.NOALLOC_MAX_LIMBS + 1, 0),
+                   (cat_lib.NOALLOC_MAX_LIMBS, 1), (1 << 63, 1 << 63)]:
+        rc = L.bigint_mul_noalloc(fake, na, fake, nb, fake, big, ctypes.byref(n), None)
+        assert rc == cat_lib.CAT_ENOMEM, (na, nb)
+    rc = L.bigint_mul_noalloc(fake, 4, fake, 4, fake, 7, ctypes.byref(n), None)
+    assert rc == cat_lib.CAT_ERANGE  # cap below na + nb, still before device work

@@ -429,3 +429,17 @@ def test_ratio_not_integral(orc):
         with pytest.raises(ValueError):
             orc.ratio_exact(a, b)
     assert orc.limbs_to_int(orc.ratio_exact([7], [2, 2, 2, 2])) == 315
+
+
+def test_exact_mt_matches_single_thread_and_cpython(orc):
+    # the OpenMP variant (tree halves and Karatsuba sub-products as tasks)
+    # computes the same integers: against CPython's math.comb / factorial at
+    # small n, against the single-threaded oracle where the tasks really split
+    for kind, n in [(0, 0), (0, 1), (0, 77), (1, 5000), (2, 3000), (0, 20000)]:
+        want = {0: math.comb(2 * n, n) // (n + 1), 1: math.comb(2 * n, n),
+                2: math.factorial(n)}[kind]
+        assert orc.limbs_to_int(orc.exact_mt(kind, n, threads=4)) == want, (kind, n)
+    for kind, n in [(0, 300_000), (2, 200_000)]:
+        a = orc.exact(kind, n)
+        for t in (1, 3, orc.max_threads()):
+            assert np.array_equal(orc.exact_mt(kind, n, threads=t), a), (kind, n, t)
