@@ -85,13 +85,18 @@ int cat_ctx_memory(const cat_ctx *ctx, size_t *in_use, size_t *peak);
 int cat_ctx_set_profiling(cat_ctx *ctx, int on);
 
 /* Totals for the i-th kernel name seen since profiling was switched on:
- * launches, summed device milliseconds, summed algorithmic bytes (the bytes
- * the launch must read and write at minimum) and summed algorithmic 32-bit
- * integer operations (the instruction count of the minimal sequence for the
- * arithmetic the launch performs; 0 where not counted).  *name is owned by ctx.
- * Returns CAT_ERANGE when i is past the last entry. */
+ * launches, summed device milliseconds, summed pass bytes (the bytes the
+ * launch itself must read and write at minimum, e.g. three residue arrays in
+ * and out for a transform pass) and summed unit bytes: the algorithmic bytes
+ * of the products the launches completed, 4 bytes per limb of each operand
+ * read once and of each product written once (for a level of the product
+ * tree, 8 bytes per limb of the level).  A product's unit bytes are counted
+ * on the one launch that holds its pointwise step (the transform's row pass,
+ * the one-block multiply, a schoolbook or leaf kernel) and are 0 for its other
+ * launches.  *name is owned by ctx.  Returns CAT_ERANGE when i is past the
+ * last entry. */
 int cat_ctx_profile(const cat_ctx *ctx, size_t i, const char **name, uint64_t *launches,
-                    double *ms, double *bytes, double *ops);
+                    double *ms, double *bytes, double *unit_bytes);
 
 /* ------------------------------------------------------------------ Phase 1
  * Grouped prime factorisation of the quantity (Sec. 3.1, Algorithm 1):
@@ -302,14 +307,16 @@ int to_decimal(cat_ctx *ctx, const uint32_t *limbs, size_t n, char *out, size_t 
  * A continuous-batching request engine on one device (the paper has a single
  * offline run; this is the serving layer around the same computation).
  * `workers` threads each own a context and a CUDA stream.  An idle worker
- * admits the queued requests in arrival order while their estimated device
- * footprint fits its share of hbm_budget_bytes (0 = no cap; at least one
- * request is always admitted) and at most max_batch of them (0 = 4096), and
- * computes them together with cat_exact_batch.  The footprint estimate is
- * 256 bytes per limb of the result bound (cat_bound_limbs); cat_server_submit
- * denies (CAT_ENOMEM) a request whose estimate alone exceeds the budget, and
- * every worker's context is capped at the budget, so a batch that still
- * outgrows it fails with CAT_ENOMEM for its tickets.  Requests that arrive while
+ * admits the queued requests in arrival order, at most max_batch of them
+ * (0 = 4096), while their estimated device footprint plus the estimates of
+ * the batches already running plus the results still held fits
+ * hbm_budget_bytes (0 = no cap; a worker admits one request when nothing
+ * else is running), and computes them together with cat_exact_batch.  The
+ * footprint estimate is 256 bytes per limb of the result bound
+ * (cat_bound_limbs) plus 2 MiB (cat_batch_footprint); cat_server_submit
+ * denies (CAT_ENOMEM) a request whose estimate alone exceeds the budget.  All workers' scratch and results count
+ * against one shared cap of hbm_budget_bytes, so a batch that still outgrows
+ * it fails with CAT_ENOMEM for its tickets.  Requests that arrive while
  * batches are running are admitted by the next idle worker, so batches
  * overlap on the GPU.  Results stay in device memory until released.
  * All functions are thread-safe. */
@@ -350,6 +357,18 @@ int cat_server_fetch(cat_server *sv, uint64_t ticket, uint32_t *dst, size_t cap,
 
 /* Forgets a finished ticket and frees its result (CAT_EBUSY while pending). */
 int cat_server_release(cat_server *sv, uint64_t ticket);
+
+/* The serving engine's estimate of the device bytes `count` requests hold
+ * while they are computed together: for each request 2 MiB plus 256 bytes per
+ * limb of cat_bound_limbs (measured peaks: at most 1.35 MB for tiny n and at
+ * most 124 bytes per limb from n = 10^4 to 3 * 10^8), summed.  Admission
+ * compares it with the budget.  Errors: CAT_EINVAL. */
+int cat_batch_footprint(const cat_request *reqs, size_t count, size_t *bytes);
+
+/* Device bytes all workers hold now (scratch and results) and their
+ * high-water mark since creation; both stay within hbm_budget_bytes when it
+ * is set.  Errors: CAT_EINVAL. */
+int cat_server_memory(cat_server *sv, size_t *in_use, size_t *peak);
 
 /* Requests waiting for admission / tickets held (queued, running, done). */
 int cat_server_pending(cat_server *sv, size_t *queued, size_t *total);

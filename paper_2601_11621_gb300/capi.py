@@ -34,7 +34,8 @@ EXPORTED = ["cat_ctx_create", "cat_ctx_destroy", "cat_last_error", "cat_ctx_memo
             "catalan_exact", "cat_exact_host", "cat_batch_bound", "cat_exact_batch",
             "cat_server_create", "cat_server_submit", "cat_server_poll", "cat_server_wait",
             "cat_server_fetch", "cat_server_release", "cat_server_pending",
-            "cat_server_destroy", "cat_decimal_bound", "to_decimal",
+            "cat_server_destroy", "cat_server_memory", "cat_batch_footprint",
+            "cat_decimal_bound", "to_decimal",
             "cat_ratio_bound_limbs", "cat_ratio_factor", "cat_ratio_exact",
             "cat_factor_text", "cat_binary"]
 
@@ -136,6 +137,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cat_exact_host.restype = i32
     u64p = ctypes.POINTER(ctypes.c_uint64)
     L.cat_batch_bound.argtypes = [ctypes.POINTER(Request), sz, szp]
+    L.cat_batch_footprint.argtypes = [ctypes.POINTER(Request), sz, szp]
+    L.cat_server_memory.argtypes = [vp, szp, szp]
+    L.cat_server_memory.restype = i32
+    L.cat_batch_footprint.restype = i32
     L.cat_batch_bound.restype = i32
     L.cat_exact_batch.argtypes = [vp, ctypes.POINTER(Request), sz, vp, sz, u64p, u64p, vp]
     L.cat_exact_batch.restype = i32
@@ -197,7 +202,8 @@ class Context:
         self.check(load().cat_ctx_set_profiling(self.handle, 1 if on else 0))
 
     def profile(self) -> dict:
-        """{kernel name: (launches, total ms, total algorithmic bytes, total ops)}."""
+        """{kernel name: (launches, total ms, total pass bytes, total unit bytes)}
+        (cat_ctx_profile)."""
         out = {}
         i = 0
         while True:
@@ -476,6 +482,15 @@ def cat_batch_bound(reqs) -> int:
     rc = load().cat_batch_bound(_requests(reqs), len(reqs), ctypes.byref(total))
     if rc != 0:
         raise CatError(rc, "cat_batch_bound")
+    return total.value
+
+
+def cat_batch_footprint(reqs) -> int:
+    """The serving engine's device-byte estimate for a batch of (kind, n)."""
+    total = ctypes.c_size_t()
+    rc = load().cat_batch_footprint(_requests(reqs), len(reqs), ctypes.byref(total))
+    if rc != 0:
+        raise CatError(rc, "cat_batch_footprint")
     return total.value
 
 

@@ -133,7 +133,7 @@ int cat_ctx_set_profiling(cat_ctx *ctx, int on)
 }
 
 int cat_ctx_profile(const cat_ctx *ctx, size_t i, const char **name, uint64_t *launches,
-                    double *ms, double *bytes, double *ops)
+                    double *ms, double *bytes, double *unit_bytes)
 {
     if (!ctx) return CAT_EINVAL;
     if (i >= ctx->c.prof.size()) return CAT_ERANGE;
@@ -142,7 +142,7 @@ int cat_ctx_profile(const cat_ctx *ctx, size_t i, const char **name, uint64_t *l
     if (launches) *launches = e.launches;
     if (ms) *ms = e.ms;
     if (bytes) *bytes = e.bytes;
-    if (ops) *ops = e.ops;
+    if (unit_bytes) *unit_bytes = e.unit_bytes;
     return CAT_OK;
 }
 

@@ -10,6 +10,7 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -347,20 +348,25 @@ struct ProfEntry {
     uint64_t launches = 0;
     double ms = 0;
     double bytes = 0;
-    double ops = 0;  // algorithmic 32-bit integer operations
+    double unit_bytes = 0;  // algorithmic bytes of the products the launches completed
 };
 
 struct ProfPending {
     int idx;
     cudaEvent_t a, b;
     double bytes;
-    double ops;
+    double unit_bytes;
 };
 
 struct Ctx {
     int device = 0;
     size_t budget = 0;   // 0 = unlimited
     size_t in_use = 0;
+    // A budget shared with other contexts (the serving engine's workers): the
+    // bytes all of them hold, and their common cap (0 = none).
+    std::atomic<size_t> *shared_in_use = nullptr;
+    std::atomic<size_t> *shared_peak = nullptr;  // high-water mark of *shared_in_use
+    size_t shared_budget = 0;
     size_t peak = 0;
     std::string last_error;
     uint2 *twiddles = nullptr;  // [set][prime][dir][kTwPerDir] multiplier pairs
@@ -377,7 +383,11 @@ struct Ctx {
 // profiling is off); prof_end records the stop event and the launch's
 // algorithmic bytes.  prof_resolve turns finished pairs into totals.
 int prof_begin(Ctx &c, const char *name, cudaStream_t s);
-void prof_end(Ctx &c, int token, cudaStream_t s, double bytes, double ops = 0);
+// unit_bytes: the algorithmic bytes of the products the launch completes
+// (operands read once and the product written once, 4 bytes per limb each),
+// counted on the one launch of a product that holds its pointwise step (the
+// row pass, the one-block multiply, a schoolbook or leaf kernel); 0 elsewhere.
+void prof_end(Ctx &c, int token, cudaStream_t s, double bytes, double unit_bytes = 0);
 void prof_resolve(Ctx &c);
 
 // Where the limbs of a batch of products go: product k at out + k *

@@ -225,7 +225,8 @@ void leaf_level(Ctx &c, const uint32_t *values, size_t count, uint32_t *out, siz
     const int tok = prof_begin(c, "leaf_products", s);
     leaf_products<<<(unsigned)((nodes + 255) / 256), 256, 0, s>>>(values, count, out, nodes);
     CAT_LAUNCH("leaf_products");
-    prof_end(c, tok, s, 4.0 * (double)count + 32.0 * (double)nodes, 2.0 * 36.0 * (double)nodes);
+    prof_end(c, tok, s, 4.0 * (double)count + 32.0 * (double)nodes,
+             4.0 * (double)count + 32.0 * (double)nodes);
 }
 
 // Products of adjacent slot-limb nodes into 2*slot-limb slots, for slots
@@ -249,8 +250,7 @@ bool comba_level(Ctx &c, const uint32_t *in, size_t slot, size_t nprod, uint32_t
     default: return false;
     }
     CAT_LAUNCH("comba_level");
-    prof_end(c, tok, s, 16.0 * (double)slot * (double)nprod,
-             3.0 * (double)slot * (double)slot * (double)nprod);
+    prof_end(c, tok, s, 16.0 * (double)slot * (double)nprod, 16.0 * (double)slot * (double)nprod);
     return true;
 }
 

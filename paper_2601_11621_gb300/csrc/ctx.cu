@@ -57,10 +57,25 @@ void *dev_alloc(Ctx &c, size_t bytes, cudaStream_t s)
         fail(CAT_ENOMEM, "scratch would exceed the context's HBM budget (" +
                              std::to_string(c.in_use + bytes) + " > " +
                              std::to_string(c.budget) + " bytes)");
+    if (c.shared_in_use) {
+        const size_t before = c.shared_in_use->fetch_add(bytes);
+        if (c.shared_budget && before + bytes > c.shared_budget) {
+            c.shared_in_use->fetch_sub(bytes);
+            fail(CAT_ENOMEM, "scratch would exceed the shared HBM budget (" +
+                                 std::to_string(before + bytes) + " > " +
+                                 std::to_string(c.shared_budget) + " bytes)");
+        }
+        if (c.shared_peak) {
+            size_t pk = c.shared_peak->load();
+            while (before + bytes > pk && !c.shared_peak->compare_exchange_weak(pk, before + bytes)) {
+            }
+        }
+    }
     void *p = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool_for(c.device), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        if (c.shared_in_use) c.shared_in_use->fetch_sub(bytes);
         fail(CAT_ENOMEM, "device allocation of " + std::to_string(bytes) +
                              " bytes failed: " + cudaGetErrorString(e));
     }
@@ -75,6 +90,7 @@ void dev_free(Ctx &c, void *p, size_t bytes, cudaStream_t s)
     bytes = (bytes + 255) & ~(size_t)255;
     cudaFreeAsync(p, s);
     c.in_use -= bytes;
+    if (c.shared_in_use) c.shared_in_use->fetch_sub(bytes);
 }
 
 // --------------------------------------------------------------- profiler
@@ -107,12 +123,12 @@ int prof_begin(Ctx &c, const char *name, cudaStream_t s)
     return (int)c.pending.size() - 1;
 }
 
-void prof_end(Ctx &c, int token, cudaStream_t s, double bytes, double ops)
+void prof_end(Ctx &c, int token, cudaStream_t s, double bytes, double unit_bytes)
 {
     if (token < 0) return;
     ProfPending &p = c.pending[token];
     p.bytes = bytes;
-    p.ops = ops;
+    p.unit_bytes = unit_bytes;
     CAT_CUDA(cudaEventRecord(p.b, s));
 }
 
@@ -126,7 +142,7 @@ void prof_resolve(Ctx &c)
             e.launches++;
             e.ms += ms;
             e.bytes += p.bytes;
-            e.ops += p.ops;
+            e.unit_bytes += p.unit_bytes;
         }
         c.event_pool.push_back(p.a);
         c.event_pool.push_back(p.b);

@@ -700,9 +700,7 @@ static void col_pass(Ctx &c, int ps, bool fwd, uint32_t *data, size_t pstride, s
         }
     }
     CAT_LAUNCH(fwd ? "ntt_col_fwd" : "ntt_col_inv");
-    // algorithmic ops: r/2 butterflies of 12 ops per point and one twiddle
-    // product (11 ops) per point, three primes
-    prof_end(c, tok, s, bytes, 3.0 * (double)total * (6.0 * r + 11.0));
+    prof_end(c, tok, s, bytes);
 }
 
 template <int LR, int PS>
@@ -796,8 +794,12 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     ra.scale = make_scale(PS, n);
     int tok = prof_begin(c, "ntt_row_mul", s);
     launch_row(PS, P.rrow, nprod, n, s, ra);
-    prof_end(c, tok, s, (mode == PAIR_SQUARE ? 24.0 : 36.0) * (double)gp,
-             3.0 * (double)gp * ((mode == PAIR_SQUARE ? 12.0 : 18.0) * P.rrow + 12.0));
+    // the products' own bytes: operands read and products written once
+    const double unit = 4.0 * (double)nprod * (double)(x.len + sink.out_len) +
+                        (mode == PAIR_SQUARE ? 0.0
+                         : mode == PAIR_BROADCAST ? 4.0 * (double)y.len
+                                                  : 4.0 * (double)nprod * (double)y.len);
+    prof_end(c, tok, s, (mode == PAIR_SQUARE ? 24.0 : 36.0) * (double)gp, unit);
     F.reset();
     // inverse column passes, reverse order
     for (int i = P.ncol - 1; i >= 0; i--) {
@@ -822,8 +824,7 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     else
         crt_carry_tiles<2><<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
     CAT_LAUNCH("crt_carry_tiles");
-    prof_end(c, tok, s, 12.0 * (double)gp + 4.0 * (double)nprod * (double)sink.out_len,
-             40.0 * (double)gp);
+    prof_end(c, tok, s, 12.0 * (double)gp + 4.0 * (double)nprod * (double)sink.out_len);
     tok = prof_begin(c, "carry_tile_scan", s);
     carry_tile_scan<<<(unsigned)nprod, 1024, 0, s>>>(maps.get(), tiles);
     CAT_LAUNCH("carry_tile_scan");
@@ -877,10 +878,9 @@ static void ntt_mul_small(Ctx &c, int n, size_t nprod, Operand x, Operand y, boo
     default: fail(CAT_EINVAL, "one-block transform size out of range");
     }
     CAT_LAUNCH("ntt_mul_fused");
-    const double Lf = (double)(1u << n);
-    prof_end(c, tok, s,
-             4.0 * (double)nprod * (double)(x.len + (square ? 0 : y.len) + sink.out_len),
-             (double)nprod * ((square ? 36.0 : 54.0) * Lf * n + 36.0 * Lf + 40.0 * Lf));
+    const double unit =
+        4.0 * (double)nprod * (double)(x.len + (square ? 0 : y.len) + sink.out_len);
+    prof_end(c, tok, s, unit, unit);
 }
 
 static int ceil_log2(size_t x)

@@ -2,16 +2,20 @@
 //
 // Requests (kind, n) are queued as they are submitted.  Each worker thread
 // owns a context and a CUDA stream; whenever it is idle it admits the queued
-// requests in arrival order while their estimated device footprint fits its
-// share of the HBM budget (at least one), runs them as one batch
-// (exact_batch), and publishes every result.  While one worker's batch is on
-// the GPU, requests that arrive meanwhile are admitted by the next idle
-// worker, so batches overlap on the device.  Results stay in device memory
-// until the client fetches or releases them; buffers are freed by the worker
-// that allocated them.
+// requests in arrival order while their estimated device footprint, added to
+// the estimates of the batches already running and to the results still held
+// by clients, fits the server's HBM budget (a worker with nothing else
+// running always admits one), runs them as one batch (exact_batch), and
+// publishes every result.  While one worker's batch is on the GPU, requests
+// that arrive meanwhile are admitted by the next idle worker, so batches
+// overlap on the device.  All workers' contexts draw on one shared byte
+// counter capped at the budget, so the budget also bounds what they really
+// hold together.  Results stay in device memory until the client fetches or
+// releases them; buffers are freed by the worker that allocated them.
 #include "cat_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -37,9 +41,12 @@ uint64_t now_ns()
         .count();
 }
 
-// Scratch per result limb while a request is on the device: the level
-// arrays, the three-prime transforms of both operands and of the products,
-// and the leaves, with headroom.
+// Device bytes a request may hold while it is computed: a fixed part (sieve
+// segments, small tables: measured at most 1.35 MB) and a part per limb of
+// the result bound (level arrays, three-prime transforms, leaves: measured at
+// most 124 bytes per limb from n = 10^4 to 3 * 10^8, all three kinds), with
+// headroom; a batch's estimate is the sum over its requests.
+constexpr uint64_t kFootprintFixed = 2u << 20;
 constexpr uint64_t kFootprintPerLimb = 256;
 
 struct Worker;
@@ -73,6 +80,10 @@ struct cat_server {
     int device = 0;
     size_t budget = 0;
     size_t max_batch = 4096;
+    std::atomic<size_t> used{0};  // bytes all workers' contexts hold (hard cap)
+    std::atomic<size_t> used_peak{0};
+    size_t reserved = 0;          // footprint estimates of the running batches
+    size_t resident = 0;          // bytes of results still held by clients
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<uint64_t> queue;
@@ -88,28 +99,49 @@ namespace {
 void release_buf(cat_server *sv, ResultBuf *b)
 {
     // caller holds sv->mu
-    if (--b->refs == 0) b->owner->to_free.push_back(b);
+    if (--b->refs == 0) {
+        sv->resident -= b->bytes;
+        b->owner->to_free.push_back(b);
+    }
+}
+
+uint64_t footprint(const cat_request &r)
+{
+    return kFootprintFixed + cat::bound_limbs(r.n, r.kind) * kFootprintPerLimb;
+}
+
+// Whether f more bytes of estimated footprint may start now (caller holds
+// sv->mu): always when nothing is running, else when the running batches'
+// estimates, the resident results and f fit the budget.
+bool fits(const cat_server *sv, uint64_t f)
+{
+    return !sv->budget || sv->reserved == 0 || sv->resident + sv->reserved + f <= sv->budget;
 }
 
 void worker_loop(cat_server *sv, Worker *w)
 {
     cudaSetDevice(sv->device);
-    const size_t share = sv->budget / sv->workers.size();
     for (;;) {
         std::vector<uint64_t> tickets;
         std::vector<cat_request> reqs;
         std::vector<ResultBuf *> frees;
         uint64_t batch_id = 0;
+        uint64_t foot = 0;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
-            sv->cv_work.wait(lk, [&] { return sv->stop || !sv->queue.empty() || !w->to_free.empty(); });
+            sv->cv_work.wait(lk, [&] {
+                return sv->stop || !w->to_free.empty() ||
+                       (!sv->queue.empty() && fits(sv, footprint(sv->jobs[sv->queue.front()].req)));
+            });
             frees.swap(w->to_free);
             if (sv->stop && sv->queue.empty() && frees.empty()) return;
-            uint64_t foot = 0;
             while (!sv->queue.empty() && reqs.size() < sv->max_batch) {
                 Job &j = sv->jobs[sv->queue.front()];
-                const uint64_t f = cat::bound_limbs(j.req.n, j.req.kind) * kFootprintPerLimb;
-                if (!reqs.empty() && share && foot + f > share) break;
+                const uint64_t f = footprint(j.req);
+                if (!fits(sv, foot + f)) break;
+                if (!reqs.empty() && sv->budget &&
+                    sv->resident + sv->reserved + foot + f > sv->budget)
+                    break;
                 foot += f;
                 j.state = 1;
                 j.t_start = now_ns();
@@ -117,6 +149,7 @@ void worker_loop(cat_server *sv, Worker *w)
                 reqs.push_back(j.req);
                 sv->queue.pop_front();
             }
+            sv->reserved += foot;
             batch_id = sv->next_batch++;
         }
         for (ResultBuf *b : frees) {
@@ -149,6 +182,7 @@ void worker_loop(cat_server *sv, Worker *w)
         const uint64_t t_end = now_ns();
         {
             std::lock_guard<std::mutex> lk(sv->mu);
+            sv->reserved -= foot;
             for (size_t i = 0; i < tickets.size(); i++) {
                 auto it = sv->jobs.find(tickets[i]);
                 if (it == sv->jobs.end()) continue;  // released while running
@@ -166,7 +200,10 @@ void worker_loop(cat_server *sv, Worker *w)
                     j.error = rc;
                 }
             }
-            if (buf->refs == 0) w->to_free.push_back(buf);
+            if (buf->refs == 0)
+                w->to_free.push_back(buf);
+            else
+                sv->resident += buf->bytes;
         }
         if (rc != CAT_OK && buf->p == nullptr) {
             std::lock_guard<std::mutex> lk(sv->mu);
@@ -195,7 +232,11 @@ int cat_server_create(int device, size_t hbm_budget_bytes, int workers, size_t m
     try {
         for (int i = 0; i < workers; i++) {
             auto w = std::make_unique<Worker>();
-            cat::ctx_init(w->ctx, device, hbm_budget_bytes);  // hard cap per worker
+            cat::ctx_init(w->ctx, device, 0);
+            // one hard cap for all workers together
+            w->ctx.shared_in_use = &sv->used;
+            w->ctx.shared_peak = &sv->used_peak;
+            w->ctx.shared_budget = hbm_budget_bytes;
             cat::check_cuda(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking),
                             "cudaStreamCreateWithFlags");
             sv->workers.push_back(std::move(w));
@@ -219,8 +260,7 @@ int cat_server_submit(cat_server *sv, int kind, uint64_t n, uint64_t *ticket)
         return CAT_EINVAL;
     // admission denial: a request whose estimated footprint alone exceeds the
     // whole budget is never queued
-    if (sv->budget && cat::bound_limbs(n, kind) * kFootprintPerLimb > sv->budget)
-        return CAT_ENOMEM;
+    if (sv->budget && footprint(cat_request{kind, n}) > sv->budget) return CAT_ENOMEM;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (sv->stop) return CAT_EINVAL;
@@ -281,6 +321,7 @@ int cat_server_fetch(cat_server *sv, uint64_t ticket, uint32_t *dst, size_t cap,
     if (!sv || !out_len || (cap && !dst)) return CAT_EINVAL;
     const uint32_t *src = nullptr;
     uint64_t len = 0;
+    ResultBuf *buf = nullptr;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         auto it = sv->jobs.find(ticket);
@@ -289,15 +330,23 @@ int cat_server_fetch(cat_server *sv, uint64_t ticket, uint32_t *dst, size_t cap,
         if (it->second.state == 3) return it->second.error;
         src = it->second.buf->p + it->second.off;
         len = it->second.len;
+        *out_len = len;
+        if (len > cap) return CAT_ERANGE;
+        // the buffer stays allocated while the copy reads it, even if another
+        // thread releases the ticket meanwhile
+        buf = it->second.buf;
+        buf->refs++;
     }
-    *out_len = len;
-    if (len > cap) return CAT_ERANGE;
     cudaSetDevice(sv->device);
-    if (len && cudaMemcpy(dst, src, 4 * len,
-                          to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice) !=
-                   cudaSuccess)
-        return CAT_ECUDA;
-    return CAT_OK;
+    const bool ok = !len || cudaMemcpy(dst, src, 4 * len,
+                                       to_host ? cudaMemcpyDeviceToHost
+                                               : cudaMemcpyDeviceToDevice) == cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        release_buf(sv, buf);
+    }
+    sv->cv_work.notify_all();
+    return ok ? CAT_OK : CAT_ECUDA;
 }
 
 int cat_server_release(cat_server *sv, uint64_t ticket)
@@ -312,6 +361,28 @@ int cat_server_release(cat_server *sv, uint64_t ticket)
         sv->jobs.erase(it);
     }
     sv->cv_work.notify_all();
+    return CAT_OK;
+}
+
+int cat_batch_footprint(const cat_request *reqs, size_t count, size_t *bytes)
+{
+    if (!bytes || (count && !reqs)) return CAT_EINVAL;
+    uint64_t t = 0;
+    for (size_t i = 0; i < count; i++) {
+        if (reqs[i].n >= (1ull << 31) || reqs[i].kind < CAT_CATALAN ||
+            reqs[i].kind > CAT_FACTORIAL)
+            return CAT_EINVAL;
+        t += footprint(reqs[i]);
+    }
+    *bytes = (size_t)t;
+    return CAT_OK;
+}
+
+int cat_server_memory(cat_server *sv, size_t *in_use, size_t *peak)
+{
+    if (!sv) return CAT_EINVAL;
+    if (in_use) *in_use = sv->used.load();
+    if (peak) *peak = sv->used_peak.load();
     return CAT_OK;
 }
 

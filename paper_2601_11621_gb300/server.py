@@ -61,6 +61,14 @@ class Server:
     def release(self, ticket: int) -> int:
         return capi.load().cat_server_release(self.h, ticket)
 
+    def memory(self):
+        """(bytes all workers hold now, their high-water mark)."""
+        a, b = ctypes.c_size_t(), ctypes.c_size_t()
+        rc = capi.load().cat_server_memory(self.h, ctypes.byref(a), ctypes.byref(b))
+        if rc != 0:
+            raise capi.CatError(rc, "cat_server_memory")
+        return a.value, b.value
+
     def pending(self):
         q, t = ctypes.c_size_t(), ctypes.c_size_t()
         capi.load().cat_server_pending(self.h, ctypes.byref(q), ctypes.byref(t))

@@ -63,3 +63,47 @@ def test_ticket_errors(cat_lib, server):
     assert r.length > 0 and r.t_end_ns >= r.t_start_ns >= r.t_submit_ns
     assert server.release(t) == 0
     assert server.release(t) == -1  # already released
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_footprint_estimate_covers_measured_peak(cat_lib, kind):
+    # admission's estimate (cat_batch_footprint) against the device bytes a
+    # fresh context really holds at its peak, for single requests and batches
+    for n in (0, 100, 1000, 10**4, 10**5, 10**6, 10**7):
+        c = cat_lib.Context(0)
+        try:
+            cat_lib.cat_exact(c, kind, n)
+            peak = c.memory()[1]
+        finally:
+            c.close()
+        assert peak <= cat_lib.cat_batch_footprint([(kind, n)]), (kind, n, peak)
+    reqs = [(k, n) for _, k, n in W.served_requests(24, 300.0, seed=kind, lo=1e3, hi=3e6)]
+    c = cat_lib.Context(0)
+    try:
+        cat_lib.cat_exact_batch(c, reqs)
+        peak = c.memory()[1]
+    finally:
+        c.close()
+    assert peak <= cat_lib.cat_batch_footprint(reqs)
+
+
+def test_server_budget_bounds_all_workers_together(cat_lib, ctx):
+    # a mix whose estimates add up to over three times the budget: batches are
+    # admitted only while they fit, the bytes all workers hold together never
+    # pass the budget, and every result equals the request computed alone
+    from paper_2601_11621_gb300.server import Server
+    reqs = [(k, n) for _, k, n in W.served_requests(40, 300.0, seed=11, lo=1e5, hi=4e6)]
+    budget = 3 * max(cat_lib.cat_batch_footprint([r]) for r in reqs) // 2
+    assert cat_lib.cat_batch_footprint(reqs) > 3 * budget
+    sv = Server(0, hbm_budget_bytes=budget, workers=3, max_batch=64)
+    try:
+        tickets = [sv.submit(k, n) for k, n in reqs]
+        got = [sv.fetch_host(t) for t in tickets]
+        _, peak = sv.memory()
+        for t in tickets:
+            sv.release(t)
+    finally:
+        sv.close()
+    assert 0 < peak <= budget
+    for (k, n), g in zip(reqs, got):
+        assert np.array_equal(g, alone(ctx, cat_lib, k, n)), (k, n)
