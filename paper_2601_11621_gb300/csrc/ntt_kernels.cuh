@@ -224,8 +224,28 @@ __device__ __forceinline__ void dit_smem(uint32_t *s, const uint2 *Ti, uint32_t 
 // A column pass block holds C columns of 2^LR rows: 16 columns at 2^10 rows
 // (64 KiB), otherwise 2^(13-LR) columns (8192 points, 32 KiB), so that
 // every thread has a group to work on even for short columns.
-__host__ __device__ constexpr int col_log_c(int lr) { return lr >= 10 ? 4 : 13 - lr; }
-constexpr int kColThreads = 512;
+// Launch shapes of the passes (tuning knobs; the defaults are the measured
+// best): points per column-pass block 2^kColPtsLog (at least 16 columns),
+// threads per column-pass block, and the row pass's minimum resident blocks
+// per SM (which caps its registers).
+#ifndef CAT_COL_PTS_LOG
+#define CAT_COL_PTS_LOG 13
+#endif
+#ifndef CAT_COL_THREADS
+#define CAT_COL_THREADS 512
+#endif
+#ifndef CAT_COL_FWD_RMAX
+#define CAT_COL_FWD_RMAX 3
+#endif
+#ifndef CAT_COL_INV_RMAX
+#define CAT_COL_INV_RMAX 3
+#endif
+#ifndef CAT_ROW_MINB
+#define CAT_ROW_MINB 1
+#endif
+constexpr int kColPtsLog = CAT_COL_PTS_LOG;
+__host__ __device__ constexpr int col_log_c(int lr) { return lr >= kColPtsLog - 4 ? 4 : kColPtsLog - lr; }
+constexpr int kColThreads = CAT_COL_THREADS;
 constexpr int kColMinLog = 4;   // columns of at least 2^4 rows
 constexpr int kColMaxLog = 10;  // and at most 2^10
 // Most stages per register round in the forward and inverse column passes.
@@ -233,8 +253,8 @@ constexpr int kColMaxLog = 10;  // and at most 2^10
 // four 512-thread blocks share an SM instead of two at 64 registers with
 // four-stage rounds (measured per C(2,050,572,903): inverse passes 25.1 ->
 // 22.1 ms, forward passes 45.5 -> 45.1 ms).
-constexpr int kColFwdRoundMax = 3;
-constexpr int kColInvRoundMax = 3;
+constexpr int kColFwdRoundMax = CAT_COL_FWD_RMAX;
+constexpr int kColInvRoundMax = CAT_COL_INV_RMAX;
 __host__ __device__ constexpr int col_rounds(int lr, int most) { return (lr + most - 1) / most; }
 
 struct ColArgs {
@@ -501,7 +521,7 @@ struct RowOut {
 // product k.  The last forward round, the product and the first inverse round
 // share one register round (their stage bits coincide).
 template <int LR, bool SQ, int PS>
-__global__ void __launch_bounds__(kRowThreads) ntt_row_mul(RowArgs a)
+__global__ void __launch_bounds__(kRowThreads, CAT_ROW_MINB) ntt_row_mul(RowArgs a)
 {
     extern __shared__ uint32_t sm[];
     constexpr int NR = rounds_of(LR);
