@@ -439,6 +439,16 @@ def main():
         dist.init_process_group("nccl")
     build.build()
     ctx = capi.Context(local_rank)
+    # the library's autotuner picks the transform plans and the schoolbook
+    # crossover for this device; its table goes next to the library, where
+    # every context created later (the serving engine's too) reads it
+    tune_path = os.path.join(os.path.dirname(capi.LIB_PATH), "autotune.txt")
+    t0 = time.perf_counter()
+    ctx.autotune(tune_path if rank == 0 else None)
+    tune_s = time.perf_counter() - t0
+    slot, rows = ctx.tuning()
+    tuning = {"seconds": round(tune_s, 2), "comba_max_slot": slot,
+              "row_log": {str(k): v for k, v in rows.items()}}
     n = args.n
     cap = capi.cat_bound_limbs(n, capi.CAT_CATALAN)
     out = torch.empty(cap, dtype=torch.int32, device=dev)
@@ -551,6 +561,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(4 * hres.size)},
             "gpu_launches": int(round(launches_per_step * args.steps)),
+            "autotune": tuning,
             "roofline": roof,
             "cpu_baseline": cpu,
             **extras,

@@ -64,9 +64,17 @@ typedef enum {
 typedef struct cat_ctx cat_ctx;
 
 /* Creates a context on CUDA device `device`.  hbm_budget_bytes caps the
- * scratch the context may hold at once (0 = no cap).  The context owns the
- * NTT twiddle tables and the scratch pool.  Returns CAT_OK and *out, or an
- * error (CAT_EINVAL, CAT_ECUDA). */
+ * scratch the context may hold at once (0 = no cap).  When the in-core
+ * reconstruction of a quantity would not fit the cap (about 128 bytes per
+ * result limb), cat_exact, catalan_exact, cat_exact_host and cat_ratio_exact
+ * reconstruct it within the cap instead, the paper's chunked products with
+ * partial products kept in pinned host memory (Sec. 3.2): the primes are
+ * multiplied in chunks sized to the cap, and products too large for it run by
+ * pieces through a sliding device window.  The result is the same integer,
+ * computed more slowly.  Phase 1 itself runs in-core (about 0.5 bytes per
+ * integer up to 2n plus 4 bytes per prime) and fails with CAT_ENOMEM if that
+ * does not fit.  The context owns the NTT twiddle tables and the scratch pool.
+ * Returns CAT_OK and *out, or an error (CAT_EINVAL, CAT_ECUDA). */
 int cat_ctx_create(int device, size_t hbm_budget_bytes, cat_ctx **out);
 
 /* Frees the context and everything it owns.  NULL is ignored. */
@@ -74,6 +82,29 @@ void cat_ctx_destroy(cat_ctx *ctx);
 
 /* Text of the last error recorded in ctx ("" if none).  Owned by ctx. */
 const char *cat_last_error(const cat_ctx *ctx);
+
+/* ------------------------------------------------------------ autotuning
+ * The device-dependent choices of the product tree's multiplications (the
+ * paper leaves them to its bignum library): the row-pass size of the
+ * multi-pass transform for each transform size 2^13 .. 2^23, and the largest
+ * tree-level slot (32 .. 256 limbs) multiplied by schoolbook (Comba) rather
+ * than by the transform.
+ *
+ * cat_autotune: times every candidate on a synthetic tree level of 2^24
+ * limbs on ctx's device (about a second; scratch from the context's pool),
+ * applies the fastest to ctx and, when path is not NULL, writes them as a
+ * text table tagged with the device's name and SM count.  Results of every
+ * entry point are the same integers with any choice; only speed changes.
+ * cat_ctx_load_tuning: applies a table written by cat_autotune
+ * (CAT_EINVAL when it is unreadable or was made on another kind of device).
+ * A new context reads the table at $CAT_TUNE_FILE, else autotune.txt next to
+ * libcatalan.so, when it exists and matches the device.
+ * cat_ctx_tuning: the values in use: the crossover slot, and row_log[n] for
+ * n < count (0 = the default plan).  Errors: CAT_EINVAL, CAT_ENOMEM,
+ * CAT_ECUDA. */
+int cat_autotune(cat_ctx *ctx, const char *path, void *stream);
+int cat_ctx_load_tuning(cat_ctx *ctx, const char *path);
+int cat_ctx_tuning(const cat_ctx *ctx, size_t *comba_max_slot, int *row_log, size_t count);
 
 /* Bytes of scratch currently held / the high-water mark since creation. */
 int cat_ctx_memory(const cat_ctx *ctx, size_t *in_use, size_t *peak);

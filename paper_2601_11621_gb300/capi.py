@@ -27,6 +27,7 @@ CAT_OK, CAT_EINVAL, CAT_ENOMEM, CAT_ERANGE = 0, -1, -2, -3
 CAT_ENOTINTEGRAL, CAT_ETIMEOUT, CAT_ECUDA, CAT_EBUSY = -4, -5, -6, -7
 
 EXPORTED = ["cat_ctx_create", "cat_ctx_destroy", "cat_last_error", "cat_ctx_memory",
+            "cat_autotune", "cat_ctx_load_tuning", "cat_ctx_tuning",
             "cat_ctx_set_profiling", "cat_ctx_profile",
             "catalan_factor", "cat_factor_free", "cat_factor_copy_primes", "bigint_mul",
             "bigint_mul_noalloc", "bigint_pow",
@@ -85,6 +86,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cat_ctx_destroy.restype = None
     L.cat_last_error.argtypes = [vp]
     L.cat_last_error.restype = ctypes.c_char_p
+    L.cat_autotune.argtypes = [vp, ctypes.c_char_p, vp]
+    L.cat_autotune.restype = i32
+    L.cat_ctx_load_tuning.argtypes = [vp, ctypes.c_char_p]
+    L.cat_ctx_load_tuning.restype = i32
+    L.cat_ctx_tuning.argtypes = [vp, szp, ctypes.POINTER(i32), sz]
+    L.cat_ctx_tuning.restype = i32
     L.cat_ctx_memory.argtypes = [vp, szp, szp]
     L.cat_ctx_memory.restype = i32
     L.cat_ctx_set_profiling.argtypes = [vp, i32]
@@ -197,6 +204,22 @@ class Context:
         a, b = ctypes.c_size_t(), ctypes.c_size_t()
         self.check(load().cat_ctx_memory(self.handle, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def autotune(self, path: str | None = None, stream=None):
+        """cat_autotune: measure, apply and (with path) save the tuned choices."""
+        self.check(load().cat_autotune(self.handle, path.encode() if path else None,
+                                       _stream(stream)))
+
+    def load_tuning(self, path: str):
+        """cat_ctx_load_tuning."""
+        self.check(load().cat_ctx_load_tuning(self.handle, path.encode()))
+
+    def tuning(self) -> tuple[int, dict]:
+        """(crossover slot, {n: row-pass log2 size} for the tuned sizes)."""
+        slot = ctypes.c_size_t()
+        rows = (ctypes.c_int * 28)()
+        self.check(load().cat_ctx_tuning(self.handle, ctypes.byref(slot), rows, 28))
+        return slot.value, {n: rows[n] for n in range(28) if rows[n]}
 
     def set_profiling(self, on: bool):
         self.check(load().cat_ctx_set_profiling(self.handle, 1 if on else 0))

@@ -116,6 +116,33 @@ const char *cat_last_error(const cat_ctx *ctx)
     return ctx ? ctx->c.last_error.c_str() : "";
 }
 
+int cat_autotune(cat_ctx *ctx, const char *path, void *stream)
+{
+    if (!ctx) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        cat::autotune(ctx->c, as_stream(stream));
+        if (path) cat::save_tuning(ctx->c, path);
+    });
+}
+
+int cat_ctx_load_tuning(cat_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return CAT_EINVAL;
+    return guarded(ctx, [&] {
+        if (!cat::load_tuning(ctx->c, path))
+            cat::fail(CAT_EINVAL, std::string("no tuning table for this device at ") + path);
+    });
+}
+
+int cat_ctx_tuning(const cat_ctx *ctx, size_t *comba_max_slot, int *row_log, size_t count)
+{
+    if (!ctx || (count && !row_log)) return CAT_EINVAL;
+    if (comba_max_slot) *comba_max_slot = ctx->c.comba_max_slot;
+    for (size_t n = 0; n < count; n++)
+        row_log[n] = n <= (size_t)cat::kLogMaxNtt ? ctx->c.row_log[n] : 0;
+    return CAT_OK;
+}
+
 int cat_ctx_memory(const cat_ctx *ctx, size_t *in_use, size_t *peak)
 {
     if (!ctx) return CAT_EINVAL;
@@ -239,6 +266,10 @@ int cat_exact(cat_ctx *ctx, int kind, uint64_t n, uint32_t *out, size_t cap,
         cat_factorization f{};
         cat::factor(ctx->c, n, kind, &f, s);
         try {
+            if (cat::reconstruct_out_of_core(ctx->c, &f)) {
+                cat::reconstruct_into(ctx->c, &f, out, cap, false, out_len, s);
+                return;
+            }
             cat::Big r = cat::reconstruct(ctx->c, &f, s);
             cat::factor_free(ctx->c, &f);
             copy_out(ctx->c, r, out, cap, out_len, s);
@@ -275,6 +306,10 @@ int cat_ratio_exact(cat_ctx *ctx, const uint64_t *a, int ka, const uint64_t *b, 
         cat_factorization f{};
         cat::factor_ratio(ctx->c, q, &f, s);
         try {
+            if (cat::reconstruct_out_of_core(ctx->c, &f)) {
+                cat::reconstruct_into(ctx->c, &f, out, cap, false, out_len, s);
+                return;
+            }
             cat::Big r = cat::reconstruct(ctx->c, &f, s);
             cat::factor_free(ctx->c, &f);
             copy_out(ctx->c, r, out, cap, out_len, s);
@@ -322,6 +357,10 @@ int cat_exact_host(cat_ctx *ctx, int kind, uint64_t n, uint32_t *host_out, size_
         cat::factor(ctx->c, n, kind, &f, s);
         cat::Big r;
         try {
+            if (cat::reconstruct_out_of_core(ctx->c, &f)) {
+                cat::reconstruct_into(ctx->c, &f, host_out, cap, true, out_len, s);
+                return;
+            }
             r = cat::reconstruct(ctx->c, &f, s);
         } catch (...) {
             cat::factor_free(ctx->c, &f);

@@ -373,6 +373,10 @@ struct Ctx {
     int num_sms = 0;
     size_t comba_max_slot = 128;  // tree levels with slots up to this use schoolbook
     int max_log = kLogMaxNtt;     // longest single transform; longer products go by pieces
+    // row-pass size (log2 points) of the multi-pass transform of 2^n points,
+    // as tuned on this device (cat_autotune); 0 = the default plan
+    int row_log[kLogMaxNtt + 1] = {};
+    std::string tuning;           // where the tuned values came from ("" = defaults)
     bool profiling = false;
     std::vector<ProfEntry> prof;
     std::vector<ProfPending> pending;
@@ -421,6 +425,9 @@ struct NvtxRange {
 // Fills h[kTwTotal] with the twiddle tables of all sets (host side).
 constexpr size_t kTwTotal = (size_t)kNumSets * kNumPrimes * 2 * kTwPerDir;
 void twiddle_tables_host(uint2 *h);
+// Copies the first 16 entries of every stage table of h into the constant
+// memory of the current device (ntt.cu).
+void upload_low_twiddles(const uint2 *h);
 
 // Device allocation from the context's stream-ordered pool (cudaMallocAsync on
 // the device's default memory pool, whose release threshold is raised at
@@ -562,6 +569,13 @@ void factor_free(Ctx &c, cat_factorization *f);
 void copy_to_host(Ctx &c, uint32_t *host, const uint32_t *dev, size_t n, cudaStream_t s);
 // Algorithm 2 on a factorisation; returns the result (normalised length).
 Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s);
+// Whether the in-core reconstruction of f would exceed the context's HBM
+// budget, and Algorithm 2 within the budget (ooc.cu): releases f (its primes
+// move to pinned host memory), multiplies by chunks and pieces, and copies
+// the result (*out_len limbs) to out, device memory or (to_host) host memory.
+bool reconstruct_out_of_core(const Ctx &c, const cat_factorization *f);
+void reconstruct_into(Ctx &c, cat_factorization *f, uint32_t *out, size_t cap, bool to_host,
+                      size_t *out_len, cudaStream_t s);
 
 // The factorisation as the paper's text layout (Sec. 3.1) into out (device),
 // titled `name`; the binary result file (bytes 01 01, then the magnitude
@@ -572,6 +586,13 @@ int binary_file(Ctx &c, const uint32_t *x, size_t n, uint8_t *out, size_t cap, s
                 cudaStream_t s);
 
 size_t bound_limbs(uint64_t n, int kind);
+
+// The tuned choices of the multiplication (autotune.cu): measure and apply
+// them, write or read a table, and the table a new context reads.
+void autotune(Ctx &c, cudaStream_t s);
+void save_tuning(const Ctx &c, const char *path);
+bool load_tuning(Ctx &c, const char *path);
+std::string default_tuning_path();
 size_t ratio_bound_limbs(const Ratio &r);
 
 }  // namespace cat

@@ -230,6 +230,7 @@ static void build_twiddles(Ctx &c)
     CAT_CUDA(cudaMalloc(&c.twiddles, h.size() * sizeof(uint2)));
     CAT_CUDA(cudaMemcpy(c.twiddles, h.data(), h.size() * sizeof(uint2),
                         cudaMemcpyHostToDevice));
+    upload_low_twiddles(h.data());
 }
 
 void ctx_init(Ctx &c, int device, size_t budget)
@@ -241,6 +242,9 @@ void ctx_init(Ctx &c, int device, size_t budget)
     c.device = device;
     c.budget = budget;
     CAT_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, device));
+    // a tuning table made on this kind of device, if there is one
+    const std::string tp = default_tuning_path();
+    if (!tp.empty()) load_tuning(c, tp.c_str());
     if (const char *e = getenv("CAT_COMBA_MAX_SLOT")) c.comba_max_slot = strtoull(e, nullptr, 10);
     // a lower single-transform limit sends shorter products through the piece
     // path (used to exercise it at small sizes)

@@ -46,6 +46,24 @@ __constant__ uint32_t c_wp1[kNumSets][kNumPrimes] = CAT_SET_CONST(CAT_WP1);
 #undef CAT_Q
 #undef CAT_WP1
 
+// Entries [0, 16) of every stage table (the twiddles of stage bits below 4,
+// [set][prime][direction][index] in the stage table's own layout and
+// multiplier form), for the register rounds with B = 0, whose twiddle indices
+// are compile-time constants: served from constant memory they are uniform
+// operands instead of registers held across the round.
+__constant__ uint2 c_tw_low[kNumSets][kNumPrimes][2][16];
+
+void upload_low_twiddles(const uint2 *tables)
+{
+    uint2 h[kNumSets][kNumPrimes][2][16];
+    for (int set = 0; set < kNumSets; set++)
+        for (int p = 0; p < kNumPrimes; p++)
+            for (int d = 0; d < 2; d++)
+                for (int j = 0; j < 16; j++)
+                    h[set][p][d][j] = tables[(((size_t)set * kNumPrimes + p) * 2 + d) * kTwPerDir + j];
+    CAT_CUDA(cudaMemcpyToSymbol(c_tw_low, h, sizeof(h)));
+}
+
 // Garner constants of a set, in Montgomery form.
 template <int PS>
 struct Garner {
@@ -520,8 +538,8 @@ __global__ void __launch_bounds__(kFusedThreads, 2) ntt_mul_fused(FusedArgs a)
 #pragma unroll 1
     for (int p = 0; p < kNumPrimes; p++) {
         const uint32_t q = c_q[0][p], qinv = c_qinv[0][p], wp1 = c_wp1[0][p];
-        const uint2 *T = tw_table(a.tw, 0, p, 0);
-        const uint2 *Ti = tw_table(a.tw, 0, p, 1);
+        const TwRef T{tw_table(a.tw, 0, p, 0), p};
+        const TwRef Ti{tw_table(a.tw, 0, p, 1), p};
         const uint2 sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
         uint32_t *Z = Rr[p];
         if constexpr (NR == 1) {
@@ -612,11 +630,23 @@ struct NttPlan {
 
 // Row pass of up to 2^12 points (at least 2^4 so column passes keep 16
 // columns), column passes of at most 2^10 rows, split as evenly as possible.
-static NttPlan make_plan(int n)
+// A row-pass size tuned for this device (Ctx::row_log, prime set 0 only:
+// rows of 2^9 .. 2^12 points, every column pass at least 2 rows) replaces
+// the default.
+bool plan_row_ok(int n, int rrow)
+{
+    if (set_for(n) != 0 || rrow < 9 || rrow > kRowMaxLog) return false;
+    const int rem = n - rrow;
+    const int ncol = (rem + kColMaxLog - 1) / kColMaxLog;
+    return rem >= 2 && ncol <= 2 && rem / ncol >= 2;
+}
+
+static NttPlan make_plan(const Ctx &c, int n)
 {
     NttPlan P;
     P.n = n;
     P.rrow = std::min(kRowMaxLog, n - kColMinLog);
+    if (n <= kLogMaxNtt && c.row_log[n] && plan_row_ok(n, c.row_log[n])) P.rrow = c.row_log[n];
     int rem = n - P.rrow;
     P.ncol = (rem + kColMaxLog - 1) / kColMaxLog;
     for (int i = 0; i < P.ncol; i++) {
@@ -642,11 +672,11 @@ static void launch_col(bool fwd, dim3 grid, cudaStream_t s, const ColArgs &a)
 {
     const size_t smem = ((size_t)1 << (LR + col_log_c(LR))) * sizeof(uint32_t);
     if (fwd) {
-        set_smem(ntt_col_fwd<LR, PS>, smem);
-        ntt_col_fwd<LR, PS><<<grid, kColThreads, smem, s>>>(a);
+        set_smem(ntt_col_fwd<LR, PS, kColV>, smem);
+        ntt_col_fwd<LR, PS, kColV><<<grid, kColFwdThreads, smem, s>>>(a);
     } else {
-        set_smem(ntt_col_inv<LR, PS>, smem);
-        ntt_col_inv<LR, PS><<<grid, kColThreads, smem, s>>>(a);
+        set_smem(ntt_col_inv<LR, PS, kColV>, smem);
+        ntt_col_inv<LR, PS, kColV><<<grid, kColInvThreads, smem, s>>>(a);
     }
 }
 
@@ -756,7 +786,7 @@ struct Operand {
 static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, Operand y,
                               const Sink &sink, cudaStream_t s)
 {
-    const NttPlan P = make_plan(n);
+    const NttPlan P = make_plan(c, n);
     const int PS = set_for(n);
     const size_t L = (size_t)1 << n;
     const size_t ntf = mode == PAIR_ADJACENT ? 2 * nprod
@@ -1155,6 +1185,11 @@ static int noalloc_setup(int dev)
     if (cudaMemcpyToSymbol(g_noalloc_twiddles, g_noalloc_tw_host, sizeof(g_noalloc_tw_host)) !=
         cudaSuccess)
         return CAT_ECUDA;
+    try {
+        upload_low_twiddles(g_noalloc_tw_host);
+    } catch (...) {
+        return CAT_ECUDA;
+    }
     d.ready = true;
     return CAT_OK;
 }
@@ -1173,7 +1208,7 @@ static void noalloc_mul(const NoAllocDevice &d, const uint32_t *a, size_t na, co
         ntt_mul_small(local, n, 1, x, y, false, plain_sink(out, 0, len), s);
         return;
     }
-    const NttPlan P = make_plan(n);
+    const NttPlan P = make_plan(local, n);
     const size_t L = (size_t)1 << n;
     uint32_t *F = d.scratch;
     uint32_t *G = d.scratch + kNoAllocF;

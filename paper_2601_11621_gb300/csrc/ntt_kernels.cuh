@@ -69,10 +69,28 @@ __host__ __device__ constexpr int swz(int a)
     return a ^ t ^ ((t & 6) << 2) ^ ((t & 8) << 1);
 }
 
+// The twiddles of one direction of one prime: the stage table in global
+// memory, and the prime's index for the entries of stage bits below 4, which
+// rounds with B = 0 read from constant memory (c_tw_low): their indices are
+// compile-time constants, so the reads are uniform and need no registers.
+struct TwRef {
+    const uint2 *t;
+    int prime;
+};
+
+template <int PS, int DIR, bool LOW>
+__device__ __forceinline__ uint2 tw_at(const TwRef &T, int idx)
+{
+    if constexpr (LOW)
+        return c_tw_low[PS][T.prime][DIR][idx];
+    else
+        return __ldg(&T.t[idx]);
+}
+
 // In a round with B = 0 the twiddle index is a compile-time constant, and the
 // butterflies with (k mod 2^st) = 0 have twiddle w^0 = 1: no multiply.
 template <int E, int B, int NA, int PS>
-__device__ __forceinline__ void dif_stages(uint32_t (&x)[NA][1 << E], int glow, const uint2 *T,
+__device__ __forceinline__ void dif_stages(uint32_t (&x)[NA][1 << E], int glow, const TwRef &T,
                                            uint32_t q)
 {
 #pragma unroll
@@ -86,7 +104,7 @@ __device__ __forceinline__ void dif_stages(uint32_t (&x)[NA][1 << E], int glow, 
                 continue;
             }
             const int p = glow + ((k & ((1 << st) - 1)) << B);
-            const uint2 w = __ldg(&T[(1 << (B + st)) + p]);
+            const uint2 w = tw_at<PS, 0, (B == 0 && E <= 4)>(T, (1 << (B + st)) + p);
 #pragma unroll
             for (int a = 0; a < NA; a++) bf_dif<PS>(x[a][k], x[a][k + (1 << st)], w, q);
         }
@@ -94,7 +112,7 @@ __device__ __forceinline__ void dif_stages(uint32_t (&x)[NA][1 << E], int glow, 
 }
 
 template <int E, int B, int NA, int PS>
-__device__ __forceinline__ void dit_stages(uint32_t (&x)[NA][1 << E], int glow, const uint2 *Ti,
+__device__ __forceinline__ void dit_stages(uint32_t (&x)[NA][1 << E], int glow, const TwRef &Ti,
                                            uint32_t q)
 {
 #pragma unroll
@@ -108,7 +126,7 @@ __device__ __forceinline__ void dit_stages(uint32_t (&x)[NA][1 << E], int glow, 
                 continue;
             }
             const int p = glow + ((k & ((1 << st) - 1)) << B);
-            const uint2 w = __ldg(&Ti[(1 << (B + st)) + p]);
+            const uint2 w = tw_at<PS, 1, (B == 0 && E <= 4)>(Ti, (1 << (B + st)) + p);
 #pragma unroll
             for (int a = 0; a < NA; a++) bf_dit<PS>(x[a][k], x[a][k + (1 << st)], w, q);
         }
@@ -121,7 +139,7 @@ __device__ __forceinline__ void dit_stages(uint32_t (&x)[NA][1 << E], int glow, 
 // columns in global memory); otherwise consecutive threads take consecutive
 // groups of one column (contiguous rows in global memory).  No barrier.
 template <int LR, int C, int B, int E, bool FWD, int NA, bool COLFAST, int PS, class IN, class OUT>
-__device__ __forceinline__ void round_io(const IN &in, const OUT &out, const uint2 *T, uint32_t q)
+__device__ __forceinline__ void round_io(const IN &in, const OUT &out, const TwRef &T, uint32_t q)
 {
     constexpr int NGC = (1 << LR) >> E;  // groups per column
     constexpr int NG = C * NGC;
@@ -186,7 +204,7 @@ struct SmemIO {
 // points, so a round has C 2^(LR - E) groups for the block's threads.  Caller
 // synchronises before; these return synchronised.
 template <int LR, int C, int PS>
-__device__ __forceinline__ void dif_smem(uint32_t *s, const uint2 *T, uint32_t q)
+__device__ __forceinline__ void dif_smem(uint32_t *s, const TwRef &T, uint32_t q)
 {
     constexpr int NR = rounds_of(LR);
     SmemIO<LR, C, false> S{s};
@@ -203,7 +221,7 @@ __device__ __forceinline__ void dif_smem(uint32_t *s, const uint2 *T, uint32_t q
 }
 
 template <int LR, int C, int PS>
-__device__ __forceinline__ void dit_smem(uint32_t *s, const uint2 *Ti, uint32_t q)
+__device__ __forceinline__ void dit_smem(uint32_t *s, const TwRef &Ti, uint32_t q)
 {
     constexpr int NR = rounds_of(LR);
     SmemIO<LR, C, false> S{s};
@@ -224,35 +242,42 @@ __device__ __forceinline__ void dit_smem(uint32_t *s, const uint2 *Ti, uint32_t 
 // A column pass block holds C columns of 2^LR rows: 16 columns at 2^10 rows
 // (64 KiB), otherwise 2^(13-LR) columns (8192 points, 32 KiB), so that
 // every thread has a group to work on even for short columns.
-// Launch shapes of the passes (tuning knobs; the defaults are the measured
-// best): points per column-pass block 2^kColPtsLog (at least 16 columns),
-// threads per column-pass block, and the row pass's minimum resident blocks
-// per SM (which caps its registers).
-#ifndef CAT_COL_PTS_LOG
-#define CAT_COL_PTS_LOG 13
+// Launch shapes of the passes (compile-time knobs; the defaults are the
+// fastest measured per C(2,050,572,903) on GB300, 142.0 -> 125.7 ms with the
+// two-column groups below): threads per forward / inverse column-pass block,
+// the most stages per register round in those passes, and the minimum
+// resident blocks per SM of the row pass and of the forward column pass
+// (which cap their registers at 64: four blocks per SM).
+#ifndef CAT_COL_FWD_THREADS
+#define CAT_COL_FWD_THREADS 256
 #endif
-#ifndef CAT_COL_THREADS
-#define CAT_COL_THREADS 512
+#ifndef CAT_COL_INV_THREADS
+#define CAT_COL_INV_THREADS 256
 #endif
 #ifndef CAT_COL_FWD_RMAX
-#define CAT_COL_FWD_RMAX 3
+#define CAT_COL_FWD_RMAX 4
 #endif
 #ifndef CAT_COL_INV_RMAX
 #define CAT_COL_INV_RMAX 3
 #endif
 #ifndef CAT_ROW_MINB
-#define CAT_ROW_MINB 1
+#define CAT_ROW_MINB 4
 #endif
-constexpr int kColPtsLog = CAT_COL_PTS_LOG;
-__host__ __device__ constexpr int col_log_c(int lr) { return lr >= kColPtsLog - 4 ? 4 : kColPtsLog - lr; }
-constexpr int kColThreads = CAT_COL_THREADS;
+#ifndef CAT_COL_FWD_MINB
+#define CAT_COL_FWD_MINB 4
+#endif
+#ifndef CAT_COL_INV_MINB
+#define CAT_COL_INV_MINB 1
+#endif
+__host__ __device__ constexpr int col_log_c(int lr) { return lr >= 10 ? 4 : 13 - lr; }
+constexpr int kColFwdThreads = CAT_COL_FWD_THREADS;
+constexpr int kColInvThreads = CAT_COL_INV_THREADS;
 constexpr int kColMinLog = 4;   // columns of at least 2^4 rows
 constexpr int kColMaxLog = 10;  // and at most 2^10
-// Most stages per register round in the forward and inverse column passes.
-// Rounds of at most three stages keep the passes at 32 to 36 registers, so
-// four 512-thread blocks share an SM instead of two at 64 registers with
-// four-stage rounds (measured per C(2,050,572,903): inverse passes 25.1 ->
-// 22.1 ms, forward passes 45.5 -> 45.1 ms).
+// Most stages per register round in the forward and inverse column passes
+// (measured per C(2,050,572,903) with two-column groups: forward passes
+// 39.2 -> 35.0 ms with four-stage rounds at 64 registers, inverse passes
+// 17.7 ms with three-stage rounds against 18.9 with four).
 constexpr int kColFwdRoundMax = CAT_COL_FWD_RMAX;
 constexpr int kColInvRoundMax = CAT_COL_INV_RMAX;
 __host__ __device__ constexpr int col_rounds(int lr, int most) { return (lr + most - 1) / most; }
@@ -267,9 +292,47 @@ struct ColArgs {
     const uint2 *tw;
 };
 
-// Column tile in global memory: element (row, c) at p[row * S + col0 + c].
-// With `src`, elements come from limbs instead (zero past src_len, reduced).
-template <int PS>
+// Column tiles hold V adjacent columns per thread group: the group's V
+// columns c V + a (a < V) are the V arrays of the register round (NA = V), so
+// they share every stage twiddle, and global memory moves V adjacent words
+// with one V-word access.  In shared memory array a holds the columns
+// c V + a, back to back (SmemIO with C / V columns and NA = V).
+#ifndef CAT_COL_V
+#define CAT_COL_V 2
+#endif
+constexpr int kColV = CAT_COL_V;
+
+template <int V>
+__device__ __forceinline__ void load_v(const uint32_t *p, uint32_t (&w)[V])
+{
+    if constexpr (V == 4) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(p);
+        w[0] = t.x; w[1] = t.y; w[2] = t.z; w[3] = t.w;
+    } else if constexpr (V == 2) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        w[0] = t.x; w[1] = t.y;
+    } else {
+        w[0] = *p;
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void store_v(uint32_t *p, const uint32_t (&w)[V])
+{
+    if constexpr (V == 4)
+        *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    else if constexpr (V == 2)
+        *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+    else
+        *p = w[0];
+}
+
+// Column tile in global memory: element (row, col) at p[row * S + col0 + col],
+// group c covering columns c V .. c V + V - 1 (V-word aligned: S, col0 and
+// the array bases are multiples of 16 words).  With `src`, elements come from
+// limbs instead (zero past src_len, reduced), word by word, since a caller's
+// limbs need not be aligned.
+template <int PS, int V>
 struct ColIn {
     const uint32_t *p;
     const uint32_t *src;
@@ -278,14 +341,21 @@ struct ColIn {
     template <int E, int B, int NA>
     __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
-        const uint32_t i0 = (uint32_t)base * S + col0 + c;
+        static_assert(NA == V, "one array per column of the group");
+        const uint32_t i0 = (uint32_t)base * S + col0 + (uint32_t)c * V;
 #pragma unroll
         for (int k = 0; k < (1 << E); k++) {
             const uint32_t idx = i0 + (uint32_t)k * (S << B);
-            if (src)
-                x[0][k] = idx < src_len ? reduce_in<PS>(src[idx], q, wp1) : 0u;
-            else
-                x[0][k] = p[idx];
+            if (src) {
+#pragma unroll
+                for (int a = 0; a < V; a++)
+                    x[a][k] = idx + a < src_len ? reduce_in<PS>(src[idx + a], q, wp1) : 0u;
+            } else {
+                uint32_t w[V];
+                load_v<V>(p + idx, w);
+#pragma unroll
+                for (int a = 0; a < V; a++) x[a][k] = w[a];
+            }
         }
     }
 };
@@ -302,94 +372,123 @@ __host__ __device__ constexpr int bitrev_c(int j, int bits)
 // bitrev_LR(base + k) = bitrev_LR(base) + bitrev_E(k) 2^(LR - E) it is
 // W0 U^bitrev_E(k), W0 = w^(col bitrev_LR(base)), U = w^(col 2^(LR - E)) (in
 // units of the root order, hence the shift), so a group takes two table
-// products and one Montgomery product per point to step through the powers.
-template <int LR, int PS, int NR = rounds_of(LR)>
+// products and one Montgomery product per point to step through the powers,
+// for each of its V columns.
+template <int LR, int PS, int NR, int THREADS, int V>
 struct ColTw {
     const uint2 *T;
     uint32_t q, qinv;
-    int shift;   // log2(root order) - m
-    uint32_t u;  // U of this thread's column, when it has one column
+    int shift;      // log2(root order) - m
+    uint32_t u[V];  // U of this thread's columns, when its groups share them
     static constexpr int E = round_size(LR, NR - 1, NR);
-    static constexpr bool kOneColumn = (1 << col_log_c(LR)) <= kColThreads;
+    static constexpr int CV = (1 << col_log_c(LR)) / V;  // column groups per tile
+    static constexpr bool kOneColumn = CV <= THREADS;
     __device__ __forceinline__ uint32_t step_of(uint32_t gcol) const
     {
         return tw_pow_mont<PS>(T, gcol << (LR - E + shift), q, qinv);
     }
-    // Each thread's groups share one column when the tile has at most as many
-    // columns as the block has threads (c = threadIdx mod C): U once per thread.
+    // Each thread's groups share their columns when the tile has at most as
+    // many column groups as the block has threads (c = threadIdx mod CV): U
+    // once per thread and column.
     __device__ __forceinline__ void init(uint32_t col0)
     {
-        if (kOneColumn) u = step_of(col0 + (threadIdx.x & ((1u << col_log_c(LR)) - 1)));
+        if (kOneColumn) {
+            const uint32_t c0 = col0 + (threadIdx.x & (CV - 1)) * V;
+#pragma unroll
+            for (int a = 0; a < V; a++) u[a] = step_of(c0 + a);
+        }
     }
+    // f(k, v) for the group's rows k (in the order bitrev_E(j)), v[a] the
+    // twiddle of column gcol + a at row base + k
     template <int EE, class F>
     __device__ __forceinline__ void each(uint32_t gcol, int base, F &&f) const
     {
         static_assert(EE == E, "twiddles are applied in the round at stage bits [0, E)");
-        uint32_t v = tw_pow_mont<PS>(T, (gcol * bitrev((uint32_t)base, LR)) << shift, q, qinv);
-        const uint32_t uu = kOneColumn ? u : step_of(gcol);
+        const uint32_t br = bitrev((uint32_t)base, LR);
+        uint32_t v[V], uu[V];
+#pragma unroll
+        for (int a = 0; a < V; a++) {
+            v[a] = tw_pow_mont<PS>(T, ((gcol + a) * br) << shift, q, qinv);
+            uu[a] = kOneColumn ? u[a] : step_of(gcol + a);
+        }
 #pragma unroll
         for (int j = 0; j < (1 << E); j++) {
             f(bitrev_c(j, E), v);
-            if (j + 1 < (1 << E)) v = mont_step<PS>(v, uu, q, qinv);
+            if (j + 1 < (1 << E))
+#pragma unroll
+                for (int a = 0; a < V; a++) v[a] = mont_step<PS>(v[a], uu[a], q, qinv);
         }
     }
 };
 
 // Forward pass output: element (row, col) times w_M^(col * bitrev(row)).
-template <int LR, int PS, int NR = rounds_of(LR)>
+template <int LR, int PS, int NR, int V>
 struct ColOutTw {
     uint32_t *p;
     uint32_t S, col0;
-    ColTw<LR, PS, NR> tw;
+    ColTw<LR, PS, NR, kColFwdThreads, V> tw;
     template <int E, int B, int NA>
     __device__ __forceinline__ void store(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
-        static_assert(B == 0, "the twiddled round has contiguous rows");
-        const uint32_t gcol = col0 + c;
+        static_assert(B == 0 && NA == V, "the twiddled round has contiguous rows");
+        const uint32_t gcol = col0 + (uint32_t)c * V;
         const uint32_t i0 = (uint32_t)base * S + gcol;
-        tw.template each<E>(gcol, base, [&](int k, uint32_t v) {
-            p[i0 + (uint32_t)k * S] = mul_mont<PS>(x[0][k], v, tw.q, tw.qinv);
+        tw.template each<E>(gcol, base, [&](int k, const uint32_t(&v)[V]) {
+            uint32_t w[V];
+#pragma unroll
+            for (int a = 0; a < V; a++) w[a] = mul_mont<PS>(x[a][k], v[a], tw.q, tw.qinv);
+            store_v<V>(p + i0 + (uint32_t)k * S, w);
         });
     }
 };
 
 // Inverse pass input: element (row, col) times w_M^-(col * bitrev(row)).
-template <int LR, int PS, int NR = rounds_of(LR)>
+template <int LR, int PS, int NR, int V>
 struct ColInTw {
     const uint32_t *p;
     uint32_t S, col0;
-    ColTw<LR, PS, NR> tw;
+    ColTw<LR, PS, NR, kColInvThreads, V> tw;
     template <int E, int B, int NA>
     __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
-        static_assert(B == 0, "the twiddled round has contiguous rows");
-        const uint32_t gcol = col0 + c;
+        static_assert(B == 0 && NA == V, "the twiddled round has contiguous rows");
+        const uint32_t gcol = col0 + (uint32_t)c * V;
         const uint32_t i0 = (uint32_t)base * S + gcol;
-        tw.template each<E>(gcol, base, [&](int k, uint32_t v) {
-            x[0][k] = mul_mont<PS>(p[i0 + (uint32_t)k * S], v, tw.q, tw.qinv);
+        tw.template each<E>(gcol, base, [&](int k, const uint32_t(&v)[V]) {
+            uint32_t w[V];
+            load_v<V>(p + i0 + (uint32_t)k * S, w);
+#pragma unroll
+            for (int a = 0; a < V; a++) x[a][k] = mul_mont<PS>(w[a], v[a], tw.q, tw.qinv);
         });
     }
 };
 
+template <int V>
 struct ColOut {
     uint32_t *p;
     uint32_t S, col0;
     template <int E, int B, int NA>
     __device__ __forceinline__ void store(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
-        const uint32_t i0 = (uint32_t)base * S + col0 + c;
+        static_assert(NA == V, "one array per column of the group");
+        const uint32_t i0 = (uint32_t)base * S + col0 + (uint32_t)c * V;
 #pragma unroll
-        for (int k = 0; k < (1 << E); k++) p[i0 + (uint32_t)k * (S << B)] = x[0][k];
+        for (int k = 0; k < (1 << E); k++) {
+            uint32_t w[V];
+#pragma unroll
+            for (int a = 0; a < V; a++) w[a] = x[a][k];
+            store_v<V>(p + i0 + (uint32_t)k * (S << B), w);
+        }
     }
 };
 
 // Forward column pass: a 2^LR-point DIF down each of C consecutive columns of
 // one block (row stride S = 2^(m-LR)), then the twiddle w_M^(col * bitrev(row)).
-template <int LR, int PS>
-__global__ void __launch_bounds__(kColThreads) ntt_col_fwd(ColArgs a)
+template <int LR, int PS, int V>
+__global__ void __launch_bounds__(kColFwdThreads, CAT_COL_FWD_MINB) ntt_col_fwd(ColArgs a)
 {
     extern __shared__ uint32_t sm[];
-    constexpr int LC = col_log_c(LR), C = 1 << LC;
+    constexpr int LC = col_log_c(LR), C = 1 << LC, CV = C / V;
     // 2^4-row columns in one round, straight from global to global memory
     constexpr int NR = LR <= 4 ? 1 : col_rounds(LR, kColFwdRoundMax);
     static_assert(NR <= 4, "at most four rounds");
@@ -401,39 +500,39 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_fwd(ColArgs a)
     const size_t col0 = (blockIdx.x % groups) << LC;
     uint32_t *base = a.data + p * a.pstride + (blk << a.m);
     const uint2 *T = tw_table(a.tw, PS, p, 0);
-    const ColIn<PS> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, (uint32_t)Sr,
-                       (uint32_t)col0, (uint32_t)a.src_len,
-                       q, c_wp1[PS][p]};
-    ColTw<LR, PS, NR> tw{T, q, c_qinv[PS][p], set_log_root(PS) - a.m, 0u};
+    const TwRef TR{T, p};
+    const ColIn<PS, V> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, (uint32_t)Sr,
+                          (uint32_t)col0, (uint32_t)a.src_len, q, c_wp1[PS][p]};
+    ColTw<LR, PS, NR, kColFwdThreads, V> tw{T, q, c_qinv[PS][p], set_log_root(PS) - a.m, {}};
     tw.init((uint32_t)col0);
-    const ColOutTw<LR, PS, NR> out{base, (uint32_t)Sr, (uint32_t)col0, tw};
+    const ColOutTw<LR, PS, NR, V> out{base, (uint32_t)Sr, (uint32_t)col0, tw};
     if constexpr (NR == 1) {
-        round_io<LR, C, 0, LR, true, 1, true, PS>(in, out, T, q);
+        round_io<LR, CV, 0, LR, true, V, true, PS>(in, out, TR, q);
     } else {
-        const SmemIO<LR, C, true> sio{sm};
-        round_io<LR, C, dif_base(LR, 0, NR), round_size(LR, 0, NR), true, 1, true, PS>(in, sio,
-                                                                                      T, q);
+        const SmemIO<LR, CV, true> sio{sm};
+        round_io<LR, CV, dif_base(LR, 0, NR), round_size(LR, 0, NR), true, V, true, PS>(in, sio,
+                                                                                       TR, q);
         __syncthreads();
         if constexpr (NR >= 3) {
-            round_io<LR, C, dif_base(LR, 1, NR), round_size(LR, 1, NR), true, 1, true, PS>(
-                sio, sio, T, q);
+            round_io<LR, CV, dif_base(LR, 1, NR), round_size(LR, 1, NR), true, V, true, PS>(
+                sio, sio, TR, q);
             __syncthreads();
         }
         if constexpr (NR >= 4) {
-            round_io<LR, C, dif_base(LR, 2, NR), round_size(LR, 2, NR), true, 1, true, PS>(
-                sio, sio, T, q);
+            round_io<LR, CV, dif_base(LR, 2, NR), round_size(LR, 2, NR), true, V, true, PS>(
+                sio, sio, TR, q);
             __syncthreads();
         }
-        round_io<LR, C, 0, round_size(LR, NR - 1, NR), true, 1, true, PS>(sio, out, T, q);
+        round_io<LR, CV, 0, round_size(LR, NR - 1, NR), true, V, true, PS>(sio, out, TR, q);
     }
 }
 
 // Inverse column pass: undo the twiddle, then the DIT down each column.
-template <int LR, int PS>
-__global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
+template <int LR, int PS, int V>
+__global__ void __launch_bounds__(kColInvThreads, CAT_COL_INV_MINB) ntt_col_inv(ColArgs a)
 {
     extern __shared__ uint32_t sm[];
-    constexpr int LC = col_log_c(LR), C = 1 << LC;
+    constexpr int LC = col_log_c(LR), C = 1 << LC, CV = C / V;
     constexpr int NR = col_rounds(LR, kColInvRoundMax);
     static_assert(NR <= 4, "at most four rounds");
     const int p = blockIdx.y;
@@ -444,28 +543,29 @@ __global__ void __launch_bounds__(kColThreads) ntt_col_inv(ColArgs a)
     const size_t col0 = (blockIdx.x % groups) << LC;
     uint32_t *base = a.data + p * a.pstride + (blk << a.m);
     const uint2 *Ti = tw_table(a.tw, PS, p, 1);
-    ColTw<LR, PS, NR> tw{Ti, q, c_qinv[PS][p], set_log_root(PS) - a.m, 0u};
+    const TwRef TRi{Ti, p};
+    ColTw<LR, PS, NR, kColInvThreads, V> tw{Ti, q, c_qinv[PS][p], set_log_root(PS) - a.m, {}};
     tw.init((uint32_t)col0);
-    const ColInTw<LR, PS, NR> in{base, (uint32_t)Sr, (uint32_t)col0, tw};
-    const ColOut out{base, (uint32_t)Sr, (uint32_t)col0};
+    const ColInTw<LR, PS, NR, V> in{base, (uint32_t)Sr, (uint32_t)col0, tw};
+    const ColOut<V> out{base, (uint32_t)Sr, (uint32_t)col0};
     if constexpr (NR == 1) {
-        round_io<LR, C, 0, LR, false, 1, true, PS>(in, out, Ti, q);
+        round_io<LR, CV, 0, LR, false, V, true, PS>(in, out, TRi, q);
     } else {
-        const SmemIO<LR, C, true> sio{sm};
-        round_io<LR, C, 0, dit_size(LR, 0, NR), false, 1, true, PS>(in, sio, Ti, q);
+        const SmemIO<LR, CV, true> sio{sm};
+        round_io<LR, CV, 0, dit_size(LR, 0, NR), false, V, true, PS>(in, sio, TRi, q);
         __syncthreads();
         if constexpr (NR >= 3) {
-            round_io<LR, C, dit_base(LR, 1, NR), dit_size(LR, 1, NR), false, 1, true, PS>(
-                sio, sio, Ti, q);
+            round_io<LR, CV, dit_base(LR, 1, NR), dit_size(LR, 1, NR), false, V, true, PS>(
+                sio, sio, TRi, q);
             __syncthreads();
         }
         if constexpr (NR >= 4) {
-            round_io<LR, C, dit_base(LR, 2, NR), dit_size(LR, 2, NR), false, 1, true, PS>(
-                sio, sio, Ti, q);
+            round_io<LR, CV, dit_base(LR, 2, NR), dit_size(LR, 2, NR), false, V, true, PS>(
+                sio, sio, TRi, q);
             __syncthreads();
         }
-        round_io<LR, C, dit_base(LR, NR - 1, NR), dit_size(LR, NR - 1, NR), false, 1, true, PS>(
-            sio, out, Ti, q);
+        round_io<LR, CV, dit_base(LR, NR - 1, NR), dit_size(LR, NR - 1, NR), false, V, true, PS>(
+            sio, out, TRi, q);
     }
 }
 
@@ -541,8 +641,8 @@ __global__ void __launch_bounds__(kRowThreads, CAT_ROW_MINB) ntt_row_mul(RowArgs
     else { ta = 0; tb = 1; }
     const uint32_t *fa = a.F + p * a.fpstride + (ta << a.n) + off;
     const uint32_t *fb = a.F + p * a.fpstride + (tb << a.n) + off;
-    const uint2 *T = tw_table(a.tw, PS, p, 0);
-    const uint2 *Ti = tw_table(a.tw, PS, p, 1);
+    const TwRef T{tw_table(a.tw, PS, p, 0), p};
+    const TwRef Ti{tw_table(a.tw, PS, p, 1), p};
     const uint2 sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
     const SmemIO<LR, C, false> sio{sm};
     // forward rounds but the last
