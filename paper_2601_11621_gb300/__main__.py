@@ -1,11 +1,11 @@
 """Command line for the library (everything runs through the C ABI on cuda:0).
 
     python -m paper_2601_11621_gb300 exact N [--kind catalan|central_binomial|factorial]
-                                             [--bin FILE] [--decimal FILE]
+                                             [--repeat K] [--bin FILE] [--decimal FILE]
                                              [--factorization FILE] [--sha256]
-        The exact quantity of n (C(n) by default), timed, with the run's files as
-        the paper describes them: the result file (bytes 01 01, then the
-        little-endian magnitude), its decimal digits, and the grouped
+        The exact quantity of n (C(n) by default), timed (K times), with the run's
+        files as the paper describes them: the result file (bytes 01 01, then
+        the little-endian magnitude), its decimal digits, and the grouped
         factorisation as text.
 
     python -m paper_2601_11621_gb300 ratio --num A1 A2 ... --den B1 B2 ...
@@ -32,12 +32,13 @@ def cmd_exact(a) -> int:
     from . import capi
     ctx = capi.Context(0)
     kind = capi.KINDS[a.kind]
-    _sync()
-    t = time.perf_counter()
-    r = capi.cat_exact(ctx, kind, a.n)
-    _sync()
-    dt = time.perf_counter() - t
-    print(f"{a.kind}({a.n}): {r.numel()} limbs in {dt * 1e3:.1f} ms")
+    for _ in range(max(1, a.repeat)):
+        _sync()
+        t = time.perf_counter()
+        r = capi.cat_exact(ctx, kind, a.n)
+        _sync()
+        dt = time.perf_counter() - t
+        print(f"{a.kind}({a.n}): {r.numel()} limbs in {dt * 1e3:.1f} ms")
     if a.bin or a.sha256:
         data = capi.cat_binary(ctx, r).cpu().numpy().tobytes()
         if a.bin:
@@ -104,6 +105,7 @@ def main(argv=None) -> int:
     e.add_argument("--decimal")
     e.add_argument("--factorization")
     e.add_argument("--sha256", action="store_true")
+    e.add_argument("--repeat", type=int, default=1)
     r = sub.add_parser("ratio")
     r.add_argument("--num", type=int, nargs="*", default=[])
     r.add_argument("--den", type=int, nargs="*", default=[])

@@ -310,10 +310,16 @@ __device__ __forceinline__ void words_to_dec(uint32_t &w0, uint32_t &w1, uint32_
 // {0, 1, 2, 3}.  Writes limbs j < min(tile_len, out_count) to out and returns
 // the tile's carry map in compact form in *tile_map (valid in every thread; it
 // fits a byte).  The tile's own carry-in is assumed 0.
-__device__ void tile_carry(const CoefRun &r, uint32_t h1, uint32_t h2a, uint32_t h2b, int tile_len,
-                           uint32_t *out, long out_count, bool dec, const uint32_t *add,
-                           long add_count, uint32_t *wsm, uint32_t *tile_map)
+// DEC / ADD: 1 or 0 when known at compile time, -1 when the runtime flag
+// (dec, add != null) decides.
+template <int DEC, int ADD>
+__device__ __forceinline__ void tile_carry_t(const CoefRun &r, uint32_t h1, uint32_t h2a,
+                                             uint32_t h2b, int tile_len, uint32_t *out,
+                                             long out_count, bool dec_rt, const uint32_t *add,
+                                             long add_count, uint32_t *wsm, uint32_t *tile_map)
 {
+    const bool dec = DEC < 0 ? dec_rt : DEC == 1;
+    if (ADD == 0) add = nullptr;
     const int j0 = threadIdx.x * kLimbsPerThread;
     const uint32_t top = dec ? kDecBase - 1 : 0xffffffffu;  // largest limb
     uint32_t limb[kLimbsPerThread];
@@ -351,10 +357,25 @@ __device__ void tile_carry(const CoefRun &r, uint32_t h1, uint32_t h2a, uint32_t
             c = dec ? (uint32_t)(v >= kDecBase) : (uint32_t)(v >> 32);
             limb[i] = dec ? (uint32_t)(v - (uint64_t)c * kDecBase) : (uint32_t)v;
         }
+        if (j0 + kLimbsPerThread <= tile_len && j0 + kLimbsPerThread <= out_count &&
+            (reinterpret_cast<uintptr_t>(out + j0) & 15) == 0) {
+            uint4 *o4 = reinterpret_cast<uint4 *>(out + j0);
+            o4[0] = make_uint4(limb[0], limb[1], limb[2], limb[3]);
+            o4[1] = make_uint4(limb[4], limb[5], limb[6], limb[7]);
+        } else {
 #pragma unroll
-        for (int i = 0; i < kLimbsPerThread; i++)
-            if (j0 + i < tile_len && j0 + i < out_count) out[j0 + i] = limb[i];
+            for (int i = 0; i < kLimbsPerThread; i++)
+                if (j0 + i < tile_len && j0 + i < out_count) out[j0 + i] = limb[i];
+        }
     }
+}
+
+__device__ void tile_carry(const CoefRun &r, uint32_t h1, uint32_t h2a, uint32_t h2b, int tile_len,
+                           uint32_t *out, long out_count, bool dec, const uint32_t *add,
+                           long add_count, uint32_t *wsm, uint32_t *tile_map)
+{
+    tile_carry_t<-1, -1>(r, h1, h2a, h2b, tile_len, out, out_count, dec, add, add_count, wsm,
+                         tile_map);
 }
 
 constexpr int kTileThreads = 256;
@@ -371,7 +392,7 @@ struct CrtArgs {
 // One tile of 2048 coefficients per block: each thread remainders its run of
 // eight (two 16-byte loads per prime: tiles, runs and the prime arrays are
 // multiples of 8 words apart) and sums them into limbs.
-template <int PS>
+template <int PS, bool DEC, bool ADD>
 __global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
 {
     __shared__ uint32_t wsm[32];
@@ -382,7 +403,7 @@ __global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
     const size_t jt = t * kTile;
     const uint32_t *g0 = a.G + (k << a.n) + jt;
     const int j0 = threadIdx.x * kLimbsPerThread;
-    const bool dec = a.sink.dec;
+    constexpr bool dec = DEC;
     uint32_t r[3][kLimbsPerThread];
 #pragma unroll
     for (int p = 0; p < 3; p++) {
@@ -420,10 +441,11 @@ __global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
     run_halo(run, f1, f2a, f2b, hsm, h1, h2a, h2b);
     const Sink &o = a.sink;
     const long remaining = (long)o.out_len - (long)jt;
-    const uint32_t *add = o.add ? o.add + k * o.add_tstride + jt : nullptr;
+    const uint32_t *add = ADD ? o.add + k * o.add_tstride + jt : nullptr;
     uint32_t map;
-    tile_carry(run, h1, h2a, h2b, kTile, o.out + k * o.out_tstride + jt, remaining, dec, add,
-               (long)o.add_len - (long)jt, wsm, &map);
+    tile_carry_t<DEC ? 1 : 0, ADD ? 1 : 0>(run, h1, h2a, h2b, kTile,
+                                           o.out + k * o.out_tstride + jt, remaining, dec, add,
+                                           (long)o.add_len - (long)jt, wsm, &map);
     if (threadIdx.x == 0) a.tile_maps[blockIdx.x] = (uint8_t)map;
 }
 
@@ -769,6 +791,32 @@ static void launch_row(int ps, int lr, size_t nprod, int n, cudaStream_t s, cons
     CAT_LAUNCH("ntt_row_mul");
 }
 
+// Remaindering of a batch, specialised by prime set and by the sink's mode
+// (base 10^9 or 2^32, with or without an addend).
+template <int PS>
+static void launch_crt_ps(unsigned grid, cudaStream_t s, const CrtArgs &a)
+{
+    const bool dec = a.sink.dec, add = a.sink.add != nullptr;
+    if (dec && add)
+        crt_carry_tiles<PS, true, true><<<grid, kTileThreads, 0, s>>>(a);
+    else if (dec)
+        crt_carry_tiles<PS, true, false><<<grid, kTileThreads, 0, s>>>(a);
+    else if (add)
+        crt_carry_tiles<PS, false, true><<<grid, kTileThreads, 0, s>>>(a);
+    else
+        crt_carry_tiles<PS, false, false><<<grid, kTileThreads, 0, s>>>(a);
+}
+
+static void launch_crt(int ps, unsigned grid, cudaStream_t s, const CrtArgs &a)
+{
+    if (ps == 0)
+        launch_crt_ps<0>(grid, s, a);
+    else if (ps == 1)
+        launch_crt_ps<1>(grid, s, a);
+    else
+        launch_crt_ps<2>(grid, s, a);
+}
+
 // One operand source of a batched product.
 struct Operand {
     const uint32_t *p;
@@ -847,12 +895,7 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     ca.sink = sink;
     ca.tile_maps = maps.get();
     tok = prof_begin(c, "crt_carry_tiles", s);
-    if (PS == 0)
-        crt_carry_tiles<0><<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
-    else if (PS == 1)
-        crt_carry_tiles<1><<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
-    else
-        crt_carry_tiles<2><<<(unsigned)(nprod * tiles), kTileThreads, 0, s>>>(ca);
+    launch_crt(PS, (unsigned)(nprod * tiles), s, ca);
     CAT_LAUNCH("crt_carry_tiles");
     prof_end(c, tok, s, 12.0 * (double)gp + 4.0 * (double)nprod * (double)sink.out_len);
     tok = prof_begin(c, "carry_tile_scan", s);
@@ -1243,7 +1286,7 @@ static void noalloc_mul(const NoAllocDevice &d, const uint32_t *a, size_t na, co
     ca.n = n;
     ca.sink = plain_sink(out, 0, len);
     ca.tile_maps = maps;
-    crt_carry_tiles<0><<<(unsigned)tiles, kTileThreads, 0, s>>>(ca);
+    launch_crt(0, (unsigned)tiles, s, ca);
     CAT_LAUNCH("crt_carry_tiles");
     carry_tile_scan<<<1, 1024, 0, s>>>(maps, tiles);
     CAT_LAUNCH("carry_tile_scan");
