@@ -86,12 +86,13 @@ const char *cat_last_error(const cat_ctx *ctx);
 /* ------------------------------------------------------------ autotuning
  * The device-dependent choices of the product tree's multiplications (the
  * paper leaves them to its bignum library): the row-pass size of the
- * multi-pass transform for each transform size 2^13 .. 2^23, and the largest
+ * multi-pass transform for each transform size 2^13 .. 2^27, and the largest
  * tree-level slot (32 .. 256 limbs) multiplied by schoolbook (Comba) rather
  * than by the transform.
  *
  * cat_autotune: times every candidate on a synthetic tree level of 2^24
- * limbs on ctx's device (about a second; scratch from the context's pool),
+ * limbs (one product of 2^n limbs above that) on ctx's device (about a
+ * second; up to about 6 GB of scratch from the context's pool),
  * applies the fastest to ctx and, when path is not NULL, writes them as a
  * text table tagged with the device's name and SM count.  Results of every
  * entry point are the same integers with any choice; only speed changes.

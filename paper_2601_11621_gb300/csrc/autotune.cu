@@ -1,13 +1,13 @@
 // autotune.cu -- measures the device-dependent choices of the product tree's
 // multiplications on the current GPU and applies them to a context:
 //   - the row-pass size (2^9 .. 2^12 points) of the multi-pass transform for
-//     every transform size 2^13 .. 2^23 (prime set 0), the rest of the
-//     transform going to one or two column passes;
+//     every transform size 2^13 .. 2^27, the rest of the transform going to
+//     one or two column passes;
 //   - the largest tree-level slot (32 .. 256 limbs) whose products the
 //     schoolbook (Comba) kernels finish faster than the transform.
-// Each candidate multiplies a synthetic tree level of 2^24 limbs (seeded
-// words) and is timed with CUDA events on the context's stream; the fastest
-// wins.  The table is written as text, tagged with the device's name and SM
+// Each candidate multiplies a synthetic tree level of 2^24 limbs (one product
+// of 2^n limbs above that; seeded words) and is timed with CUDA events on the
+// context's stream; the fastest wins.  The largest trial holds about 6 GB.  The table is written as text, tagged with the device's name and SM
 // count, and read back by contexts created later on the same kind of device.
 #include "cat_internal.cuh"
 
@@ -32,7 +32,7 @@ bool plan_row_ok(int n, int rrow);
 namespace {
 
 constexpr size_t kTuneLimbs = (size_t)1 << 24;
-constexpr int kTuneMinLog = 13, kTuneMaxLog = 23;
+constexpr int kTuneMinLog = 13, kTuneMaxLog = kLogMaxNtt;
 const size_t kCombaSlots[] = {32, 64, 128, 256};
 
 // Seeded pseudo-random words (an integer hash of the index), so that no
@@ -86,12 +86,14 @@ std::string device_tag(int device)
 void autotune(Ctx &c, cudaStream_t s)
 {
     NvtxRange range("autotune");
-    DevBuf<uint32_t> in(c, kTuneLimbs, s), out(c, kTuneLimbs, s);
-    tune_fill<<<c.num_sms * 4, 256, 0, s>>>(in.get(), kTuneLimbs, 0x9e3779b9u);
+    const int top = std::min(kTuneMaxLog, c.max_log);
+    const size_t limbs = std::max(kTuneLimbs, (size_t)1 << top);
+    DevBuf<uint32_t> in(c, limbs, s), out(c, limbs, s);
+    tune_fill<<<c.num_sms * 4, 256, 0, s>>>(in.get(), limbs, 0x9e3779b9u);
     CAT_LAUNCH("tune_fill");
-    // row-pass size per transform size
-    for (int n = kTuneMinLog; n <= std::min(kTuneMaxLog, c.max_log); n++) {
-        const size_t slot = (size_t)1 << (n - 1), nprod = kTuneLimbs >> n;
+    // row-pass size per transform size (one product per trial above 2^24 points)
+    for (int n = kTuneMinLog; n <= top; n++) {
+        const size_t slot = (size_t)1 << (n - 1), nprod = std::max<size_t>(1, kTuneLimbs >> n);
         int best = 0;
         float best_ms = 0;
         for (int r = 9; r <= 12; r++) {

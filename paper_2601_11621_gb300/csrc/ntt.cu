@@ -141,12 +141,16 @@ __device__ __forceinline__ uint32_t mul_mont(uint32_t x, uint32_t vm, uint32_t q
     }
 }
 
-// Product of two Montgomery-form multipliers, reduced below q.
+// Product of two Montgomery-form multipliers, reduced below q, with the
+// second one's companion up = um q^-1 mod 2^32 precomputed (three multiplies:
+// the low word of vm um times q^-1 is vm up).
 template <int PS>
-__device__ __forceinline__ uint32_t mont_step(uint32_t vm, uint32_t um, uint32_t q, uint32_t qinv)
+__device__ __forceinline__ uint32_t mont_step(uint32_t vm, uint32_t um, uint32_t up, uint32_t q)
 {
-    if constexpr (PS == 2) return mont_mul(vm, um, q, qinv);
-    return mont<true>(vm, um, q, qinv);
+    if constexpr (PS == 2) return mont_mul_pre(vm, um, up, q);
+    const uint32_t hi = __umulhi(vm, um);
+    const uint32_t m = vm * up;
+    return csub(hi - __umulhi(m, q) + q, q);
 }
 
 // ----------------------------------------------- remaindering and carries
@@ -652,15 +656,17 @@ struct NttPlan {
 
 // Row pass of up to 2^12 points (at least 2^4 so column passes keep 16
 // columns), column passes of at most 2^10 rows, split as evenly as possible.
-// A row-pass size tuned for this device (Ctx::row_log, prime set 0 only:
-// rows of 2^9 .. 2^12 points, every column pass at least 2 rows) replaces
-// the default.
+// A row-pass size tuned for this device (Ctx::row_log: rows of 2^9 .. 2^12
+// points, at most two column passes of at least 2 rows, at least 2^4 rows in
+// prime sets 1 and 2, whose column passes are built for 2^4 .. 2^10 rows)
+// replaces the default.
 bool plan_row_ok(int n, int rrow)
 {
-    if (set_for(n) != 0 || rrow < 9 || rrow > kRowMaxLog) return false;
+    if (n > kLogMaxNtt || rrow < 9 || rrow > kRowMaxLog) return false;
     const int rem = n - rrow;
     const int ncol = (rem + kColMaxLog - 1) / kColMaxLog;
-    return rem >= 2 && ncol <= 2 && rem / ncol >= 2;
+    if (rem < 2 || ncol > 2) return false;
+    return rem / ncol >= (set_for(n) == 0 ? 2 : kColMinLog);
 }
 
 static NttPlan make_plan(const Ctx &c, int n)
@@ -737,17 +743,28 @@ static void col_pass(Ctx &c, int ps, bool fwd, uint32_t *data, size_t pstride, s
         default: fail(CAT_EINVAL, "column pass size out of range");
         }
     } else if (ps == 1) {
-        // 2^24 .. 2^26 points: plans [6, 6], [7, 6], [7, 7] + 12
+        // 2^24 .. 2^26 points: default plans [6, 6], [7, 6], [7, 7] + 12; tuned
+        // plans column passes of 2^4 .. 2^10 rows
         switch (r) {
+        case 4: launch_col<4, 1>(fwd, grid, s, a); break;
+        case 5: launch_col<5, 1>(fwd, grid, s, a); break;
         case 6: launch_col<6, 1>(fwd, grid, s, a); break;
         case 7: launch_col<7, 1>(fwd, grid, s, a); break;
+        case 8: launch_col<8, 1>(fwd, grid, s, a); break;
+        case 9: launch_col<9, 1>(fwd, grid, s, a); break;
+        case 10: launch_col<10, 1>(fwd, grid, s, a); break;
         default: fail(CAT_EINVAL, "column pass size out of range");
         }
     } else {
-        // 2^27 points: plan [8, 7] + 12
+        // 2^27 points: default plan [8, 7] + 12; tuned plans 2^4 .. 2^10 rows
         switch (r) {
+        case 4: launch_col<4, 2>(fwd, grid, s, a); break;
+        case 5: launch_col<5, 2>(fwd, grid, s, a); break;
+        case 6: launch_col<6, 2>(fwd, grid, s, a); break;
         case 7: launch_col<7, 2>(fwd, grid, s, a); break;
         case 8: launch_col<8, 2>(fwd, grid, s, a); break;
+        case 9: launch_col<9, 2>(fwd, grid, s, a); break;
+        case 10: launch_col<10, 2>(fwd, grid, s, a); break;
         default: fail(CAT_EINVAL, "column pass size out of range");
         }
     }
@@ -781,12 +798,22 @@ static void launch_row(int ps, int lr, size_t nprod, int n, cudaStream_t s, cons
         case 12: launch_row_t<12, 0>(grid, s, a); break;
         default: fail(CAT_EINVAL, "row pass size out of range");
         }
+    } else if (ps == 1) {
+        switch (lr) {
+        case 9: launch_row_t<9, 1>(grid, s, a); break;
+        case 10: launch_row_t<10, 1>(grid, s, a); break;
+        case 11: launch_row_t<11, 1>(grid, s, a); break;
+        case 12: launch_row_t<12, 1>(grid, s, a); break;
+        default: fail(CAT_EINVAL, "row pass size out of range");
+        }
     } else {
-        if (lr != 12) fail(CAT_EINVAL, "row pass size out of range");
-        if (ps == 1)
-            launch_row_t<12, 1>(grid, s, a);
-        else
-            launch_row_t<12, 2>(grid, s, a);
+        switch (lr) {
+        case 9: launch_row_t<9, 2>(grid, s, a); break;
+        case 10: launch_row_t<10, 2>(grid, s, a); break;
+        case 11: launch_row_t<11, 2>(grid, s, a); break;
+        case 12: launch_row_t<12, 2>(grid, s, a); break;
+        default: fail(CAT_EINVAL, "row pass size out of range");
+        }
     }
     CAT_LAUNCH("ntt_row_mul");
 }

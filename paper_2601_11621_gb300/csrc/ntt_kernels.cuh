@@ -405,18 +405,19 @@ struct ColTw {
     {
         static_assert(EE == E, "twiddles are applied in the round at stage bits [0, E)");
         const uint32_t br = bitrev((uint32_t)base, LR);
-        uint32_t v[V], uu[V];
+        uint32_t v[V], uu[V], up[V];
 #pragma unroll
         for (int a = 0; a < V; a++) {
             v[a] = tw_pow_mont<PS>(T, ((gcol + a) * br) << shift, q, qinv);
             uu[a] = kOneColumn ? u[a] : step_of(gcol + a);
+            up[a] = uu[a] * qinv;
         }
 #pragma unroll
         for (int j = 0; j < (1 << E); j++) {
             f(bitrev_c(j, E), v);
             if (j + 1 < (1 << E))
 #pragma unroll
-                for (int a = 0; a < V; a++) v[a] = mont_step<PS>(v[a], uu[a], q, qinv);
+                for (int a = 0; a < V; a++) v[a] = mont_step<PS>(v[a], uu[a], up[a], q);
         }
     }
 };

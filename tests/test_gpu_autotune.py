@@ -22,13 +22,13 @@ def host(t):
 
 
 def plan_ok(n, r):
-    # the rule of the library's plan_row_ok: prime set 0 (n <= 23), rows of
-    # 2^9 .. 2^12 points, at most two column passes of at least 2 rows each
-    if n > 23 or r < 9 or r > 12:
+    # the rule of the library's plan_row_ok: rows of 2^9 .. 2^12 points, at
+    # most two column passes of at least 2 rows each (2^4 rows for n > 23)
+    if n > 27 or r < 9 or r > 12:
         return False
     rem = n - r
     ncol = (rem + 9) // 10
-    return rem >= 2 and ncol <= 2 and rem // ncol >= 2
+    return rem >= 2 and ncol <= 2 and rem // ncol >= (2 if n <= 23 else 4)
 
 
 def device_tag():
@@ -51,7 +51,7 @@ def golden_sha(kind, n):
             return parts[4]
 
 
-@pytest.mark.parametrize("n", list(range(13, 24)))
+@pytest.mark.parametrize("n", list(range(13, 28)))
 def test_every_tunable_plan_is_exact(cat_lib, orc, ctx, n, tmp_path):
     a = W.random_limbs32(1 << (n - 1), seed=n)
     b = W.random_limbs32((1 << (n - 1)) - 3, seed=n + 100)
@@ -85,8 +85,8 @@ def test_autotune_round_trip_and_exact_catalan(cat_lib, tmp_path):
     finally:
         c.close()
     assert slot in (16, 32, 64, 128, 256)
-    assert set(rows) == set(range(13, 24)) and all(plan_ok(n, r) for n, r in rows.items())
-    assert open(path).read().count("row_log") == 11
+    assert set(rows) == set(range(13, 28)) and all(plan_ok(n, r) for n, r in rows.items())
+    assert open(path).read().count("row_log") == 15
     c = cat_lib.Context(0)
     try:
         c.load_tuning(path)
@@ -101,7 +101,7 @@ def test_tuned_crossover_and_plans_in_the_tree(cat_lib, orc, tmp_path):
     # the extreme choices at once: schoolbook up to 256-limb slots, the
     # smallest row passes; a product tree and C(n) still come out exact
     path = str(tmp_path / "t.txt")
-    write_table(path, 256, {n: 9 for n in range(13, 24)})
+    write_table(path, 256, {n: 9 for n in range(13, 28)})
     c = cat_lib.Context(0)
     try:
         c.load_tuning(path)
