@@ -48,7 +48,14 @@ def cmd_exact(a) -> int:
         if a.sha256:
             print(f"sha256 of the result file: {hashlib.sha256(data).hexdigest()}")
     if a.decimal:
-        d = capi.to_decimal(ctx, r).cpu().numpy().tobytes()
+        for _ in range(max(1, a.repeat)):
+            _sync()
+            t = time.perf_counter()
+            dd = capi.to_decimal(ctx, r)
+            _sync()
+            dt = time.perf_counter() - t
+            print(f"to_decimal: {dd.numel()} digits in {dt * 1e3:.1f} ms")
+        d = dd.cpu().numpy().tobytes()
         with open(a.decimal, "wb") as f:
             f.write(d)
         print(f"wrote {a.decimal}: {len(d)} digits")

@@ -699,9 +699,15 @@ template <int LR, int PS>
 static void launch_col(bool fwd, dim3 grid, cudaStream_t s, const ColArgs &a)
 {
     const size_t smem = ((size_t)1 << (LR + col_log_c(LR))) * sizeof(uint32_t);
-    if (fwd) {
-        set_smem(ntt_col_fwd<LR, PS, kColV>, smem);
-        ntt_col_fwd<LR, PS, kColV><<<grid, kColFwdThreads, smem, s>>>(a);
+    // the first pass of operands of at most half the transform (every tree
+    // level) knows its upper half is zero
+    const bool zt = fwd && a.src && a.src_len <= ((size_t)1 << (a.m - 1));
+    if (zt) {
+        set_smem(ntt_col_fwd<LR, PS, kColV, true>, smem);
+        ntt_col_fwd<LR, PS, kColV, true><<<grid, kColFwdThreads, smem, s>>>(a);
+    } else if (fwd) {
+        set_smem(ntt_col_fwd<LR, PS, kColV, false>, smem);
+        ntt_col_fwd<LR, PS, kColV, false><<<grid, kColFwdThreads, smem, s>>>(a);
     } else {
         set_smem(ntt_col_inv<LR, PS, kColV>, smem);
         ntt_col_inv<LR, PS, kColV><<<grid, kColInvThreads, smem, s>>>(a);

@@ -14,7 +14,17 @@
 // (2^(s+1) <= 2^13).
 #pragma once
 
+#include <type_traits>
+
 __host__ __device__ constexpr int rounds_of(int lr) { return (lr + 3) / 4; }
+
+// Whether an input of a register round knows that the upper half of its
+// points (k >= 2^(E-1), the top stage's second inputs) are zero: the first
+// forward round of an operand no longer than half the transform.
+template <class T, class = void>
+struct zero_top : std::false_type {};
+template <class T>
+struct zero_top<T, std::void_t<decltype(T::kZeroTop)>> : std::bool_constant<T::kZeroTop> {};
 
 // size of DIF round rd of nr rounds (counted from the top stage bits); when
 // the stages do not split evenly the last rounds take the extra ones, so that
@@ -88,8 +98,10 @@ __device__ __forceinline__ uint2 tw_at(const TwRef &T, int idx)
 }
 
 // In a round with B = 0 the twiddle index is a compile-time constant, and the
-// butterflies with (k mod 2^st) = 0 have twiddle w^0 = 1: no multiply.
-template <int E, int B, int NA, int PS>
+// butterflies with (k mod 2^st) = 0 have twiddle w^0 = 1: no multiply.  With
+// ZT the top stage's second inputs are zero, so its butterflies are
+// (x, 0) -> (x, x w): one product, no sum or difference.
+template <int E, int B, int NA, int PS, bool ZT = false>
 __device__ __forceinline__ void dif_stages(uint32_t (&x)[NA][1 << E], int glow, const TwRef &T,
                                            uint32_t q)
 {
@@ -98,6 +110,18 @@ __device__ __forceinline__ void dif_stages(uint32_t (&x)[NA][1 << E], int glow, 
 #pragma unroll
         for (int k = 0; k < (1 << E); k++) {
             if (k & (1 << st)) continue;
+            if (ZT && st == E - 1) {
+                if (B == 0 && k == 0) {
+#pragma unroll
+                    for (int a = 0; a < NA; a++) x[a][k + (1 << st)] = x[a][k];
+                } else {
+                    const uint2 w = tw_at<PS, 0, (B == 0 && E <= 4)>(T, (1 << (B + st)) + glow +
+                                                                            (k << B));
+#pragma unroll
+                    for (int a = 0; a < NA; a++) x[a][k + (1 << st)] = mul_w<PS>(x[a][k], w, q);
+                }
+                continue;
+            }
             if (B == 0 && (k & ((1 << st) - 1)) == 0) {
 #pragma unroll
                 for (int a = 0; a < NA; a++) bf_dif1<PS>(x[a][k], x[a][k + (1 << st)], q);
@@ -151,7 +175,7 @@ __device__ __forceinline__ void round_io(const IN &in, const OUT &out, const TwR
         uint32_t x[NA][1 << E];
         in.template load<E, B, NA>(x, base, c);
         if (FWD)
-            dif_stages<E, B, NA, PS>(x, glow, T, q);
+            dif_stages<E, B, NA, PS, zero_top<IN>::value>(x, glow, T, q);
         else
             dit_stages<E, B, NA, PS>(x, glow, T, q);
         out.template store<E, B, NA>(x, base, c);
@@ -332,8 +356,11 @@ __device__ __forceinline__ void store_v(uint32_t *p, const uint32_t (&w)[V])
 // the array bases are multiples of 16 words).  With `src`, elements come from
 // limbs instead (zero past src_len, reduced), word by word, since a caller's
 // limbs need not be aligned.
-template <int PS, int V>
+template <int PS, int V, bool ZT = false>
 struct ColIn {
+    // ZT: the first round of the first pass of an operand of at most half the
+    // transform's length, whose points k >= 2^(E-1) lie in the zero upper half
+    static constexpr bool kZeroTop = ZT;
     const uint32_t *p;
     const uint32_t *src;
     uint32_t S, col0, src_len;  // offsets within one transform fit in 32 bits
@@ -345,6 +372,11 @@ struct ColIn {
         const uint32_t i0 = (uint32_t)base * S + col0 + (uint32_t)c * V;
 #pragma unroll
         for (int k = 0; k < (1 << E); k++) {
+            if (ZT && k >= (1 << (E - 1))) {
+#pragma unroll
+                for (int a = 0; a < V; a++) x[a][k] = 0u;
+                continue;
+            }
             const uint32_t idx = i0 + (uint32_t)k * (S << B);
             if (src) {
 #pragma unroll
@@ -485,7 +517,7 @@ struct ColOut {
 
 // Forward column pass: a 2^LR-point DIF down each of C consecutive columns of
 // one block (row stride S = 2^(m-LR)), then the twiddle w_M^(col * bitrev(row)).
-template <int LR, int PS, int V>
+template <int LR, int PS, int V, bool ZT>
 __global__ void __launch_bounds__(kColFwdThreads, CAT_COL_FWD_MINB) ntt_col_fwd(ColArgs a)
 {
     extern __shared__ uint32_t sm[];
@@ -502,8 +534,8 @@ __global__ void __launch_bounds__(kColFwdThreads, CAT_COL_FWD_MINB) ntt_col_fwd(
     uint32_t *base = a.data + p * a.pstride + (blk << a.m);
     const uint2 *T = tw_table(a.tw, PS, p, 0);
     const TwRef TR{T, p};
-    const ColIn<PS, V> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, (uint32_t)Sr,
-                          (uint32_t)col0, (uint32_t)a.src_len, q, c_wp1[PS][p]};
+    const ColIn<PS, V, ZT> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, (uint32_t)Sr,
+                              (uint32_t)col0, (uint32_t)a.src_len, q, c_wp1[PS][p]};
     ColTw<LR, PS, NR, kColFwdThreads, V> tw{T, q, c_qinv[PS][p], set_log_root(PS) - a.m, {}};
     tw.init((uint32_t)col0);
     const ColOutTw<LR, PS, NR, V> out{base, (uint32_t)Sr, (uint32_t)col0, tw};
