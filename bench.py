@@ -260,6 +260,27 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def verify_result(n: int, limbs) -> dict:
+    """The computed C(n) checked after timing: at the paper's n the result file
+    (bytes 01 01, then the little-endian magnitude) must hash to Table 1's
+    SHA-256 (tests/golden/paper_table1.txt); a mismatch stops the benchmark."""
+    if n != PAPER_N:
+        return {}
+    want = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "paper_table1.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split(None, 1)
+            want[k] = v.strip()
+    top = int(limbs[-1])
+    bits = (len(limbs) - 1) * 32 + top.bit_length()
+    nbytes = (bits + 7) // 8
+    body = limbs.astype("<u4").tobytes()[:nbytes]
+    sha = hashlib.sha256(bytes.fromhex(want["sha256_header_hex"]) + body).hexdigest()
+    if sha != want["sha256"] or bits != int(want["bit_length"]):
+        raise RuntimeError(f"C({n}) does not match Table 1: sha256 {sha}, {bits} bits")
+    return {"bits": bits, "sha256_table1": True}
+
+
 def workload_config(args):
     return {"workload": f"catalan_exact n={args.n:,} (Table 1 scale)" if args.n == PAPER_N
             else f"catalan_exact n={args.n:,}",
@@ -503,6 +524,7 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_s = slowest_rank(e2e_s, dist, dev)
     e2e_value = per_unit(e2e_s, e2e_steps, world)
+    check = verify_result(n, hres)
 
     # dominant kernel by device time, against the measured HBM copy peak
     peak, peak_kind = read_peaks()
@@ -556,7 +578,7 @@ def main():
             "dtype": "u32",
             "data": "synthetic (the input is n itself)",
             "config": workload_config(args),
-            "result": {"limbs": int(nlimbs), "host_limbs": int(hres.size)},
+            "result": {"limbs": int(nlimbs), "host_limbs": int(hres.size), **check},
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(4 * hres.size)},

@@ -126,3 +126,26 @@ def test_table_from_another_device_is_refused(cat_lib, tmp_path):
         assert c.tuning() == before
     finally:
         c.close()
+
+
+@pytest.mark.slow
+def test_paper_scale_with_tuned_plans(cat_lib, tmp_path):
+    """C(2,050,572,903) with the plans the autotuner picks on this device (the
+    configuration bench.py times) against Table 1's SHA-256."""
+    t = {}
+    for line in open(os.path.join(GOLDEN, "paper_table1.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split(None, 1)
+            t[k] = v.strip()
+    path = str(tmp_path / "autotune.txt")
+    c = cat_lib.Context(0)
+    try:
+        c.autotune(path)
+        got = host(cat_lib.catalan_exact(c, int(t["n"])))
+    finally:
+        c.close()
+    bits = (len(got) - 1) * 32 + int(got[-1]).bit_length()
+    assert bits == int(t["bit_length"])
+    body = got.astype("<u4").tobytes()[:(bits + 7) // 8]
+    sha = hashlib.sha256(bytes.fromhex(t["sha256_header_hex"]) + body).hexdigest()
+    assert sha == t["sha256"]
