@@ -29,7 +29,9 @@ Prints one JSON line (rank 0):
                cat_exact calls, results compared;
   served       a seeded Poisson stream through the serving engine against the
                same stream one request at a time: p50/p99 latency, req/s,
-               results compared.
+               results compared;
+  decimal      to_decimal of the C(n) just computed (its 1,234,567,890 digits at
+               the paper's n).
 """
 from __future__ import annotations
 
@@ -400,6 +402,30 @@ def batched(ctx, capi, W):
             "checked": f"first {sub} equal to one-at-a-time results; 16 mod q"}
 
 
+def decimal(ctx, capi, limbs, n):
+    """to_decimal of the computed C(n) (the optional decimal output): median of
+    two timed conversions after one warm-up; at the paper's n the digit count
+    must be Table 1's 1,234,567,890."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = torch.empty(capi.cat_decimal_bound(limbs.numel()), dtype=torch.uint8,
+                      device=limbs.device)
+    d = capi.to_decimal(ctx, limbs, out=out)
+    ms = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d = capi.to_decimal(ctx, limbs, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    if n == PAPER_N and d.numel() != 1_234_567_890:
+        raise RuntimeError(f"to_decimal gave {d.numel()} digits")
+    return {"digits": int(d.numel()), "ms": round(min(ms), 2),
+            "checked": "digit count (Table 1)" if n == PAPER_N else "none"}
+
+
 def served(ctx, capi, W, device, rate=300.0, count=96):
     from paper_2601_11621_gb300 import server
     stream = W.served_requests(count, rate, seed=1)
@@ -562,6 +588,7 @@ def main():
         extras["mul_sweep"] = mul_sweep(ctx, capi, W, dev)
         extras["batched"] = batched(ctx, capi, W)
         extras["served"] = served(ctx, capi, W, local_rank)
+        extras["decimal"] = decimal(ctx, capi, out[:nlimbs], n)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
