@@ -67,6 +67,7 @@ typedef struct cat_ctx cat_ctx;
  * scratch the context may hold at once (0 = no cap).  When the in-core
  * reconstruction of a quantity would not fit the cap (about 128 bytes per
  * result limb), cat_exact, catalan_exact, cat_exact_host and cat_ratio_exact
+ * (and cat_reconstruct, which leaves the caller's factorisation as it is)
  * reconstruct it within the cap instead, the paper's chunked products with
  * partial products kept in pinned host memory (Sec. 3.2): the primes are
  * multiplied in chunks sized to the cap, and products too large for it run by

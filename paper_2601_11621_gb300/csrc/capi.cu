@@ -243,6 +243,12 @@ int cat_reconstruct(cat_ctx *ctx, const cat_factorization *f, uint32_t *out, siz
     if (!ctx || !f || !out_len || (cap && !out)) return CAT_EINVAL;
     return guarded(ctx, [&] {
         cudaStream_t s = as_stream(stream);
+        if (cat::reconstruct_out_of_core(ctx->c, f)) {
+            // the caller's factorisation stays as it is
+            cat::reconstruct_into(ctx->c, const_cast<cat_factorization *>(f), out, cap, false,
+                                  out_len, s, false);
+            return;
+        }
         cat::Big r = cat::reconstruct(ctx->c, f, s);
         copy_out(ctx->c, r, out, cap, out_len, s);
     });

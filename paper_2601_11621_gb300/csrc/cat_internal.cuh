@@ -570,12 +570,13 @@ void copy_to_host(Ctx &c, uint32_t *host, const uint32_t *dev, size_t n, cudaStr
 // Algorithm 2 on a factorisation; returns the result (normalised length).
 Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s);
 // Whether the in-core reconstruction of f would exceed the context's HBM
-// budget, and Algorithm 2 within the budget (ooc.cu): releases f (its primes
-// move to pinned host memory), multiplies by chunks and pieces, and copies
-// the result (*out_len limbs) to out, device memory or (to_host) host memory.
+// budget, and Algorithm 2 within the budget (ooc.cu): copies f's primes to
+// pinned host memory (and, with release, frees f's device arrays), multiplies
+// by chunks and pieces, and copies the result (*out_len limbs) to out, device
+// memory or (to_host) host memory.
 bool reconstruct_out_of_core(const Ctx &c, const cat_factorization *f);
 void reconstruct_into(Ctx &c, cat_factorization *f, uint32_t *out, size_t cap, bool to_host,
-                      size_t *out_len, cudaStream_t s);
+                      size_t *out_len, cudaStream_t s, bool release = true);
 
 // The factorisation as the paper's text layout (Sec. 3.1) into out (device),
 // titled `name`; the binary result file (bytes 01 01, then the magnitude

@@ -638,6 +638,26 @@ struct RowIn {
     }
 };
 
+// The product's inverse rounds with two rows per group (rows c and c + CH,
+// CH = half the block's rows): they are the two arrays of the register round,
+// so each stage twiddle and every index serves both rows.
+#ifndef CAT_ROW_PAIR
+#define CAT_ROW_PAIR 1
+#endif
+
+template <int LR, int CH>
+struct RowOutPair {
+    uint32_t *p;
+    template <int E, int B, int NA>
+    __device__ __forceinline__ void store(uint32_t (&x)[NA][1 << E], int base, int c) const
+    {
+#pragma unroll
+        for (int a = 0; a < NA; a++)
+#pragma unroll
+            for (int k = 0; k < (1 << E); k++) p[((c + a * CH) << LR) + base + (k << B)] = x[a][k];
+    }
+};
+
 template <int LR>
 struct RowOut {
     uint32_t *p;
@@ -703,7 +723,25 @@ __global__ void __launch_bounds__(kRowThreads, CAT_ROW_MINB) ntt_row_mul(RowArgs
     }
     __syncthreads();
     uint32_t *g = a.G + p * a.gpstride + (k << a.n) + off;
-    if constexpr (NR == 2) {
+    // rows in pairs when the block has two rows or more and the paired rounds
+    // still give every thread a group; the single-array layout (row r at
+    // r 2^LR) is the paired layout's (array a at a CH 2^LR, column c at c 2^LR)
+    constexpr int CH = C / 2 > 0 ? C / 2 : 1;
+    constexpr bool kPair =
+        CAT_ROW_PAIR && C >= 2 && CH * ((1 << LR) >> dit_size(LR, 1)) >= kRowThreads &&
+        (NR == 2 || CH * ((1 << LR) >> dit_size(LR, 2)) >= kRowThreads);
+    if constexpr (kPair) {
+        const SmemIO<LR, CH, false> sp{sm};
+        if constexpr (NR == 2) {
+            round_io<LR, CH, dit_base(LR, 1), dit_size(LR, 1), false, 2, false, PS>(
+                sp, RowOutPair<LR, CH>{g}, Ti, q);
+        } else {
+            round_io<LR, CH, dit_base(LR, 1), dit_size(LR, 1), false, 2, false, PS>(sp, sp, Ti, q);
+            __syncthreads();
+            round_io<LR, CH, dit_base(LR, 2), dit_size(LR, 2), false, 2, false, PS>(
+                sp, RowOutPair<LR, CH>{g}, Ti, q);
+        }
+    } else if constexpr (NR == 2) {
         round_io<LR, C, dit_base(LR, 1), dit_size(LR, 1), false, 1, false, PS>(sio, RowOut<LR>{g},
                                                                                Ti, q);
     } else {

@@ -242,11 +242,12 @@ bool reconstruct_out_of_core(const Ctx &c, const cat_factorization *f)
 }
 
 // Algorithm 2 within the context's budget: the grouped primes go to pinned
-// host memory (the device factorisation is released), Q_e = product of G_e
-// by chunks, P_e = Q_e^e, C = balanced product of the P_e.  The result is
-// copied to `out` (device memory, or host memory with to_host), cap limbs.
+// host memory (the device factorisation is released when it belongs to this
+// call), Q_e = product of G_e by chunks, P_e = Q_e^e, C = balanced product of
+// the P_e.  The result is copied to `out` (device memory, or host memory with
+// to_host), cap limbs.
 void reconstruct_into(Ctx &c, cat_factorization *f, uint32_t *out, size_t cap, bool to_host_out,
-                      size_t *out_len, cudaStream_t s)
+                      size_t *out_len, cudaStream_t s, bool release)
 {
     NvtxRange range("phase2: reconstruction by chunks");
     const uint64_t ng = f->num_groups, np = f->num_primes;
@@ -256,7 +257,7 @@ void reconstruct_into(Ctx &c, cat_factorization *f, uint32_t *out, size_t cap, b
     if (np)
         CAT_CUDA(cudaMemcpyAsync(primes.p, f->primes, 4 * np, cudaMemcpyDeviceToHost, s));
     CAT_CUDA(cudaStreamSynchronize(s));
-    factor_free(c, f);
+    if (release) factor_free(c, f);
     std::vector<HostBig> P;
     for (uint64_t g = 0; g < ng; g++) {
         HostBig Q = chunk_product(c, primes.p + offs[g], offs[g + 1] - offs[g], s);

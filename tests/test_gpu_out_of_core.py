@@ -89,3 +89,22 @@ def test_catalan_5e7_within_a_small_budget(cat_lib):
     assert len(got) == want["limbs"]
     assert hashlib.sha256(got.astype("<u4").tobytes()).hexdigest() == want["sha"]
     assert peak <= budget
+
+
+def test_budgeted_reconstruct_keeps_the_callers_factorization(cat_lib, orc):
+    # a factorisation made in one context, reconstructed in a small-budget one
+    # twice (the caller still owns it afterwards)
+    big = cat_lib.Context(0)
+    small = cat_lib.Context(0, hbm_budget_bytes=700_000)
+    try:
+        f = cat_lib.catalan_factor(big, 160_000, 0)
+        cap = cat_lib.cat_bound_limbs(160_000, 0)
+        for _ in range(2):
+            got = host(cat_lib.cat_reconstruct(small, f, cap))
+            assert np.array_equal(got, orc.catalan(160_000))
+        assert f.primes().numel() == f.num_primes
+        f.free()
+        assert small.memory()[1] <= 700_000
+    finally:
+        small.close()
+        big.close()
