@@ -49,7 +49,7 @@ __global__ void tune_fill(uint32_t *x, size_t n, uint32_t seed)
     }
 }
 
-// Median device milliseconds of three runs of f after one warm-up run.
+// Median device milliseconds of five runs of f after one warm-up run.
 template <class F>
 float time_ms(cudaStream_t s, F &&f)
 {
@@ -57,7 +57,7 @@ float time_ms(cudaStream_t s, F &&f)
     CAT_CUDA(cudaEventCreate(&a));
     CAT_CUDA(cudaEventCreate(&b));
     f();
-    float t[3];
+    float t[5];
     for (float &x : t) {
         CAT_CUDA(cudaEventRecord(a, s));
         f();
@@ -67,9 +67,13 @@ float time_ms(cudaStream_t s, F &&f)
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    std::sort(t, t + 3);
-    return t[1];
+    std::sort(t, t + 5);
+    return t[2];
 }
+
+// The default row-pass size of a 2^n-point transform (the plan without a
+// tuned value).
+int default_row(int n) { return std::min(12, n - 4); }
 
 std::string device_tag(int device)
 {
@@ -94,19 +98,23 @@ void autotune(Ctx &c, cudaStream_t s)
     // row-pass size per transform size (one product per trial above 2^24 points)
     for (int n = kTuneMinLog; n <= top; n++) {
         const size_t slot = (size_t)1 << (n - 1), nprod = std::max<size_t>(1, kTuneLimbs >> n);
-        int best = 0;
-        float best_ms = 0;
+        // the default plan first; another size replaces it only when at least
+        // 1 % faster, so that near-ties keep the default
+        const int def = default_row(n);
+        c.row_log[n] = 0;
+        int best = def;
+        float best_ms = time_ms(s, [&] { ntt_level(c, in.get(), slot, nprod, out.get(), s); });
         for (int r = 9; r <= 12; r++) {
-            if (!plan_row_ok(n, r)) continue;
+            if (r == def || !plan_row_ok(n, r)) continue;
             c.row_log[n] = r;
             const float ms =
                 time_ms(s, [&] { ntt_level(c, in.get(), slot, nprod, out.get(), s); });
-            if (!best || ms < best_ms) {
+            if (ms < 0.99f * best_ms) {
                 best = r;
                 best_ms = ms;
             }
         }
-        c.row_log[n] = best;
+        c.row_log[n] = plan_row_ok(n, best) ? best : 0;
     }
     // schoolbook / transform crossover: the largest slot up to which Comba wins
     size_t cross = 16;

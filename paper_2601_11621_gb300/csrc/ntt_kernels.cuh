@@ -645,6 +645,31 @@ struct RowIn {
 #define CAT_ROW_PAIR 1
 #endif
 
+// The forward rounds but the last with two rows per group and both operands:
+// arrays a-row c, a-row c + CH, b-row c, b-row c + CH (NA = 4, or 2 when
+// squaring), which is the layout of SmemIO with CH columns and NA arrays.
+#ifndef CAT_ROW_PAIR_FWD
+#define CAT_ROW_PAIR_FWD 1
+#endif
+
+template <int LR, int CH>
+struct RowInPair {
+    const uint32_t *pa, *pb;
+    template <int E, int B, int NA>
+    __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
+    {
+#pragma unroll
+        for (int k = 0; k < (1 << E); k++) {
+            x[0][k] = pa[(c << LR) + base + (k << B)];
+            x[1][k] = pa[((c + CH) << LR) + base + (k << B)];
+            if (NA > 2) {
+                x[NA - 2][k] = pb[(c << LR) + base + (k << B)];
+                x[NA - 1][k] = pb[((c + CH) << LR) + base + (k << B)];
+            }
+        }
+    }
+};
+
 template <int LR, int CH>
 struct RowOutPair {
     uint32_t *p;
@@ -698,13 +723,31 @@ __global__ void __launch_bounds__(kRowThreads, CAT_ROW_MINB) ntt_row_mul(RowArgs
     const TwRef Ti{tw_table(a.tw, PS, p, 1), p};
     const uint2 sc = p == 0 ? a.scale.c[0] : (p == 1 ? a.scale.c[1] : a.scale.c[2]);
     const SmemIO<LR, C, false> sio{sm};
-    // forward rounds but the last
-    round_io<LR, C, dif_base(LR, 0), round_size(LR, 0), true, NA, false, PS>(RowIn<LR>{fa, fb},
-                                                                             sio, T, q);
-    __syncthreads();
-    if constexpr (NR == 3) {
-        round_io<LR, C, dif_base(LR, 1), round_size(LR, 1), true, NA, false, PS>(sio, sio, T, q);
+    // forward rounds but the last, two rows per group when every thread still
+    // gets a group
+    constexpr int CF = C / 2 > 0 ? C / 2 : 1;
+    constexpr bool kPairFwd =
+        CAT_ROW_PAIR_FWD && C >= 2 && CF * ((1 << LR) >> round_size(LR, 0)) >= kRowThreads &&
+        (NR == 2 || CF * ((1 << LR) >> round_size(LR, 1)) >= kRowThreads);
+    if constexpr (kPairFwd) {
+        const SmemIO<LR, CF, false> sp{sm};
+        round_io<LR, CF, dif_base(LR, 0), round_size(LR, 0), true, 2 * NA, false, PS>(
+            RowInPair<LR, CF>{fa, fb}, sp, T, q);
         __syncthreads();
+        if constexpr (NR == 3) {
+            round_io<LR, CF, dif_base(LR, 1), round_size(LR, 1), true, 2 * NA, false, PS>(sp, sp, T,
+                                                                                       q);
+            __syncthreads();
+        }
+    } else {
+        round_io<LR, C, dif_base(LR, 0), round_size(LR, 0), true, NA, false, PS>(
+            RowIn<LR>{fa, fb}, sio, T, q);
+        __syncthreads();
+        if constexpr (NR == 3) {
+            round_io<LR, C, dif_base(LR, 1), round_size(LR, 1), true, NA, false, PS>(sio, sio, T,
+                                                                                   q);
+            __syncthreads();
+        }
     }
     // last forward round + pointwise product + first inverse round
     constexpr int NGC = (1 << LR) >> EL;
