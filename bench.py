@@ -192,29 +192,33 @@ def _extrapolate(oracle, point, alpha: float, n_from: int, n_to: int) -> float:
     return t_p1 * n_to / n_from + (t_all - t_p1) * (full / limbs) ** alpha
 
 
-FIT_NS = (10**6, 10**7, 5 * 10**7)
+# The oracle's growth steepens with size (Karatsuba's exponent takes over from
+# the schoolbook base cases and the sieve), so the exponent is fitted at the
+# top of the measured range, where the extrapolation starts.
+FIT_NS = (10**7, 2 * 10**7, 5 * 10**7)
+ST_NS = (10**6, 10**7)
 
 
 def oracle_baseline(n: int):
-    """The CPU oracle timed on all host cores at n = 10^6, 10^7, 5 * 10^7 and
-    single-threaded at 10^6, 10^7; the all-core figure extrapolated to C(n)
-    with the growth exponent fitted to the three all-core points."""
+    """The CPU oracle timed on all host cores at n = 10^7, 2 * 10^7, 5 * 10^7
+    and single-threaded at 10^6, 10^7; the all-core figure extrapolated to C(n)
+    from the largest point with the growth exponent fitted to the three."""
     import oracle
     oracle.build()
     threads = oracle.max_threads()
     pts = [_oracle_point(oracle, m, threads) for m in FIT_NS]
     alpha = _fit_exponent(pts)
     value = _extrapolate(oracle, pts[-1], alpha, FIT_NS[-1], n)
-    st = [_oracle_point(oracle, m, 1) for m in FIT_NS[:2]]
+    st = [_oracle_point(oracle, m, 1) for m in ST_NS]
     alpha_st = _fit_exponent(st)
-    value_st = _extrapolate(oracle, st[-1], alpha_st, FIT_NS[1], n)
+    value_st = _extrapolate(oracle, st[-1], alpha_st, ST_NS[-1], n)
     measured = {f"{m:.0e}": round(p[2], 3) for m, p in zip(FIT_NS, pts)}
     desc = (f"oracle (plain C, OpenMP tasks over product-tree halves and Karatsuba "
-            f"sub-products, {threads} threads) timed end to end at n = 1e6, 1e7, 5e7 "
+            f"sub-products, {threads} threads) timed end to end at n = 1e7, 2e7, 5e7 "
             f"({', '.join(f'{k}: {v} s' for k, v in measured.items())}); Phase 2 growth "
-            f"exponent fitted = {alpha:.3f} (limbs); extrapolated to n = {n:,} (Phase 1 "
-            f"linear in n); single-threaded: {st[0][2]:.2f} s at 1e6, {st[1][2]:.2f} s at 1e7, "
-            f"extrapolated {value_st:.0f} s (exponent {alpha_st:.3f})")
+            f"exponent fitted = {alpha:.3f} (limbs); extrapolated from 5e7 to n = {n:,} "
+            f"(Phase 1 linear in n); single-threaded: {st[0][2]:.2f} s at 1e6, "
+            f"{st[1][2]:.2f} s at 1e7, extrapolated {value_st:.0f} s (exponent {alpha_st:.3f})")
     return {"value": value, "unit": "s", "cores": threads, "kind": "oracle",
             "sample": desc, "extrapolated": True, "fitted_exponent": round(alpha, 4),
             "measured_s": measured, "config2_n5e7_measured_s": round(pts[-1][2], 3),
@@ -222,30 +226,29 @@ def oracle_baseline(n: int):
 
 
 def run_reference(args, rank, world):
-    """The oracle as the reference arm: warm-up steps time it at n = 10^6 and
-    10^7 on all host cores (the growth exponent is fitted from them); each
-    timed step is one all-core oracle run at n = 10^7, extrapolated to the
-    bench's n with that exponent."""
+    """The oracle as the reference arm: the warm-up steps time it on all host
+    cores at n = 10^7, 2 * 10^7, 5 * 10^7 in turn (every size at least once;
+    the growth exponent is fitted from them), and each timed step is one
+    all-core oracle run at n = 2 * 10^7, extrapolated to the bench's n with
+    that exponent."""
     if rank != 0:
         return
     import oracle
     oracle.build()
     threads = oracle.max_threads()
-    fit = []
-    for i in range(max(1, args.warmup)):
-        fit.append(_oracle_point(oracle, FIT_NS[i % 2], threads))
-    if len({p[0] for p in fit}) < 2:
-        fit.append(_oracle_point(oracle, FIT_NS[1], threads))
+    fit = [_oracle_point(oracle, FIT_NS[i % len(FIT_NS)], threads)
+           for i in range(max(len(FIT_NS), args.warmup))]
     alpha = _fit_exponent(fit)
+    step_n = FIT_NS[1]
     vals, cpu_s = [], 0.0
     for _ in range(args.steps):
-        p = _oracle_point(oracle, FIT_NS[1], threads)
+        p = _oracle_point(oracle, step_n, threads)
         cpu_s += p[2] + p[1]
-        vals.append(_extrapolate(oracle, p, alpha, FIT_NS[1], args.n))
+        vals.append(_extrapolate(oracle, p, alpha, step_n, args.n))
     value = statistics.median(vals)
-    desc = (f"oracle (plain C, {threads} threads) at n = 1e7 per step, extrapolated to "
+    desc = (f"oracle (plain C, {threads} threads) at n = 2e7 per step, extrapolated to "
             f"n = {args.n:,} with the Phase 2 exponent {alpha:.3f} fitted in the warm-up "
-            f"steps (n = 1e6 and 1e7)")
+            f"steps (n = 1e7, 2e7, 5e7)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,

@@ -53,6 +53,7 @@ def test_fit_and_extrapolation_recover_a_power_law():
 def test_reference_arm_prints_one_line(monkeypatch, capsys):
     # small sizes in place of 10^6 / 10^7 so that the arm runs in seconds
     monkeypatch.setattr(bench, "FIT_NS", (2000, 20000, 50000))
+    monkeypatch.setattr(bench, "ST_NS", (2000, 20000))
 
     class Args:
         n, steps, warmup, gpus = 10**6, 2, 2, 1
