@@ -491,18 +491,30 @@ def cat_exact_host(ctx: Context, kind: int, n: int, out: np.ndarray | None = Non
     return out[:m.value]
 
 
+_REQUEST_DTYPE = np.dtype({"names": ["kind", "n"], "formats": [np.int32, np.uint64],
+                           "offsets": [Request.kind.offset, Request.n.offset],
+                           "itemsize": ctypes.sizeof(Request)})
+
+
 def _requests(reqs):
-    arr = (Request * max(1, len(reqs)))()
-    for i, (kind, n) in enumerate(reqs):
-        arr[i].kind = int(kind)
-        arr[i].n = int(n)
+    """(kind, n) pairs as a numpy-backed array of cat_request (at least one
+    element); pass it through _request_ptr and keep it alive for the call."""
+    v = np.asarray(reqs, dtype=np.int64).reshape(-1, 2)
+    arr = np.zeros(max(1, len(v)), dtype=_REQUEST_DTYPE)
+    arr["kind"][:len(v)] = v[:, 0]
+    arr["n"][:len(v)] = v[:, 1].astype(np.uint64)
     return arr
+
+
+def _request_ptr(arr):
+    return arr.ctypes.data_as(ctypes.POINTER(Request))
 
 
 def cat_batch_bound(reqs) -> int:
     """Total limbs a batch of (kind, n) requests needs."""
     total = ctypes.c_size_t()
-    rc = load().cat_batch_bound(_requests(reqs), len(reqs), ctypes.byref(total))
+    arr = _requests(reqs)
+    rc = load().cat_batch_bound(_request_ptr(arr), len(reqs), ctypes.byref(total))
     if rc != 0:
         raise CatError(rc, "cat_batch_bound")
     return total.value
@@ -511,7 +523,8 @@ def cat_batch_bound(reqs) -> int:
 def cat_batch_footprint(reqs) -> int:
     """The serving engine's device-byte estimate for a batch of (kind, n)."""
     total = ctypes.c_size_t()
-    rc = load().cat_batch_footprint(_requests(reqs), len(reqs), ctypes.byref(total))
+    arr = _requests(reqs)
+    rc = load().cat_batch_footprint(_request_ptr(arr), len(reqs), ctypes.byref(total))
     if rc != 0:
         raise CatError(rc, "cat_batch_footprint")
     return total.value
@@ -522,13 +535,17 @@ def cat_exact_batch(ctx: Context, reqs, out=None, stream=None):
     lengths): request r's limbs are out[offsets[r] : offsets[r] + lengths[r]]
     (out an int32 device tensor of uint32 limbs)."""
     count = len(reqs)
-    cap = cat_batch_bound(reqs)
+    arr = _requests(reqs)
+    total = ctypes.c_size_t()
+    rc = load().cat_batch_bound(_request_ptr(arr), count, ctypes.byref(total))
+    if rc != 0:
+        raise CatError(rc, "cat_batch_bound")
     if out is None:
-        out = _empty(cap, f"cuda:{ctx.device}")
+        out = _empty(total.value, f"cuda:{ctx.device}")
     offs = np.zeros(max(1, count), dtype=np.uint64)
     lens = np.zeros(max(1, count), dtype=np.uint64)
     u64p = ctypes.POINTER(ctypes.c_uint64)
-    ctx.check(load().cat_exact_batch(ctx.handle, _requests(reqs), count, _ptr(out), out.numel(),
+    ctx.check(load().cat_exact_batch(ctx.handle, _request_ptr(arr), count, _ptr(out), out.numel(),
                                      offs.ctypes.data_as(u64p), lens.ctypes.data_as(u64p),
                                      _stream(stream)))
     return out, offs[:count], lens[:count]

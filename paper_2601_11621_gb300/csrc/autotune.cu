@@ -23,10 +23,6 @@
 
 namespace cat {
 
-void ntt_level(Ctx &c, const uint32_t *level, size_t slot, size_t nprod, uint32_t *out,
-               cudaStream_t s);
-bool comba_level(Ctx &c, const uint32_t *in, size_t slot, size_t nprod, uint32_t *out,
-                 cudaStream_t s);
 bool plan_row_ok(int n, int rrow);
 
 namespace {

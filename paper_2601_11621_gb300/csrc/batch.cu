@@ -15,6 +15,8 @@
 #include "cat_internal.cuh"
 #include "legendre.cuh"
 
+#include <string.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -22,10 +24,6 @@ namespace cat {
 
 DevBuf<uint32_t> sieve_primes(Ctx &c, uint64_t limit, uint64_t *count, cudaStream_t s);
 void exclusive_scan_u32(Ctx &c, uint32_t *data, size_t n, cudaStream_t s);
-bool comba_level(Ctx &c, const uint32_t *in, size_t slot, size_t nprod, uint32_t *out,
-                 cudaStream_t s);
-void ntt_level(Ctx &c, const uint32_t *level, size_t slot, size_t nprod, uint32_t *out,
-               cudaStream_t s);
 
 namespace {
 
@@ -97,9 +95,11 @@ __global__ void batch_seg_starts(const uint64_t *pre, int count, const uint32_t 
     seg[r] = (r < count && pre[r] < pre[count]) ? pos[pre[r]] : total_leaves;
 }
 
-// node j of segment r = product of its leaves [8j, 8j+8) (missing ones = 1)
+// node j of segment r = product of its leaves [8j, 8j+8) (missing ones = 1),
+// written to node dpos[r] + j of out
 __global__ void batch_leaf_nodes(const uint32_t *leaves, const uint64_t *seg,
-                                 const uint64_t *node_pre, int count, uint32_t *out)
+                                 const uint64_t *node_pre, const uint64_t *dpos, int count,
+                                 uint32_t *out)
 {
     const uint64_t total = node_pre[count];
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,7 +121,9 @@ __global__ void batch_leaf_nodes(const uint32_t *leaves, const uint64_t *seg,
         }
     }
 #pragma unroll
-    for (int j = 0; j < kBatchLeafSlot; j++) out[t * kBatchLeafSlot + j] = acc[j];
+    const uint64_t node = dpos[r] + (t - node_pre[r]);
+#pragma unroll
+    for (int j = 0; j < kBatchLeafSlot; j++) out[node * kBatchLeafSlot + j] = acc[j];
 }
 
 __global__ void batch_copy(const CopyJob *jobs, int njobs)
@@ -183,108 +185,206 @@ void run_copy_jobs(Ctx &c, const std::vector<CopyJob> &jobs, cudaStream_t s)
     CAT_CUDA(cudaStreamSynchronize(s));
 }
 
+namespace {
+
+// A copy job of the segmented tree, planned before the level buffers exist:
+// offsets into the launch's source and destination levels (src == kOne
+// writes the value 1; dst_abs, when set, replaces the destination level).
+struct LevelJob {
+    uint64_t src, dst;
+    uint32_t *dst_abs;
+    uint64_t len, cap;
+};
+constexpr uint64_t kOne = ~(uint64_t)0;
+
+__global__ void batch_copy_level(const LevelJob *jobs, int njobs, const uint32_t *src_base,
+                                 uint32_t *dst_base)
+{
+    for (int j = blockIdx.y; j < njobs; j += gridDim.y) {
+        const LevelJob J = jobs[j];
+        uint32_t *dst = J.dst_abs ? J.dst_abs : dst_base + J.dst;
+        const uint32_t *src = J.src == kOne ? nullptr : src_base + J.src;
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < J.cap;
+             i += (uint64_t)gridDim.x * blockDim.x)
+            dst[i] = src ? (i < J.len ? src[i] : 0u) : (uint32_t)(i == 0);
+    }
+}
+
+// Output nodes of all the tree's products, every level's products numbered
+// one after another: run i covers products [rs[i], rs[i+1]) and sends them
+// to nodes dst[i], dst[i] + 1, ... of their level's output.
+__global__ void batch_level_index(const uint64_t *rs, const uint64_t *dst, int runs,
+                                  uint32_t *index)
+{
+    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= rs[runs]) return;
+    const int i = find_segment(rs, runs, k);
+    index[k] = (uint32_t)(dst[i] + (k - rs[i]));
+}
+
+}  // namespace
+
 // The segmented level-synchronous product tree (see segmented_tree in
 // cat_internal.cuh).  Level 0 multiplies eight leaves per node; every later
-// level pads each active segment to an even node count with a node of value 1
-// and multiplies adjacent pairs of the whole level in one batched call.
+// level multiplies adjacent pairs of the whole level in one batched call.
+//
+// Every level's node counts follow from the segment lengths alone, so the
+// whole schedule is planned on the host first and uploaded once; the levels
+// then run back to back without waiting for the device.  A level's buffer
+// holds the segments still multiplying, each padded to an even node count
+// by a node of value 1, then the segments that are down to one node (their
+// roots, copied out).  Each product is written straight to its node of the
+// next level's buffer through an index table, so that no level is gathered
+// or re-packed between products.
 void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> &seg,
                     std::vector<TreeRoot> &roots, cudaStream_t s)
 {
     const size_t count = seg.size() - 1;
     const int nr = (int)count;
-    std::vector<CopyJob> finish;
-    std::vector<uint64_t> nodes(count, 0), node_pre(count + 1, 0);
-    auto sink = [&](size_t r, const uint32_t *src, uint64_t len) {
-        TreeRoot &t = roots[r];
-        if (!t.dst) {
-            const uint64_t n = std::max<uint64_t>(len, 1);
-            t.big.buf = DevBuf<uint32_t>(c, n, s);
-            t.big.n = n;
-            finish.push_back(CopyJob{src, t.big.buf.get(), src ? len : 1, n});
-        } else {
-            finish.push_back(CopyJob{src, t.dst, src ? std::min<uint64_t>(len, t.cap) : 1, t.cap});
-        }
+    struct Level {
+        size_t slot;
+        uint64_t padded, nodes;  // padded multiplying nodes; all nodes of the buffer
+        size_t job0, njobs;      // pads and root copies of this level's buffer
+        uint64_t prod0;          // first product (all levels numbered in turn)
+        size_t run0, nruns;      // runs of this level's products
     };
+    std::vector<LevelJob> jobs;
+    std::vector<Level> levels;
+    std::vector<uint64_t> rs{0}, rdst;  // runs of products
+    auto root_dst = [&](size_t r, uint64_t len, uint64_t &cap) -> uint32_t * {
+        TreeRoot &t = roots[r];
+        if (t.dst) {
+            cap = t.cap;
+            return t.dst;
+        }
+        const uint64_t n = std::max<uint64_t>(len, 1);
+        t.big.buf = DevBuf<uint32_t>(c, n, s);
+        t.big.n = n;
+        cap = n;
+        return t.big.buf.get();
+    };
+    // positions of a level's nodes: multiplying segments first, each padded
+    // to an even count, then the one-node segments
+    auto layout = [&](const std::vector<uint64_t> &cnt, std::vector<uint64_t> &pos,
+                      uint64_t &padded, uint64_t &nodes) {
+        uint64_t at = 0;
+        for (size_t r = 0; r < count; r++)
+            if (cnt[r] >= 2) {
+                pos[r] = at;
+                at += cnt[r] + (cnt[r] & 1);
+            }
+        padded = at;
+        for (size_t r = 0; r < count; r++)
+            if (cnt[r] == 1) pos[r] = at++;
+        nodes = at;
+    };
+    std::vector<uint64_t> cnt(count), node_pre(count + 1, 0), pos(count, 0), nxt_cnt(count),
+        nxt_pos(count, 0);
     for (size_t r = 0; r < count; r++) {
-        const uint64_t L = seg[r + 1] - seg[r];
-        nodes[r] = (L + kBatchLeafSlot - 1) / kBatchLeafSlot;
-        node_pre[r + 1] = node_pre[r] + nodes[r];
-        if (L == 0) sink(r, nullptr, 1);
+        cnt[r] = (seg[r + 1] - seg[r] + kBatchLeafSlot - 1) / kBatchLeafSlot;
+        node_pre[r + 1] = node_pre[r] + cnt[r];
     }
-    size_t slot = kBatchLeafSlot;
-    DevBuf<uint32_t> cur(c, node_pre[count] * slot + 1, s);
+    uint64_t padded = 0, nodes = 0, prod = 0;
+    layout(cnt, pos, padded, nodes);
+    const std::vector<uint64_t> pos0 = pos;
+    const uint64_t nodes0 = nodes;
+    for (size_t r = 0; r < count; r++)  // empty segments: the value 1
+        if (seg[r + 1] == seg[r]) {
+            uint64_t cap = 0;
+            uint32_t *d = root_dst(r, 1, cap);
+            jobs.push_back(LevelJob{kOne, 0, d, 1, cap});
+        }
+    for (size_t slot = kBatchLeafSlot;; slot *= 2) {
+        Level lv{slot, padded, nodes, 0, 0, prod, rs.size() - 1, 0};
+        lv.job0 = levels.empty() ? 0 : jobs.size();
+        for (size_t r = 0; r < count; r++) {
+            if (cnt[r] >= 2 && (cnt[r] & 1))
+                jobs.push_back(LevelJob{kOne, (pos[r] + cnt[r]) * slot, nullptr, 1, slot});
+            if (cnt[r] == 1) {
+                const uint64_t len = std::min<uint64_t>(slot, seg[r + 1] - seg[r]);
+                uint64_t cap = 0;
+                uint32_t *d = root_dst(r, len, cap);
+                jobs.push_back(LevelJob{pos[r] * slot, 0, d, std::min(len, cap), cap});
+            }
+        }
+        lv.njobs = jobs.size() - lv.job0;
+        if (padded == 0) {
+            levels.push_back(lv);
+            break;
+        }
+        for (size_t r = 0; r < count; r++) nxt_cnt[r] = cnt[r] >= 2 ? (cnt[r] + 1) / 2 : 0;
+        uint64_t npadded = 0, nnodes = 0;
+        layout(nxt_cnt, nxt_pos, npadded, nnodes);
+        for (size_t r = 0; r < count; r++)
+            if (cnt[r] >= 2) {
+                rs.push_back(rs.back() + nxt_cnt[r]);
+                rdst.push_back(nxt_pos[r]);
+            }
+        lv.nruns = rs.size() - 1 - lv.run0;
+        prod += padded / 2;
+        levels.push_back(lv);
+        cnt.swap(nxt_cnt);
+        pos.swap(nxt_pos);
+        padded = npadded;
+        nodes = nnodes;
+    }
+    const uint64_t total_prod = prod;
+    const int runs = (int)rdst.size();
+    // one upload: segment starts, level-0 node offsets and positions, runs,
+    // jobs
+    std::vector<uint64_t> blob;
+    auto put = [&](const std::vector<uint64_t> &v) {
+        const size_t at = blob.size();
+        blob.insert(blob.end(), v.begin(), v.end());
+        return at;
+    };
+    const size_t at_seg = put(seg), at_np = put(node_pre), at_pos = put(pos0), at_rs = put(rs),
+                 at_rd = put(rdst), at_jobs = blob.size();
+    static_assert(sizeof(LevelJob) % sizeof(uint64_t) == 0, "LevelJob packs into words");
+    blob.resize(at_jobs + jobs.size() * (sizeof(LevelJob) / sizeof(uint64_t)));
+    if (!jobs.empty()) memcpy(blob.data() + at_jobs, jobs.data(), jobs.size() * sizeof(LevelJob));
+    DevBuf<uint64_t> d_blob = upload(c, blob, s);
+    const uint64_t *d = d_blob.get();
+    const LevelJob *d_jobs = reinterpret_cast<const LevelJob *>(d + at_jobs);
+    DevBuf<uint32_t> index(c, std::max<uint64_t>(total_prod, 1), s);
+    if (total_prod) {
+        batch_level_index<<<(unsigned)((total_prod + 255) / 256), 256, 0, s>>>(
+            d + at_rs, d + at_rd, runs, index.get());
+        CAT_LAUNCH("batch_level_index");
+    }
+    const uint64_t tn = node_pre[count];
+    DevBuf<uint32_t> cur(c, std::max<uint64_t>(nodes0, 1) * kBatchLeafSlot, s);
     {
-        DevBuf<uint64_t> d_seg = upload(c, seg, s);
-        DevBuf<uint64_t> d_np = upload(c, node_pre, s);
-        const uint64_t tn = node_pre[count];
         const int tok = prof_begin(c, "batch_leaf_nodes", s);
         if (tn)
             batch_leaf_nodes<<<(unsigned)((tn + 255) / 256), 256, 0, s>>>(
-                leaves, d_seg.get(), d_np.get(), nr, cur.get());
+                leaves, d + at_seg, d + at_np, d + at_pos, nr, cur.get());
         CAT_LAUNCH("batch_leaf_nodes");
         prof_end(c, tok, s, 4.0 * (double)(seg[count] - seg[0]) + 32.0 * (double)tn);
-        CAT_CUDA(cudaStreamSynchronize(s));
     }
-    // cur holds, for every still-active segment, its nodes (slot limbs each)
-    // at node_pre[r]; a segment with exactly one node is finished.  A root of
-    // L leaves fits in L limbs.
-    for (;;) {
-        std::vector<CopyJob> gather;
-        std::vector<uint64_t> next_pre(count + 1, 0);
-        uint64_t padded = 0;
-        for (size_t r = 0; r < count; r++) {
-            next_pre[r + 1] = next_pre[r];
-            if (nodes[r] == 1) {
-                sink(r, cur.get() + node_pre[r] * slot,
-                     std::min<uint64_t>(slot, seg[r + 1] - seg[r]));
-                nodes[r] = 0;
-            } else if (nodes[r] >= 2) {
-                const uint64_t cnt = nodes[r] + (nodes[r] & 1);
-                gather.push_back(CopyJob{cur.get() + node_pre[r] * slot, nullptr,
-                                         nodes[r] * slot, cnt * slot});
-                next_pre[r + 1] = next_pre[r] + cnt / 2;
-                padded += cnt;
+    for (size_t li = 0; li < levels.size(); li++) {
+        const Level &lv = levels[li];
+        if (lv.njobs) {
+            batch_copy_level<<<dim3(64, (unsigned)std::min<size_t>(lv.njobs, 4096)), 256, 0, s>>>(
+                d_jobs + lv.job0, (int)lv.njobs, cur.get(), cur.get());
+            CAT_LAUNCH("batch_copy_level");
+        }
+        if (lv.padded == 0) break;
+        const size_t slot = lv.slot, nprod = lv.padded / 2, ns = 2 * slot;
+        DevBuf<uint32_t> nxt(c, levels[li + 1].nodes * ns, s);
+        const uint32_t *ix = index.get() + lv.prod0;
+        if (slot > c.comba_max_slot || !comba_level(c, cur.get(), slot, nprod, nxt.get(), s, ix)) {
+            std::vector<uint32_t> host_ix;
+            if (ns > ((size_t)1 << c.max_log)) {  // products by pieces, placed from the host
+                host_ix.resize(nprod);
+                for (size_t i = lv.run0; i < lv.run0 + lv.nruns; i++)
+                    for (uint64_t k = rs[i]; k < rs[i + 1]; k++)
+                        host_ix[k - lv.prod0] = (uint32_t)(rdst[i] + (k - rs[i]));
             }
+            ntt_level(c, cur.get(), slot, nprod, nxt.get(), s, ix,
+                      host_ix.empty() ? nullptr : host_ix.data());
         }
-        if (!finish.empty()) {
-            DevBuf<CopyJob> d_jobs = upload(c, finish, s);
-            const int nj = (int)finish.size();
-            batch_copy<<<dim3(64, std::min(nj, 4096)), 256, 0, s>>>(d_jobs.get(), nj);
-            CAT_LAUNCH("batch_copy");
-            CAT_CUDA(cudaStreamSynchronize(s));
-            finish.clear();
-        }
-        if (padded == 0) break;
-        // padded level: each active segment's nodes, plus a node of value 1
-        // when its count is odd
-        DevBuf<uint32_t> lvl(c, padded * slot, s);
-        {
-            uint64_t at = 0;
-            std::vector<CopyJob> jobs;
-            for (auto &g : gather) {
-                const uint64_t n_own = g.len / slot, cnt = g.cap / slot;
-                jobs.push_back(CopyJob{g.src, lvl.get() + at * slot, g.len, g.len});
-                if (cnt > n_own)
-                    jobs.push_back(CopyJob{nullptr, lvl.get() + (at + n_own) * slot, 1, slot});
-                at += cnt;
-            }
-            DevBuf<CopyJob> d_jobs = upload(c, jobs, s);
-            const int nj = (int)jobs.size();
-            const int tok = prof_begin(c, "batch_gather", s);
-            batch_copy<<<dim3(64, std::min(nj, 4096)), 256, 0, s>>>(d_jobs.get(), nj);
-            CAT_LAUNCH("batch_copy");
-            prof_end(c, tok, s, 8.0 * (double)padded * slot);
-            CAT_CUDA(cudaStreamSynchronize(s));
-        }
-        const size_t nprod = padded / 2, ns = 2 * slot;
-        DevBuf<uint32_t> nxt(c, nprod * ns, s);
-        if (slot > c.comba_max_slot || !comba_level(c, lvl.get(), slot, nprod, nxt.get(), s))
-            ntt_level(c, lvl.get(), slot, nprod, nxt.get(), s);
-        lvl.reset();
         cur = std::move(nxt);
-        slot = ns;
-        node_pre = next_pre;
-        for (size_t r = 0; r < count; r++) nodes[r] = next_pre[r + 1] - next_pre[r];
     }
 }
 

@@ -404,7 +404,15 @@ struct Sink {
     bool dec;
     const uint32_t *add;
     size_t add_tstride, add_len;
+    // when set, product k goes to out + out_index[k] * out_tstride (a device
+    // table), else to out + k * out_tstride
+    const uint32_t *out_index = nullptr;
 };
+
+__host__ __device__ __forceinline__ size_t sink_node(const Sink &o, size_t k)
+{
+    return o.out_index ? (size_t)o.out_index[k] : k;
+}
 
 constexpr uint32_t kDecBase = 1000000000u;
 
@@ -510,6 +518,17 @@ void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> 
 
 // ------------------------------------------------------- internal entry points
 // (all on stream s; lengths are limb counts)
+
+// One level of a product tree: nprod products of adjacent slot-limb nodes
+// (in[2k] times in[2k+1]) into 2*slot-limb nodes of out.  Product k goes to
+// node out_index[k] of out (a device table; out_index_host, where given, is
+// its host copy) or, without a table, to node k.  comba_level returns false
+// for slots it has no schoolbook kernel for.
+bool comba_level(Ctx &c, const uint32_t *in, size_t slot, size_t nprod, uint32_t *out,
+                 cudaStream_t s, const uint32_t *out_index = nullptr);
+void ntt_level(Ctx &c, const uint32_t *level, size_t slot, size_t nprod, uint32_t *out,
+               cudaStream_t s, const uint32_t *out_index = nullptr,
+               const uint32_t *out_index_host = nullptr);
 
 // out[0 .. na+nb) = a * b (exact, zero-padded).  out must hold na + nb limbs.
 void mul_into(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,

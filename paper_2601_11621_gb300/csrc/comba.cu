@@ -56,7 +56,8 @@ __global__ void leaf_products(const uint32_t *v, size_t count, uint32_t *out, si
 // ---------------------------------------------- one product per thread
 
 template <int S>
-__global__ void comba_thread(const uint32_t *in, size_t nprod, uint32_t *out)
+__global__ void comba_thread(const uint32_t *in, size_t nprod, uint32_t *out,
+                             const uint32_t *out_index)
 {
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nprod) return;
@@ -82,7 +83,8 @@ __global__ void comba_thread(const uint32_t *in, size_t nprod, uint32_t *out)
         c2 = 0;
     }
     O[2 * S - 1] = c0;
-    uint4 *o4 = reinterpret_cast<uint4 *>(out + 2 * k * S);
+    const size_t node = out_index ? (size_t)out_index[k] : k;
+    uint4 *o4 = reinterpret_cast<uint4 *>(out + 2 * node * S);
 #pragma unroll
     for (int i = 0; i < S / 2; i++)
         o4[i] = make_uint4(O[4 * i], O[4 * i + 1], O[4 * i + 2], O[4 * i + 3]);
@@ -106,7 +108,8 @@ constexpr int kWarpsPerBlock = 8;
 // one-bit carries are resolved by a generate/propagate scan across the warp.
 template <int S>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) comba_warp(const uint32_t *in,
-                                                                  size_t nprod, uint32_t *out)
+                                                                  size_t nprod, uint32_t *out,
+                                                                  const uint32_t *out_index)
 {
     constexpr int W = 2 * S / 32;
     static_assert(W >= 2, "warp Comba needs at least two columns per lane");
@@ -196,7 +199,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) comba_warp(const uint32_t
         limb[w] = (uint32_t)t;
         cin = (uint32_t)(t >> 32);
     }
-    uint32_t *o = out + 2 * k * S + lane * W;
+    const size_t node = out_index ? (size_t)out_index[k] : k;
+    uint32_t *o = out + 2 * node * S + lane * W;
 #pragma unroll
     for (int w = 0; w < W; w++) o[w] = limb[w];
 }
@@ -232,7 +236,7 @@ void leaf_level(Ctx &c, const uint32_t *values, size_t count, uint32_t *out, siz
 // Products of adjacent slot-limb nodes into 2*slot-limb slots, for slots
 // handled by schoolbook multiplication.  Returns false if slot is too large.
 bool comba_level(Ctx &c, const uint32_t *in, size_t slot, size_t nprod, uint32_t *out,
-                 cudaStream_t s)
+                 cudaStream_t s, const uint32_t *out_index)
 {
     if (nprod == 0) return true;
     if (slot > 256) return false;
@@ -241,12 +245,12 @@ bool comba_level(Ctx &c, const uint32_t *in, size_t slot, size_t nprod, uint32_t
     const unsigned gt = (unsigned)((nprod + tb - 1) / tb);
     const unsigned gw = (unsigned)((nprod + kWarpsPerBlock - 1) / kWarpsPerBlock);
     switch (slot) {
-    case 8: comba_thread<8><<<gt, tb, 0, s>>>(in, nprod, out); break;
-    case 16: comba_thread<16><<<gt, tb, 0, s>>>(in, nprod, out); break;
-    case 32: comba_warp<32><<<gw, 32 * kWarpsPerBlock, 0, s>>>(in, nprod, out); break;
-    case 64: comba_warp<64><<<gw, 32 * kWarpsPerBlock, 0, s>>>(in, nprod, out); break;
-    case 128: comba_warp<128><<<gw, 32 * kWarpsPerBlock, 0, s>>>(in, nprod, out); break;
-    case 256: comba_warp<256><<<gw, 32 * kWarpsPerBlock, 0, s>>>(in, nprod, out); break;
+    case 8: comba_thread<8><<<gt, tb, 0, s>>>(in, nprod, out, out_index); break;
+    case 16: comba_thread<16><<<gt, tb, 0, s>>>(in, nprod, out, out_index); break;
+    case 32: comba_warp<32><<<gw, 32 * kWarpsPerBlock, 0, s>>>(in, nprod, out, out_index); break;
+    case 64: comba_warp<64><<<gw, 32 * kWarpsPerBlock, 0, s>>>(in, nprod, out, out_index); break;
+    case 128: comba_warp<128><<<gw, 32 * kWarpsPerBlock, 0, s>>>(in, nprod, out, out_index); break;
+    case 256: comba_warp<256><<<gw, 32 * kWarpsPerBlock, 0, s>>>(in, nprod, out, out_index); break;
     default: return false;
     }
     CAT_LAUNCH("comba_level");

@@ -405,6 +405,7 @@ __global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
     const size_t k = blockIdx.x / tiles;
     const size_t t = blockIdx.x % tiles;
     const size_t jt = t * kTile;
+    const size_t node = sink_node(a.sink, k);
     const uint32_t *g0 = a.G + (k << a.n) + jt;
     const int j0 = threadIdx.x * kLimbsPerThread;
     constexpr bool dec = DEC;
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(kTileThreads) crt_carry_tiles(CrtArgs a)
     const uint32_t *add = ADD ? o.add + k * o.add_tstride + jt : nullptr;
     uint32_t map;
     tile_carry_t<DEC ? 1 : 0, ADD ? 1 : 0>(run, h1, h2a, h2b, kTile,
-                                           o.out + k * o.out_tstride + jt, remaining, dec, add,
+                                           o.out + node * o.out_tstride + jt, remaining, dec, add,
                                            (long)o.add_len - (long)jt, wsm, &map);
     if (threadIdx.x == 0) a.tile_maps[blockIdx.x] = (uint8_t)map;
 }
@@ -477,14 +478,15 @@ __global__ void __launch_bounds__(1024) carry_tile_scan(uint8_t *tile_maps, size
 // Add each tile's carry-in to its first limbs (rarely more than one), in
 // base 2^32 or (dec) 10^9.
 __global__ void carry_fix(const uint8_t *tile_cin, size_t tiles_total, size_t tiles, int n,
-                          uint32_t *out, size_t out_tstride, size_t out_len, bool dec)
+                          uint32_t *out, size_t out_tstride, size_t out_len, bool dec,
+                          const uint32_t *out_index = nullptr)
 {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= tiles_total) return;
     uint32_t c = tile_cin[t];
     if (!c) return;
     const size_t k = t / tiles, tt = t % tiles;
-    uint32_t *o = out + k * out_tstride;
+    uint32_t *o = out + (out_index ? (size_t)out_index[k] : k) * out_tstride;
     size_t j = tt * kTile;
     const size_t end = std::min(j + kTile, out_len);
     for (; c && j < end; j++) {
@@ -641,7 +643,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2) ntt_mul_fused(FusedArgs a)
         for (int i = 0; i < kLimbsPerThread; i++) words_to_dec(run.c0[i], run.c1[i], run.c2[i]);
     uint32_t h1, h2a, h2b, map;
     run_halo(run, 0u, 0u, 0u, hsm, h1, h2a, h2b);
-    tile_carry(run, h1, h2a, h2b, L, o.out + k * o.out_tstride, (long)o.out_len, o.dec,
+    tile_carry(run, h1, h2a, h2b, L, o.out + sink_node(o, k) * o.out_tstride, (long)o.out_len, o.dec,
                o.add ? o.add + k * o.add_tstride : nullptr, (long)o.add_len, wsm, &map);
 }
 
@@ -939,7 +941,7 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     tok = prof_begin(c, "carry_fix", s);
     carry_fix<<<(unsigned)((tt + 255) / 256), 256, 0, s>>>(maps.get(), tt, tiles, n, sink.out,
                                                              sink.out_tstride, sink.out_len,
-                                                             sink.dec);
+                                                             sink.dec, sink.out_index);
     CAT_LAUNCH("carry_fix");
     prof_end(c, tok, s, (double)tt);
 }
@@ -999,24 +1001,27 @@ static int ceil_log2(size_t x)
 // Level products of the fixed-slot product tree: nprod products of adjacent
 // slot-limb nodes of `level`, each written into a 2*slot-limb slot of out.
 void ntt_level(Ctx &c, const uint32_t *level, size_t slot, size_t nprod, uint32_t *out,
-               cudaStream_t s)
+               cudaStream_t s, const uint32_t *out_index, const uint32_t *out_index_host)
 {
     const int n = ceil_log2(2 * slot);
     Operand x{level, slot, slot};
     if (n > c.max_log) {  // longer than one transform: each pair by pieces
+        if (out_index && !out_index_host) fail(CAT_EINVAL, "indexed level needs its host table");
         for (size_t k = 0; k < nprod; k++) {
-            uint32_t *o = out + 2 * k * slot;
+            uint32_t *o = out + 2 * (out_index ? (size_t)out_index_host[k] : k) * slot;
             CAT_CUDA(cudaMemsetAsync(o, 0, 8 * slot, s));
             mul_acc(c, level + 2 * k * slot, slot, level + (2 * k + 1) * slot, slot, o, 2 * slot,
                     false, s);
         }
         return;
     }
+    Sink sink = plain_sink(out, 2 * slot, 2 * slot);
+    sink.out_index = out_index;
     if (n <= kFusedMaxLog) {
         Operand a{level, 2 * slot, slot}, b{level + slot, 2 * slot, slot};
-        ntt_mul_small(c, n, nprod, a, b, false, plain_sink(out, 2 * slot, 2 * slot), s);
+        ntt_mul_small(c, n, nprod, a, b, false, sink, s);
     } else {
-        ntt_mul_multipass(c, n, PAIR_ADJACENT, nprod, x, x, plain_sink(out, 2 * slot, 2 * slot), s);
+        ntt_mul_multipass(c, n, PAIR_ADJACENT, nprod, x, x, sink, s);
     }
 }
 

@@ -22,11 +22,7 @@ namespace cat {
 // comba.cu
 void leaf_level(Ctx &c, const uint32_t *values, size_t count, uint32_t *out, size_t nodes,
                 cudaStream_t s);
-bool comba_level(Ctx &c, const uint32_t *in, size_t slot, size_t nprod, uint32_t *out,
-                 cudaStream_t s);
 // ntt.cu
-void ntt_level(Ctx &c, const uint32_t *level, size_t slot, size_t nprod, uint32_t *out,
-               cudaStream_t s);
 void ntt_mul(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
              uint32_t *out, cudaStream_t s);
 

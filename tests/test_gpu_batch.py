@@ -68,3 +68,33 @@ def test_config3_batch(ctx, cat_lib, orc):
         kind, n = reqs[i]
         alone = host(cat_lib.cat_exact(ctx, kind, n))
         assert alone.shape == res[i].shape and (alone == res[i]).all(), (kind, n)
+
+
+@pytest.fixture(scope="module")
+def small_transform_ctx(cat_lib):
+    """A context whose single-transform limit is 2^13 points: tree nodes
+    above 4,096 limbs are multiplied by pieces."""
+    import os
+    old = os.environ.get("CAT_MAX_TRANSFORM_LOG")
+    os.environ["CAT_MAX_TRANSFORM_LOG"] = "13"
+    try:
+        c = cat_lib.Context(0)
+    finally:
+        if old is None:
+            del os.environ["CAT_MAX_TRANSFORM_LOG"]
+        else:
+            os.environ["CAT_MAX_TRANSFORM_LOG"] = old
+    yield c
+    c.close()
+
+
+def test_batch_with_products_by_pieces(small_transform_ctx, cat_lib, orc):
+    """The batched tree's top levels through the piece path (each product
+    placed by the host copy of its level's index table), beside small
+    requests that finish early; 40000! goes through the bit-decomposed
+    reconstruction, whose segmented tree takes the same path."""
+    reqs = [(0, 262144), (1, 5), (2, 40000), (0, 3), (1, 99991), (0, 0)]
+    out, offs, lens = cat_lib.cat_exact_batch(small_transform_ctx, reqs)
+    for (kind, n), got in zip(reqs, split(out, offs, lens)):
+        want = orc.exact(kind, n)
+        assert got.shape == want.shape and (got == want).all(), (kind, n)
