@@ -21,7 +21,7 @@ Prints one JSON line (rank 0):
   cpu_baseline the CPU oracle (plain C) timed on all host cores at n = 10^6,
                10^7 and 5 * 10^7, extrapolated to the paper's n by a fitted
                growth exponent (single-threaded runs reported beside);
-  mul_sweep    bigint_mul of seeded random operands at 2^16, 2^20, 2^24
+  mul_sweep    bigint_mul of seeded random operands at 2^10, 2^12, ..., 2^26
                uint64 limbs (ratios 1:1 and 1:4): GB/s of algorithmic bytes,
                each product checked modulo two primes;
   batched      4,096 seeded requests (C(n) / C(2n, n), n log-uniform in
@@ -335,11 +335,17 @@ def binomial_mod(kind: int, n: int, q: int) -> int:
 CHECK_PRIMES = (2147483647, 2147483629)  # primes below 2^31, above every 2n used here
 
 
+# bigint_mul sweep sizes (log2 of the uint64 limbs of the longer operand):
+# every second power from 2^10 to 2^26; the 2^26 products (2^28 uint32
+# limbs) are longer than one transform and go by pieces
+SWEEP_LOGS = (10, 12, 14, 16, 18, 20, 22, 24, 26)
+
+
 def mul_sweep(ctx, capi, W, dev):
     import torch
     out = []
     stream = torch.cuda.current_stream()
-    for k in (16, 20, 24):
+    for k in SWEEP_LOGS:
         for ratio in (1, 4):
             na64, nb64 = 1 << k, (1 << k) // ratio
             a = torch.from_numpy(W.random_limbs(na64, 100 + k).view("i4")).to(dev)
@@ -348,7 +354,7 @@ def mul_sweep(ctx, capi, W, dev):
             for q in CHECK_PRIMES:
                 if limbs_mod_dev(r, q) != limbs_mod_dev(a, q) * limbs_mod_dev(b, q) % q:
                     raise RuntimeError(f"mul_sweep check failed at 2^{k} 1:{ratio}")
-            reps = 5 if k < 24 else 3
+            reps = 20 if k <= 16 else (5 if k < 24 else 3)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
