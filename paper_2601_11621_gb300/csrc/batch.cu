@@ -95,22 +95,22 @@ __global__ void batch_seg_starts(const uint64_t *pre, int count, const uint32_t 
     seg[r] = (r < count && pre[r] < pre[count]) ? pos[pre[r]] : total_leaves;
 }
 
-// node j of segment r = product of its leaves [8j, 8j+8) (missing ones = 1),
+// node j of segment r = product of its leaves [lpn j, lpn j + lpn) (missing
+// ones = 1; the caller picks lpn so that the product fits eight limbs),
 // written to node dpos[r] + j of out
 __global__ void batch_leaf_nodes(const uint32_t *leaves, const uint64_t *seg,
                                  const uint64_t *node_pre, const uint64_t *dpos, int count,
-                                 uint32_t *out)
+                                 int lpn, uint32_t *out)
 {
     const uint64_t total = node_pre[count];
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
     const int r = find_segment(node_pre, count, t);
-    const uint64_t first = seg[r] + (t - node_pre[r]) * kBatchLeafSlot, end = seg[r + 1];
+    const uint64_t first = seg[r] + (t - node_pre[r]) * (uint64_t)lpn, end = seg[r + 1];
     uint32_t acc[kBatchLeafSlot];
 #pragma unroll
     for (int j = 0; j < kBatchLeafSlot; j++) acc[j] = j == 0;
-#pragma unroll
-    for (int k = 0; k < kBatchLeafSlot; k++) {
+    for (int k = 0; k < lpn; k++) {
         const uint32_t x = first + k < end ? leaves[first + k] : 1u;
         uint32_t carry = 0;
 #pragma unroll
@@ -237,10 +237,12 @@ __global__ void batch_level_index(const uint64_t *rs, const uint64_t *dst, int r
 // next level's buffer through an index table, so that no level is gathered
 // or re-packed between products.
 void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> &seg,
-                    std::vector<TreeRoot> &roots, cudaStream_t s)
+                    std::vector<TreeRoot> &roots, cudaStream_t s, int leaf_bits)
 {
     const size_t count = seg.size() - 1;
     const int nr = (int)count;
+    // leaves per first-level node: their product stays below 2^(32 * 8)
+    const int lpn = std::min(32, 32 * kBatchLeafSlot / std::max(1, std::min(32, leaf_bits)));
     struct Level {
         size_t slot;
         uint64_t padded, nodes;  // padded multiplying nodes; all nodes of the buffer
@@ -281,7 +283,7 @@ void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> 
     std::vector<uint64_t> cnt(count), node_pre(count + 1, 0), pos(count, 0), nxt_cnt(count),
         nxt_pos(count, 0);
     for (size_t r = 0; r < count; r++) {
-        cnt[r] = (seg[r + 1] - seg[r] + kBatchLeafSlot - 1) / kBatchLeafSlot;
+        cnt[r] = (seg[r + 1] - seg[r] + lpn - 1) / lpn;
         node_pre[r + 1] = node_pre[r] + cnt[r];
     }
     uint64_t padded = 0, nodes = 0, prod = 0;
@@ -358,7 +360,7 @@ void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> 
         const int tok = prof_begin(c, "batch_leaf_nodes", s);
         if (tn)
             batch_leaf_nodes<<<(unsigned)((tn + 255) / 256), 256, 0, s>>>(
-                leaves, d + at_seg, d + at_np, d + at_pos, nr, cur.get());
+                leaves, d + at_seg, d + at_np, d + at_pos, nr, lpn, cur.get());
         CAT_LAUNCH("batch_leaf_nodes");
         prof_end(c, tok, s, 4.0 * (double)(seg[count] - seg[0]) + 32.0 * (double)tn);
     }
@@ -461,7 +463,9 @@ static void batch_core(Ctx &c, const cat_request *reqs, size_t count, uint32_t *
         roots[r].dst = out + offsets[r];
         roots[r].cap = caps[r];
     }
-    segmented_tree(c, leaves.get(), seg, roots, s);
+    int leaf_bits = 1;  // every leaf is a prime <= M
+    while (leaf_bits < 32 && (M >> leaf_bits)) leaf_bits++;
+    segmented_tree(c, leaves.get(), seg, roots, s, leaf_bits);
     leaves.reset();
     // ---- lengths
     DevBuf<uint64_t> d_off = upload(c, std::vector<uint64_t>(offsets, offsets + count), s);

@@ -512,9 +512,11 @@ struct TreeRoot {
 
 // Products of the segments leaves[seg[j] .. seg[j+1]) for all j at once: one
 // level-synchronous tree in which every level of every segment is a single
-// batched multiplication.  An empty segment's product is 1.
+// batched multiplication.  An empty segment's product is 1.  Every leaf is
+// below 2^leaf_bits, so that a first-level node of eight limbs takes
+// floor(256 / leaf_bits) leaves (at most 32).
 void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> &seg,
-                    std::vector<TreeRoot> &roots, cudaStream_t s);
+                    std::vector<TreeRoot> &roots, cudaStream_t s, int leaf_bits = 32);
 
 // ------------------------------------------------------- internal entry points
 // (all on stream s; lengths are limb counts)
