@@ -242,7 +242,7 @@ void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> 
     const size_t count = seg.size() - 1;
     const int nr = (int)count;
     // leaves per first-level node: their product stays below 2^(32 * 8)
-    const int lpn = std::min(32, 32 * kBatchLeafSlot / std::max(1, std::min(32, leaf_bits)));
+    const int lpn = leaves_per_node(leaf_bits);
     struct Level {
         size_t slot;
         uint64_t padded, nodes;  // padded multiplying nodes; all nodes of the buffer
@@ -463,9 +463,7 @@ static void batch_core(Ctx &c, const cat_request *reqs, size_t count, uint32_t *
         roots[r].dst = out + offsets[r];
         roots[r].cap = caps[r];
     }
-    int leaf_bits = 1;  // every leaf is a prime <= M
-    while (leaf_bits < 32 && (M >> leaf_bits)) leaf_bits++;
-    segmented_tree(c, leaves.get(), seg, roots, s, leaf_bits);
+    segmented_tree(c, leaves.get(), seg, roots, s, bits_below(M));  // leaves: primes <= M
     leaves.reset();
     // ---- lengths
     DevBuf<uint64_t> d_off = upload(c, std::vector<uint64_t>(offsets, offsets + count), s);
@@ -521,7 +519,7 @@ void exact_batch(Ctx &c, const cat_request *reqs, size_t count, uint32_t *out, s
         factor(c, reqs[r].n, reqs[r].kind, &f, s);
         Big v;
         try {
-            v = reconstruct(c, &f, s);
+            v = reconstruct(c, &f, s, bits_below(reqs[r].n));  // primes <= n
         } catch (...) {
             factor_free(c, &f);
             throw;

@@ -276,7 +276,9 @@ int cat_exact(cat_ctx *ctx, int kind, uint64_t n, uint32_t *out, size_t cap,
                 cat::reconstruct_into(ctx->c, &f, out, cap, false, out_len, s);
                 return;
             }
-            cat::Big r = cat::reconstruct(ctx->c, &f, s);
+            // the primes are at most the sieve limit
+            cat::Big r = cat::reconstruct(ctx->c, &f, s,
+                                          cat::bits_below(kind == CAT_FACTORIAL ? n : 2 * n));
             cat::factor_free(ctx->c, &f);
             copy_out(ctx->c, r, out, cap, out_len, s);
         } catch (...) {
@@ -316,7 +318,9 @@ int cat_ratio_exact(cat_ctx *ctx, const uint64_t *a, int ka, const uint64_t *b, 
                 cat::reconstruct_into(ctx->c, &f, out, cap, false, out_len, s);
                 return;
             }
-            cat::Big r = cat::reconstruct(ctx->c, &f, s);
+            uint64_t top = 1;  // the primes are at most the largest numerator term
+            for (int i = 0; i < q.ka; i++) top = std::max<uint64_t>(top, q.a[i]);
+            cat::Big r = cat::reconstruct(ctx->c, &f, s, cat::bits_below(top));
             cat::factor_free(ctx->c, &f);
             copy_out(ctx->c, r, out, cap, out_len, s);
         } catch (...) {
@@ -367,7 +371,8 @@ int cat_exact_host(cat_ctx *ctx, int kind, uint64_t n, uint32_t *host_out, size_
                 cat::reconstruct_into(ctx->c, &f, host_out, cap, true, out_len, s);
                 return;
             }
-            r = cat::reconstruct(ctx->c, &f, s);
+            r = cat::reconstruct(ctx->c, &f, s,
+                                 cat::bits_below(kind == CAT_FACTORIAL ? n : 2 * n));
         } catch (...) {
             cat::factor_free(ctx->c, &f);
             throw;

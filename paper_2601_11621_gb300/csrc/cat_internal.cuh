@@ -510,6 +510,24 @@ struct TreeRoot {
     Big big;
 };
 
+// Leaves of a product tree per first-level node (eight limbs) when every
+// leaf is below 2^bits: their product stays below 2^256.
+inline int leaves_per_node(int bits)
+{
+    bits = bits < 1 ? 1 : (bits > 32 ? 32 : bits);
+    const int k = 256 / bits;
+    return k > 32 ? 32 : k;
+}
+
+// Bits of the largest value <= limit (limit < 2^32): a bound on the primes
+// of a factorisation whose sieve stopped at limit.
+inline int bits_below(uint64_t limit)
+{
+    int b = 1;
+    while (b < 32 && (limit >> b)) b++;
+    return b;
+}
+
 // Products of the segments leaves[seg[j] .. seg[j+1]) for all j at once: one
 // level-synchronous tree in which every level of every segment is a single
 // batched multiplication.  An empty segment's product is 1.  Every leaf is
@@ -560,8 +578,10 @@ size_t normalized_length(Ctx &c, const uint32_t *x, size_t n, cudaStream_t s);
 // Product of count 32-bit values (balanced tree).  Returns the result.
 // The product of values[0 .. count), times *extra when given; exact = false
 // returns a length bound (zero top limbs) without a host read-back (tree.cu).
+// Every value is below 2^leaf_bits: a first-level node of eight limbs then
+// takes leaves_per_node(leaf_bits) values.
 Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s,
-                 const Big *extra = nullptr, bool exact = true);
+                 const Big *extra = nullptr, bool exact = true, int leaf_bits = 32);
 // a^e.
 Big power(Ctx &c, const uint32_t *a, size_t na, uint64_t e, cudaStream_t s, bool exact = true);
 // Factorial ratios (Sec. 6.3): N = prod_i a_i! / prod_j b_j!.  A Ratio also
@@ -589,7 +609,8 @@ void factor_free(Ctx &c, cat_factorization *f);
 // device, a copy-engine transfer otherwise.
 void copy_to_host(Ctx &c, uint32_t *host, const uint32_t *dev, size_t n, cudaStream_t s);
 // Algorithm 2 on a factorisation; returns the result (normalised length).
-Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s);
+// Every prime of f is below 2^leaf_bits (32 when nothing smaller is known).
+Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s, int leaf_bits = 32);
 // Whether the in-core reconstruction of f would exceed the context's HBM
 // budget, and Algorithm 2 within the budget (ooc.cu): copies f's primes to
 // pinned host memory (and, with release, frees f's device arrays), multiplies

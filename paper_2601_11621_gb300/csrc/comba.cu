@@ -26,9 +26,11 @@ __device__ __forceinline__ void mac96(uint32_t a, uint32_t b, uint32_t &c0, uint
 
 constexpr int kLeafSlot = 8;
 
-// Node i = product of values[8i .. 8i+8) (values past `count` count as 1),
+// Node i (eight limbs) = product of values[lpn i .. lpn i + lpn) (values
+// past `count` count as 1; the caller picks lpn so that the product fits),
 // accumulated by single-limb multiplications.
-__global__ void leaf_products(const uint32_t *v, size_t count, uint32_t *out, size_t nodes)
+__global__ void leaf_products(const uint32_t *v, size_t count, uint32_t *out, size_t nodes,
+                              int lpn)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nodes) return;
@@ -36,9 +38,8 @@ __global__ void leaf_products(const uint32_t *v, size_t count, uint32_t *out, si
 #pragma unroll
     for (int j = 0; j < kLeafSlot; j++) acc[j] = 0;
     acc[0] = 1;
-#pragma unroll
-    for (int k = 0; k < kLeafSlot; k++) {
-        const size_t idx = i * kLeafSlot + k;
+    for (int k = 0; k < lpn; k++) {
+        const size_t idx = i * (size_t)lpn + k;
         const uint32_t x = idx < count ? v[idx] : 1u;
         uint32_t carry = 0;
 #pragma unroll
@@ -224,10 +225,11 @@ __global__ void find_top(const uint32_t *x, size_t n, unsigned long long *top)
 // ----------------------------------------------------------- host side
 
 void leaf_level(Ctx &c, const uint32_t *values, size_t count, uint32_t *out, size_t nodes,
-                cudaStream_t s)
+                int lpn, cudaStream_t s)
 {
     const int tok = prof_begin(c, "leaf_products", s);
-    leaf_products<<<(unsigned)((nodes + 255) / 256), 256, 0, s>>>(values, count, out, nodes);
+    leaf_products<<<(unsigned)((nodes + 255) / 256), 256, 0, s>>>(values, count, out, nodes,
+                                                                    lpn);
     CAT_LAUNCH("leaf_products");
     prof_end(c, tok, s, 4.0 * (double)count + 32.0 * (double)nodes,
              4.0 * (double)count + 32.0 * (double)nodes);

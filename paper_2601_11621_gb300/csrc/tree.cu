@@ -21,7 +21,7 @@ namespace cat {
 
 // comba.cu
 void leaf_level(Ctx &c, const uint32_t *values, size_t count, uint32_t *out, size_t nodes,
-                cudaStream_t s);
+                int lpn, cudaStream_t s);
 // ntt.cu
 void ntt_mul(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb,
              uint32_t *out, cudaStream_t s);
@@ -114,10 +114,10 @@ void mul_into(Ctx &c, const uint32_t *a, size_t na, const uint32_t *b, size_t nb
 static Big copy_big(Ctx &c, const uint32_t *a, size_t n, cudaStream_t s);
 static Big mul_big(Ctx &c, const Big &x, const Big &y, cudaStream_t s, bool exact = true);
 
-// Levels above the leaves of a tree over `count` values.
-static int tree_depth(size_t count)
+// Levels above the leaves of a tree over `count` values, lpn to a node.
+static int tree_depth(size_t count, int lpn)
 {
-    size_t nodes = (count + kLeafSlot - 1) / kLeafSlot;
+    size_t nodes = (count + lpn - 1) / lpn;
     int d = 0;
     for (; nodes > 1; d++) nodes = (nodes + 1) / 2;
     return d;
@@ -132,24 +132,26 @@ static int tree_depth(size_t count)
 // top slot (zero-padded) as the length instead of reading the true length
 // back: no host synchronisation.
 Big tree_product(Ctx &c, const uint32_t *values, size_t count, cudaStream_t s, const Big *extra,
-                 bool exact)
+                 bool exact, int leaf_bits)
 {
     NvtxRange range("product tree");
     if (count == 0) return extra ? copy_big(c, extra->buf.get(), extra->n, s) : make_one(c, s);
+    const int lpn = leaves_per_node(leaf_bits);
     size_t total = count, inj_slot = 0;
     if (extra) {
         size_t S = 2 * kLeafSlot;
         while (S < extra->n) S <<= 1;
-        const size_t padded = (count + S - 1) / S * S + S;
-        if (tree_depth(padded) == tree_depth(count)) {
+        const size_t per = S / kLeafSlot * (size_t)lpn;  // leaves under one node of slot S
+        const size_t padded = (count + per - 1) / per * per + per;
+        if (tree_depth(padded, lpn) == tree_depth(count, lpn)) {
             total = padded;
             inj_slot = S;
         }
     }
     size_t slot = kLeafSlot;
-    size_t nodes = (total + kLeafSlot - 1) / kLeafSlot;
+    size_t nodes = (total + lpn - 1) / lpn;
     DevBuf<uint32_t> cur(c, nodes * slot, s);
-    leaf_level(c, values, count, cur.get(), nodes, s);
+    leaf_level(c, values, count, cur.get(), nodes, lpn, s);
     while (nodes > 1) {
         NvtxRange level("tree level");
         const size_t nprod = nodes / 2, odd = nodes & 1, nn = nprod + odd, ns = 2 * slot;
@@ -234,7 +236,7 @@ constexpr uint64_t kManyGroups = 64;
 // X = R_top; X = X^2 R_b for b below the top bit.  Same integer as
 // Algorithm 2 with about 2 log2(max e) large multiplications instead of one
 // powering chain per group.
-static Big reconstruct_bits(Ctx &c, const cat_factorization *f, cudaStream_t s)
+static Big reconstruct_bits(Ctx &c, const cat_factorization *f, cudaStream_t s, int leaf_bits)
 {
     uint64_t emax = 0;
     for (uint64_t g = 0; g < f->num_groups; g++) emax = std::max(emax, f->host_exps[g]);
@@ -260,7 +262,7 @@ static Big reconstruct_bits(Ctx &c, const cat_factorization *f, cudaStream_t s)
     }
     run_copy_jobs(c, jobs, s);
     std::vector<TreeRoot> R(B);
-    segmented_tree(c, leaves.get(), seg, R, s);
+    segmented_tree(c, leaves.get(), seg, R, s, leaf_bits);
     leaves.reset();
     for (int b = 0; b < B; b++) R[b].big.n = trim(c, R[b].big.buf.get(), R[b].big.n, s);
     Big X = std::move(R[B - 1].big);
@@ -274,10 +276,10 @@ static Big reconstruct_bits(Ctx &c, const cat_factorization *f, cudaStream_t s)
 // Algorithm 2: Q_e by the tree, P_e = Q_e^e, then the P_e combined by
 // repeatedly multiplying the two shortest (equal-length operands meet
 // first, so intermediates stay as short as possible).
-Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s)
+Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s, int leaf_bits)
 {
     NvtxRange range("phase2: reconstruction");
-    if (f->num_groups > kManyGroups) return reconstruct_bits(c, f, s);
+    if (f->num_groups > kManyGroups) return reconstruct_bits(c, f, s, leaf_bits);
     // P_e = Q_e^e for e >= 2 first, combined into R; then Q_1's tree takes R
     // in as one of its nodes, so that the long P_1 needs no final product
     // (the same integer: the final product of the P_e, re-associated).  The
@@ -292,7 +294,7 @@ Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s)
             continue;
         }
         const uint64_t off = f->host_offsets[g], cnt = f->host_offsets[g + 1] - off;
-        Big Q = tree_product(c, f->primes + off, cnt, s, nullptr, false);
+        Big Q = tree_product(c, f->primes + off, cnt, s, nullptr, false, leaf_bits);
         P.push_back(power(c, Q.buf.get(), Q.n, f->host_exps[g], s, false));
     }
     while (P.size() > 1) {
@@ -309,7 +311,7 @@ Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s)
         return std::move(P[0]);
     }
     const uint64_t off = f->host_offsets[g1], cnt = f->host_offsets[g1 + 1] - off;
-    return tree_product(c, f->primes + off, cnt, s, P.empty() ? nullptr : &P[0]);
+    return tree_product(c, f->primes + off, cnt, s, P.empty() ? nullptr : &P[0], true, leaf_bits);
 }
 
 }  // namespace cat

@@ -37,7 +37,12 @@ def in_core_peak(cat_lib, kind, n):
     (0, 2, 300_000), (0, 0, 300_000), (2, 1, 300_000),
 ])
 def test_budgeted_exact_matches_oracle(cat_lib, orc, kind, n, budget):
-    assert n < 100 or in_core_peak(cat_lib, kind, n) > budget  # really out of core
+    # really out of core: the listed budget or 80 % of the measured in-core
+    # peak, whichever is smaller
+    if n >= 100:
+        peak_in_core = in_core_peak(cat_lib, kind, n)
+        budget = min(budget, peak_in_core * 4 // 5)
+        assert peak_in_core > budget
     c = cat_lib.Context(0, hbm_budget_bytes=budget)
     try:
         got = host(cat_lib.cat_exact(c, kind, n))
