@@ -40,6 +40,26 @@ __device__ __forceinline__ int find_segment(const uint64_t *pre, int count, uint
     return lo;
 }
 
+// The segment of flat index t (< pre[count]) for a block of consecutive
+// indices: one binary search per block (for its first index), then a short
+// walk forward; a thread more than a few segments past the block's first one
+// searches for itself.  Every thread of the block must call it.
+__device__ __forceinline__ int block_segment(const uint64_t *pre, int count, uint64_t t)
+{
+    __shared__ int first;
+    const uint64_t total = pre[count];
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x;
+        first = t0 < total ? find_segment(pre, count, t0) : 0;
+    }
+    __syncthreads();
+    if (t >= total) return 0;
+    int r = first;
+    for (int k = 0; k < 8 && pre[r + 1] <= t; k++) r++;
+    if (pre[r + 1] <= t) r = find_segment(pre, count, t);
+    return r;
+}
+
 // pi(limit_r) for each request: binary search in the ascending prime list
 __global__ void count_primes_le(const uint32_t *primes, uint64_t np, const uint64_t *limits,
                                 int count, uint64_t *out)
@@ -65,25 +85,34 @@ __global__ void batch_exponents(const uint32_t *primes, const uint64_t *pre, int
 {
     const uint64_t total = pre[count];
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = block_segment(pre, count, t);
     if (t >= total) return;
-    const int r = find_segment(pre, count, t);
-    const int64_t v = exponent_of(primes[t - pre[r]], reqs[r].n, reqs[r].kind);
+    const uint32_t p = primes[t - pre[r]], n = reqs[r].n;
+    const int kind = reqs[r].kind;
+    // primes above sqrt(2n) of the binomial kinds: one division at most
+    if (kind != CAT_FACTORIAL && (uint64_t)p * p > 2 * (uint64_t)n) {
+        e[t] = unit_exponent(p, n, kind);
+        return;
+    }
+    const int64_t v = exponent_of(p, n, kind);
     if (v < 0) atomicOr(negative, 1u);
     e[t] = v < 0 ? 0u : (uint32_t)v;
 }
 
-// after the scan: pos[t] = first leaf slot of flat index t; write p e times
+// after the scan: pos[t] = first leaf slot of flat index t, and the exponent
+// of flat index t is pos[t + 1] - pos[t]; write p that many times
 __global__ void batch_leaves(const uint32_t *primes, const uint64_t *pre, int count,
-                             const ReqDev *reqs, const uint32_t *pos, uint32_t *leaves)
+                             const uint32_t *pos, uint32_t *leaves)
 {
     const uint64_t total = pre[count];
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = block_segment(pre, count, t);
     if (t >= total) return;
-    const int r = find_segment(pre, count, t);
-    const uint32_t p = primes[t - pre[r]];
-    const int64_t v = exponent_of(p, reqs[r].n, reqs[r].kind);
     uint32_t at = pos[t];
-    for (int64_t k = 0; k < v; k++) leaves[at++] = p;
+    const uint32_t end = pos[t + 1];
+    if (at == end) return;
+    const uint32_t p = primes[t - pre[r]];
+    for (; at < end; at++) leaves[at] = p;
 }
 
 // leaf segment start of every request (flat index pre[r] -> its position)
@@ -104,8 +133,8 @@ __global__ void batch_leaf_nodes(const uint32_t *leaves, const uint64_t *seg,
 {
     const uint64_t total = node_pre[count];
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = block_segment(node_pre, count, t);
     if (t >= total) return;
-    const int r = find_segment(node_pre, count, t);
     const uint64_t first = seg[r] + (t - node_pre[r]) * (uint64_t)lpn, end = seg[r + 1];
     uint32_t acc[kBatchLeafSlot];
 #pragma unroll
@@ -443,8 +472,8 @@ static void batch_core(Ctx &c, const cat_request *reqs, size_t count, uint32_t *
     if (hneg) fail(CAT_ENOTINTEGRAL, "a prime exponent is negative");
     DevBuf<uint32_t> leaves(c, total_leaves ? total_leaves : 1, s);
     tok = prof_begin(c, "batch_leaves", s);
-    if (F) batch_leaves<<<fb, 256, 0, s>>>(primes.get(), d_pre.get(), nr, d_req.get(),
-                                           pos.get(), leaves.get());
+    if (F) batch_leaves<<<fb, 256, 0, s>>>(primes.get(), d_pre.get(), nr, pos.get(),
+                                           leaves.get());
     CAT_LAUNCH("batch_leaves");
     prof_end(c, tok, s, 8.0 * (double)F + 4.0 * total_leaves);
     DevBuf<uint64_t> d_seg(c, count + 1, s);
