@@ -168,6 +168,8 @@ int cat_factor_copy_primes(cat_ctx *ctx, const cat_factorization *f, uint32_t *d
 /* ------------------------------------------------------------------ Phase 2
  * out = a * b.  a has na limbs, b has nb limbs (device).  out has room for
  * cap limbs; na + nb limbs always suffice.  *out_len = normalised length.
+ * out may overlap a or b (the product is then formed in library scratch and
+ * copied); a disjoint out of at least na + nb limbs receives it directly.
  * Errors: CAT_EINVAL, CAT_ERANGE (cap < normalised length), CAT_ENOMEM,
  * CAT_ECUDA.  Products of up to 2^27 limbs take one three-prime transform;
  * longer ones are summed from products of pieces of at most 2^26 limbs (any

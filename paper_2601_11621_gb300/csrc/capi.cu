@@ -206,11 +206,22 @@ int bigint_mul(cat_ctx *ctx, const uint32_t *a, size_t na, const uint32_t *b, si
     if (!ctx || !out_len || (na && !a) || (nb && !b) || (cap && !out)) return CAT_EINVAL;
     return guarded(ctx, [&] {
         cudaStream_t s = as_stream(stream);
-        cat::Big r;
         const size_t n = na + nb;
+        // straight into out when it holds na + nb limbs and overlaps neither
+        // operand; otherwise through a scratch product
+        auto apart = [&](const uint32_t *x, size_t nx) {
+            const uintptr_t o = (uintptr_t)out, xs = (uintptr_t)x;
+            return o + 4 * cap <= xs || xs + 4 * nx <= o;
+        };
+        if (cap >= n && apart(a, na) && apart(b, nb)) {
+            cat::mul_into(ctx->c, a, na, b, nb, out, s);
+            *out_len = cat::trim(ctx->c, out, n, s);
+            return;
+        }
+        cat::Big r;
         r.buf = cat::DevBuf<uint32_t>(ctx->c, n ? n : 1, s);
         cat::mul_into(ctx->c, a, na, b, nb, r.buf.get(), s);
-        r.n = cat::normalized_length(ctx->c, r.buf.get(), n, s);
+        r.n = cat::trim(ctx->c, r.buf.get(), n, s);
         copy_out(ctx->c, r, out, cap, out_len, s);
     });
 }

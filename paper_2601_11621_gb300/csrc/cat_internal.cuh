@@ -377,6 +377,10 @@ struct Ctx {
     // as tuned on this device (cat_autotune); 0 = the default plan
     int row_log[kLogMaxNtt + 1] = {};
     std::string tuning;           // where the tuned values came from ("" = defaults)
+    // small read-backs (lengths of results): a pinned host word and a device
+    // word, allocated once per context
+    uint64_t *host_word = nullptr;
+    unsigned long long *dev_word = nullptr;
     bool profiling = false;
     std::vector<ProfEntry> prof;
     std::vector<ProfPending> pending;
@@ -575,6 +579,9 @@ int to_decimal_dev(Ctx &c, const uint32_t *x, size_t n, char *out, size_t cap, s
                    cudaStream_t s);
 // Normalised length of x[0..n) (reads the device array).
 size_t normalized_length(Ctx &c, const uint32_t *x, size_t n, cudaStream_t s);
+// The same, reading only the top four limbs when one of them is nonzero (the
+// usual case for a product of normalised operands).
+size_t trim(Ctx &c, const uint32_t *x, size_t n, cudaStream_t s);
 // Product of count 32-bit values (balanced tree).  Returns the result.
 // The product of values[0 .. count), times *extra when given; exact = false
 // returns a length bound (zero top limbs) without a host read-back (tree.cu).

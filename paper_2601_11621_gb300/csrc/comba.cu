@@ -263,18 +263,24 @@ bool comba_level(Ctx &c, const uint32_t *in, size_t slot, size_t nprod, uint32_t
 size_t normalized_length(Ctx &c, const uint32_t *x, size_t n, cudaStream_t s)
 {
     if (n == 0) return 0;
-    DevBuf<unsigned long long> top(c, 1, s);
-    CAT_CUDA(cudaMemsetAsync(top.get(), 0, sizeof(unsigned long long), s));
+    DevBuf<unsigned long long> scratch;
+    unsigned long long *top = c.dev_word;
+    if (!top) {
+        scratch = DevBuf<unsigned long long>(c, 1, s);
+        top = scratch.get();
+    }
+    CAT_CUDA(cudaMemsetAsync(top, 0, sizeof(unsigned long long), s));
     const size_t threads = 256;
     size_t blocks = (n + threads - 1) / threads;
     const size_t cap = (size_t)c.num_sms * 8;
     if (blocks > cap) blocks = cap;
-    find_top<<<(unsigned)blocks, threads, 0, s>>>(x, n, top.get());
+    find_top<<<(unsigned)blocks, threads, 0, s>>>(x, n, top);
     CAT_LAUNCH("find_top");
-    unsigned long long h = 0;
-    CAT_CUDA(cudaMemcpyAsync(&h, top.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+    unsigned long long local = 0;
+    unsigned long long *h = c.host_word ? reinterpret_cast<unsigned long long *>(c.host_word) : &local;
+    CAT_CUDA(cudaMemcpyAsync(h, top, sizeof(*h), cudaMemcpyDeviceToHost, s));
     CAT_CUDA(cudaStreamSynchronize(s));
-    return (size_t)h;
+    return (size_t)*h;
 }
 
 }  // namespace cat

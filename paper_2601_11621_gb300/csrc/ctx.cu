@@ -254,14 +254,24 @@ void ctx_init(Ctx &c, int device, size_t budget)
     }
     pool_for(device);
     build_twiddles(c);
+    CAT_CUDA(cudaMallocHost(&c.host_word, 4 * sizeof(uint64_t)));
+    CAT_CUDA(cudaMalloc(&c.dev_word, sizeof(unsigned long long)));
 }
 
 void ctx_release(Ctx &c)
 {
+    cudaSetDevice(c.device);
     if (c.twiddles) {
-        cudaSetDevice(c.device);
         cudaFree(c.twiddles);
         c.twiddles = nullptr;
+    }
+    if (c.dev_word) {
+        cudaFree(c.dev_word);
+        c.dev_word = nullptr;
+    }
+    if (c.host_word) {
+        cudaFreeHost(c.host_word);
+        c.host_word = nullptr;
     }
 }
 

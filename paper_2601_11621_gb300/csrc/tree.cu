@@ -41,11 +41,12 @@ static Big make_one(Ctx &c, cudaStream_t s)
 
 // Length of x[0..n) after dropping zero top limbs, reading only the top few
 // limbs when they decide it.
-static size_t trim(Ctx &c, const uint32_t *x, size_t n, cudaStream_t s)
+size_t trim(Ctx &c, const uint32_t *x, size_t n, cudaStream_t s)
 {
     if (n == 0) return 0;
     const size_t k = std::min<size_t>(n, 4);
-    uint32_t h[4];
+    uint32_t local[4];
+    uint32_t *h = c.host_word ? reinterpret_cast<uint32_t *>(c.host_word) : local;
     CAT_CUDA(cudaMemcpyAsync(h, x + n - k, 4 * k, cudaMemcpyDeviceToHost, s));
     CAT_CUDA(cudaStreamSynchronize(s));
     for (size_t i = k; i-- > 0;)

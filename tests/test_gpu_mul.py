@@ -74,6 +74,33 @@ def test_mul_edge_cases(ctx, cat_lib):
     assert got.tolist() == [15]
 
 
+@pytest.mark.parametrize("na,nb", [(3000, 2000), (40000, 30000)])
+def test_mul_output_overlapping_an_operand(ctx, cat_lib, orc, na, nb):
+    """The C ABI's out may overlap an operand (here out starts at a): the
+    product then goes through scratch; a disjoint out takes it directly."""
+    import ctypes
+    import torch
+    a = W.random_limbs32(na, seed=na + 11)
+    b = W.random_limbs32(nb, seed=nb + 12)
+    want = orc.mul(a, b)
+    buf = torch.zeros(na + nb, dtype=torch.int32, device="cuda")
+    buf[:na] = torch.from_numpy(a.view(np.int32)).cuda()
+    tb = torch.from_numpy(b.view(np.int32)).cuda()
+    n = ctypes.c_size_t()
+    rc = cat_lib.load().bigint_mul(ctx.handle, cat_lib._ptr(buf), na, cat_lib._ptr(tb), nb,
+                                   cat_lib._ptr(buf), na + nb, ctypes.byref(n),
+                                   cat_lib._stream(None))
+    assert rc == 0
+    assert n.value == want.size and (host(buf[:n.value]) == want).all()
+    out = torch.zeros(na + nb, dtype=torch.int32, device="cuda")
+    ta = torch.from_numpy(a.view(np.int32)).cuda()
+    rc = cat_lib.load().bigint_mul(ctx.handle, cat_lib._ptr(tb), nb, cat_lib._ptr(ta), na,
+                                   cat_lib._ptr(out), na + nb, ctypes.byref(n),
+                                   cat_lib._stream(None))
+    assert rc == 0
+    assert n.value == want.size and (host(out[:n.value]) == want).all()
+
+
 @pytest.mark.parametrize("n", [1, 5, 2048, 2049, 70000, 1 << 20])
 def test_square(ctx, cat_lib, n):
     import torch
