@@ -107,9 +107,13 @@ __global__ void __launch_bounds__(kSieveThreads) sieve_segments(SieveArgs a)
     __shared__ uint32_t red[kSieveThreads / 32], red_all[kSieveThreads / 32];
     const uint32_t seg = blockIdx.x;
     const uint32_t ibase = seg * (uint32_t)kSegBits;  // odd index of bit 0
+    // words of this segment at or below the last odd index (the last segment,
+    // or the only one of a small limit, is sieved only that far)
+    const uint32_t used = (uint32_t)std::min<uint64_t>(kSegWords, (a.imax - ibase) / 32 + 1);
+    const uint64_t used_bits = 32ull * used;
     // primes 3..31: bit b of word w is odd number x = 2(ibase + 32 w + b) + 1;
     // p | x  <=>  ibase + 32 w + b = (p - 1)/2 (mod p)
-    for (int w = threadIdx.x; w < kSegWords; w += blockDim.x) {
+    for (int w = threadIdx.x; w < (int)used; w += blockDim.x) {
         const uint32_t i0 = ibase + 32u * w;
         uint32_t m = 0;
 #pragma unroll
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(kSieveThreads) sieve_segments(SieveArgs a)
         if (x0 < p * p) x0 = p * p;
         if (!(x0 & 1)) x0 += p;
         const uint64_t first = (x0 - 1) / 2 - ibase;
-        for (uint64_t i = first + (uint64_t)lane * p; i < (uint64_t)kSegBits; i += 32 * p)
+        for (uint64_t i = first + (uint64_t)lane * p; i < used_bits; i += 32 * p)
             atomicOr(&bm[i >> 5], 1u << (i & 31));
     }
     // large primes: one thread per prime
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(kSieveThreads) sieve_segments(SieveArgs a)
         uint64_t x0 = (lo_num + p - 1) / p * p;
         if (x0 < p * p) x0 = p * p;
         if (!(x0 & 1)) x0 += p;
-        for (uint64_t i = (x0 - 1) / 2 - ibase; i < (uint64_t)kSegBits; i += p)
+        for (uint64_t i = (x0 - 1) / 2 - ibase; i < used_bits; i += p)
             atomicOr(&bm[i >> 5], 1u << (i & 31));
     }
     __syncthreads();
@@ -158,8 +162,8 @@ __global__ void __launch_bounds__(kSieveThreads) sieve_segments(SieveArgs a)
     uint32_t cnt = 0, all = 0;
     uint32_t *out = a.bits + (size_t)seg * kSegWords;
     for (int w = threadIdx.x; w < kSegWords; w += blockDim.x) {
-        uint32_t v = ~bm[w];
         const uint64_t i0 = (uint64_t)ibase + 32u * w;
+        uint32_t v = w < (int)used ? ~bm[w] : 0u;
         if (i0 > a.imax) v = 0;
         else if (i0 + 31 > a.imax) v &= (uint32_t)((2ull << (a.imax - i0)) - 1);
         if (a.unit_kind >= 0) {
