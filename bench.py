@@ -27,9 +27,10 @@ Prints one JSON line (rank 0):
   batched      4,096 seeded requests (C(n) / C(2n, n), n log-uniform in
                [10^3, 10^6]) in one cat_exact_batch call against one-at-a-time
                cat_exact calls, results compared;
-  served       a seeded Poisson stream through the serving engine against the
-               same stream one request at a time: p50/p99 latency, req/s,
-               results compared;
+  served       a seeded Poisson stream (300 req/s offered) through the serving
+               engine against the same stream one request at a time: p50/p99
+               latency, req/s, results compared; served_rates the same at 10,
+               30, 100 and 1000 req/s;
   decimal      to_decimal of the C(n) just computed (its 1,234,567,890 digits at
                the paper's n).
 """
@@ -435,6 +436,11 @@ def decimal(ctx, capi, limbs, n):
             "checked": "digit count (Table 1)" if n == PAPER_N else "none"}
 
 
+# the other offered rates of the serving sweep (req/s, requests per stream),
+# each stream a few seconds long at most
+SERVED_RATES = ((10.0, 20), (30.0, 40), (100.0, 96), (1000.0, 192))
+
+
 def served(ctx, capi, W, device, rate=300.0, count=96):
     from paper_2601_11621_gb300 import server
     stream = W.served_requests(count, rate, seed=1)
@@ -597,6 +603,10 @@ def main():
         extras["mul_sweep"] = mul_sweep(ctx, capi, W, dev)
         extras["batched"] = batched(ctx, capi, W)
         extras["served"] = served(ctx, capi, W, local_rank)
+        extras["served_rates"] = [
+            {k: v for k, v in served(ctx, capi, W, local_rank, rate, count).items()
+             if k not in ("checked", "mix")}
+            for rate, count in SERVED_RATES]
         extras["decimal"] = decimal(ctx, capi, out[:nlimbs], n)
 
     cpu = None
