@@ -3,15 +3,22 @@
 // of C(2,050,572,903), 1,234,567,890).
 //
 // Method (no division of long numbers).  The little-endian 2^32-limbs are cut
-// into leaves of 64 limbs, each converted to base 10^9 ("chunks" of nine
+// into leaves of 59 limbs, each converted to base 10^9 ("chunks" of nine
 // digits) by Horner's rule in one thread.  Then, level by level, adjacent
 // nodes (lo, hi) of w limbs each are joined into lo + hi 2^(32 w), computed in
 // base 10^9: one batched product of all hi nodes with the common power
 // P_j = 2^(32 w) written in base 10^9 (transformed once), whose remaindering
 // splits every exact coefficient into base-10^9 digits, adds the lo node and
-// carries in base 10^9.  P_{j+1} = P_j^2 by the same product.  The top node
-// is the whole number in base 10^9; a last pass prints nine digits per chunk
-// (the top chunk without leading zeros).
+// carries in base 10^9.  P_{j+1} = P_j^2 by the same product.  An odd last
+// node of a level (no hi) moves up unchanged.  The top node is the whole
+// number in base 10^9; a last pass prints nine digits per chunk (the top
+// chunk without leading zeros).
+//
+// Leaf size.  A w-limb value has at most 1.0704 w chunks, so 59-limb leaves
+// fill 64 chunks (2^1888 < 10^569) and a level-j node at most 64 2^j: the
+// product hi P_j then has at most 2^(7 + j) coefficients, exactly one
+// transform size.  (64-limb leaves would need 69 chunks, and every product a
+// transform twice its length.)
 //
 // Exactness: a level's product coefficients are below min(len) (10^9)^2 <
 // 2^26 10^18 < 10^26, inside the three-prime range, and each node sum lo +
@@ -27,8 +34,8 @@
 
 namespace cat {
 
-constexpr int kDecLeafLimbs = 64;
-constexpr int kDecLeafChunks = 69;  // 2^2048 < 10^617: 69 chunks of nine digits
+constexpr int kDecLeafLimbs = 59;
+constexpr int kDecLeafChunks = 64;  // 2^1888 < 10^569: 64 chunks of nine digits
 
 // chunks of nine digits that hold any value below 2^bits (a little spare)
 static size_t chunks_for_bits(double bits)
@@ -36,7 +43,7 @@ static size_t chunks_for_bits(double bits)
     return (size_t)ceil((bits * log10(2.0) + 2.0) / 9.0);
 }
 
-// Leaf i: limbs [64 i, 64 i + 64) of x (zero past n) in base 10^9, by
+// Leaf i: limbs [59 i, 59 i + 59) of x (zero past n) in base 10^9, by
 // acc <- acc 2^32 + limb from the top limb down.  After m limbs acc < 2^(32 m)
 // has at most ceil(32 m log10(2) / 9) + 1 chunks, so step m touches only those.
 __global__ void __launch_bounds__(128) dec_leaves(const uint32_t *x, size_t n, size_t leaves,
@@ -90,7 +97,7 @@ size_t decimal_bound(size_t n)
     return (size_t)floor((double)n * 32.0 * log10(2.0)) + 2;
 }
 
-// P_0 = 2^(32 * 64) in base 10^9, on the host.
+// P_0 = 2^(32 * 59) in base 10^9, on the host.
 static std::vector<uint32_t> leaf_power()
 {
     std::vector<uint32_t> p(1, 1u);
@@ -119,19 +126,18 @@ int to_decimal_dev(Ctx &c, const uint32_t *x, size_t n, char *out, size_t cap, s
         CAT_CUDA(cudaStreamSynchronize(s));
         return CAT_OK;
     }
-    const size_t leaves_used = (n + kDecLeafLimbs - 1) / kDecLeafLimbs;
+    const size_t leaves = (n + kDecLeafLimbs - 1) / kDecLeafLimbs;
     int h = 0;
-    while (((size_t)1 << h) < leaves_used) h++;
-    const size_t leaves = (size_t)1 << h;
+    while (((size_t)1 << h) < leaves) h++;
 
-    // level 0: leaves of 64 limbs in 69 chunks
-    size_t S = kDecLeafChunks;
-    DevBuf<uint32_t> cur(c, leaves * S, s);
+    // level 0: leaves of 59 limbs in 64 chunks
+    size_t S = kDecLeafChunks, nodes = leaves;
+    DevBuf<uint32_t> cur(c, nodes * S, s);
     {
         const int tok = prof_begin(c, "dec_leaves", s);
-        dec_leaves<<<(unsigned)((leaves + 127) / 128), 128, 0, s>>>(x, n, leaves, cur.get());
+        dec_leaves<<<(unsigned)((nodes + 127) / 128), 128, 0, s>>>(x, n, nodes, cur.get());
         CAT_LAUNCH("dec_leaves");
-        prof_end(c, tok, s, 4.0 * (double)n + 4.0 * (double)(leaves * S));
+        prof_end(c, tok, s, 4.0 * (double)n + 4.0 * (double)(nodes * S));
     }
     const std::vector<uint32_t> p0 = leaf_power();
     size_t plen = p0.size();
@@ -139,24 +145,33 @@ int to_decimal_dev(Ctx &c, const uint32_t *x, size_t n, char *out, size_t cap, s
     CAT_CUDA(cudaMemcpyAsync(P.get(), p0.data(), 4 * plen, cudaMemcpyHostToDevice, s));
 
     for (int j = 0; j < h; j++) {
-        const size_t nprod = leaves >> (j + 1);
-        // node width 64 * 2^j limbs -> the joined node holds 2^(32 * 64 * 2^(j+1))
+        const size_t nprod = nodes / 2, odd = nodes & 1, nn = nprod + odd;
+        // node width 59 * 2^j limbs -> the joined node holds 2^(32 * 59 * 2^(j+1))
         const size_t S1 = chunks_for_bits(32.0 * kDecLeafLimbs * (double)((size_t)2 << j));
-        DevBuf<uint32_t> nxt(c, nprod * S1, s);
-        if (S + plen <= ((size_t)1 << c.max_log)) {
+        DevBuf<uint32_t> nxt(c, nn * S1, s);
+        if (nprod && S + plen <= ((size_t)1 << c.max_log)) {
             mul_broadcast(c, cur.get() + S, 2 * S, S, nprod, P.get(), plen,
                           Sink{nxt.get(), S1, S1, true, cur.get(), 2 * S, S}, s);
         } else {
             for (size_t k = 0; k < nprod; k++) {
                 uint32_t *acc = nxt.get() + k * S1;
+                const uint32_t *hi = cur.get() + (2 * k + 1) * S;
                 CAT_CUDA(cudaMemcpyAsync(acc, cur.get() + 2 * k * S, 4 * S,
                                          cudaMemcpyDeviceToDevice, s));
                 CAT_CUDA(cudaMemsetAsync(acc + S, 0, 4 * (S1 - S), s));
-                mul_acc(c, cur.get() + (2 * k + 1) * S, S, P.get(), plen, acc, S1, true, s);
+                // the top node's hi part may be much shorter than its slot
+                mul_acc(c, hi, normalized_length(c, hi, S, s), P.get(), plen, acc, S1, true, s);
             }
+        }
+        if (odd) {  // no hi: the last node moves up
+            uint32_t *dst = nxt.get() + nprod * S1;
+            CAT_CUDA(cudaMemcpyAsync(dst, cur.get() + 2 * nprod * S, 4 * S,
+                                     cudaMemcpyDeviceToDevice, s));
+            CAT_CUDA(cudaMemsetAsync(dst + S, 0, 4 * (S1 - S), s));
         }
         cur = std::move(nxt);
         S = S1;
+        nodes = nn;
         if (j + 1 < h) {  // P_{j+1} = P_j^2
             DevBuf<uint32_t> P2(c, 2 * plen, s);
             if (2 * plen <= ((size_t)1 << c.max_log)) {

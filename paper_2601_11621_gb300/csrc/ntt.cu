@@ -1102,18 +1102,28 @@ void add_into(Ctx &c, uint32_t *acc, size_t R, const uint32_t *t, size_t tn, boo
     prof_end(c, tok, s, 8.0 * (double)R + 4.0 * (double)tn);
 }
 
-// acc[0 .. R) += x y for operands of any length: pieces of at most 2^26
-// limbs (2^(max_log - 1)), so that every piece product fits one transform of
-// at most 2^27 points, each added in at its offset (the sum must fit R limbs).
+// acc[0 .. R) += x y for operands of any length: pieces of Mx and My limbs
+// with Mx + My <= 2^max_log, so that every piece product fits one transform,
+// each added in at its offset (the sum must fit R limbs).  Both pieces are
+// 2^(max_log - 1) limbs, or an operand shorter than that is one piece and the
+// other takes the rest of the transform.
 void mul_acc(Ctx &c, const uint32_t *x, size_t xlen, const uint32_t *y, size_t ylen,
              uint32_t *acc, size_t R, bool dec, cudaStream_t s)
 {
     if (xlen == 0 || ylen == 0) return;
-    const size_t M = (size_t)1 << (c.max_log - 1);
-    for (size_t i = 0; i < xlen; i += M)
-        for (size_t j = 0; j < ylen; j += M) {
+    const size_t L = (size_t)1 << c.max_log, M = L / 2;
+    size_t Mx = M, My = M;
+    if (xlen < M) {
+        Mx = xlen;
+        My = L - xlen;
+    } else if (ylen < M) {
+        My = ylen;
+        Mx = L - ylen;
+    }
+    for (size_t i = 0; i < xlen; i += Mx)
+        for (size_t j = 0; j < ylen; j += My) {
             if (i + j >= R) continue;
-            const size_t lx = std::min(M, xlen - i), ly = std::min(M, ylen - j);
+            const size_t lx = std::min(Mx, xlen - i), ly = std::min(My, ylen - j);
             DevBuf<uint32_t> t(c, lx + ly, s);
             mul_broadcast(c, x + i, 0, lx, 1, y + j, ly,
                           Sink{t.get(), 0, lx + ly, dec, nullptr, 0, 0}, s);
