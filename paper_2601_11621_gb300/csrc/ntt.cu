@@ -1052,6 +1052,13 @@ void mul_broadcast(Ctx &c, const uint32_t *x, size_t xstride, size_t xlen, size_
     const int n = std::max(1, ceil_log2(xlen + ylen));
     if (n > kLogMaxNtt) fail(CAT_EINVAL, "operands too long for one transform");
     Operand ox{x, xstride, xlen}, oy{y, 0, ylen};
+    if (nprod == 1 && x == y && xlen == ylen) {  // a square: one forward transform
+        if (n <= kFusedMaxLog)
+            ntt_mul_small(c, n, 1, ox, ox, true, sink, s);
+        else
+            ntt_mul_multipass(c, n, PAIR_SQUARE, 1, ox, ox, sink, s);
+        return;
+    }
     if (n <= kFusedMaxLog)
         ntt_mul_small(c, n, nprod, ox, oy, false, sink, s);
     else
