@@ -781,9 +781,13 @@ static void col_pass(Ctx &c, int ps, bool fwd, uint32_t *data, size_t pstride, s
 }
 
 template <int LR, int PS>
-static void launch_row_t(dim3 grid, cudaStream_t s, const RowArgs &a)
+static void launch_row_t(dim3 grid, cudaStream_t s, const RowArgs &a, bool pre)
 {
-    if (a.mode == PAIR_SQUARE) {
+    if (pre) {  // broadcast products, the common transform complete
+        const size_t smem = ((size_t)1 << kRowMaxLog) * sizeof(uint32_t);
+        set_smem(ntt_row_mul_bcast<LR, PS>, smem);
+        ntt_row_mul_bcast<LR, PS><<<grid, kRowThreads, smem, s>>>(a);
+    } else if (a.mode == PAIR_SQUARE) {
         const size_t smem = ((size_t)1 << kRowMaxLog) * sizeof(uint32_t);
         set_smem(ntt_row_mul<LR, true, PS>, smem);
         ntt_row_mul<LR, true, PS><<<grid, kRowThreads, smem, s>>>(a);
@@ -794,36 +798,69 @@ static void launch_row_t(dim3 grid, cudaStream_t s, const RowArgs &a)
     }
 }
 
-// The fused row pass of nprod products of 2^n points with prime set ps.
-static void launch_row(int ps, int lr, size_t nprod, int n, cudaStream_t s, const RowArgs &a)
+// The fused row pass of nprod products of 2^n points with prime set ps
+// (pre: broadcast products whose common transform ntt_row_fwd completed).
+static void launch_row(int ps, int lr, size_t nprod, int n, cudaStream_t s, const RowArgs &a,
+                       bool pre = false)
 {
     dim3 grid((unsigned)(nprod << (n - kRowMaxLog)), kNumPrimes);
     if (ps == 0) {
         switch (lr) {
-        case 9: launch_row_t<9, 0>(grid, s, a); break;
-        case 10: launch_row_t<10, 0>(grid, s, a); break;
-        case 11: launch_row_t<11, 0>(grid, s, a); break;
-        case 12: launch_row_t<12, 0>(grid, s, a); break;
+        case 9: launch_row_t<9, 0>(grid, s, a, pre); break;
+        case 10: launch_row_t<10, 0>(grid, s, a, pre); break;
+        case 11: launch_row_t<11, 0>(grid, s, a, pre); break;
+        case 12: launch_row_t<12, 0>(grid, s, a, pre); break;
         default: fail(CAT_EINVAL, "row pass size out of range");
         }
     } else if (ps == 1) {
         switch (lr) {
-        case 9: launch_row_t<9, 1>(grid, s, a); break;
-        case 10: launch_row_t<10, 1>(grid, s, a); break;
-        case 11: launch_row_t<11, 1>(grid, s, a); break;
-        case 12: launch_row_t<12, 1>(grid, s, a); break;
+        case 9: launch_row_t<9, 1>(grid, s, a, pre); break;
+        case 10: launch_row_t<10, 1>(grid, s, a, pre); break;
+        case 11: launch_row_t<11, 1>(grid, s, a, pre); break;
+        case 12: launch_row_t<12, 1>(grid, s, a, pre); break;
         default: fail(CAT_EINVAL, "row pass size out of range");
         }
     } else {
         switch (lr) {
-        case 9: launch_row_t<9, 2>(grid, s, a); break;
-        case 10: launch_row_t<10, 2>(grid, s, a); break;
-        case 11: launch_row_t<11, 2>(grid, s, a); break;
-        case 12: launch_row_t<12, 2>(grid, s, a); break;
+        case 9: launch_row_t<9, 2>(grid, s, a, pre); break;
+        case 10: launch_row_t<10, 2>(grid, s, a, pre); break;
+        case 11: launch_row_t<11, 2>(grid, s, a, pre); break;
+        case 12: launch_row_t<12, 2>(grid, s, a, pre); break;
         default: fail(CAT_EINVAL, "row pass size out of range");
         }
     }
     CAT_LAUNCH("ntt_row_mul");
+}
+
+template <int LR, int PS>
+static void launch_row_fwd_t(dim3 grid, cudaStream_t s, const RowArgs &a)
+{
+    const size_t smem = ((size_t)1 << kRowMaxLog) * sizeof(uint32_t);
+    set_smem(ntt_row_fwd<LR, PS>, smem);
+    ntt_row_fwd<LR, PS><<<grid, kRowThreads, smem, s>>>(a);
+}
+
+// The row pass's forward rounds of one transform of 2^n points in place (the
+// common operand of broadcast products; a.F at its slot).
+static void launch_row_fwd(int ps, int lr, int n, cudaStream_t s, const RowArgs &a)
+{
+    dim3 grid((unsigned)((size_t)1 << (n - kRowMaxLog)), kNumPrimes);
+    switch (ps * 16 + lr) {
+    case 9: launch_row_fwd_t<9, 0>(grid, s, a); break;
+    case 10: launch_row_fwd_t<10, 0>(grid, s, a); break;
+    case 11: launch_row_fwd_t<11, 0>(grid, s, a); break;
+    case 12: launch_row_fwd_t<12, 0>(grid, s, a); break;
+    case 16 + 9: launch_row_fwd_t<9, 1>(grid, s, a); break;
+    case 16 + 10: launch_row_fwd_t<10, 1>(grid, s, a); break;
+    case 16 + 11: launch_row_fwd_t<11, 1>(grid, s, a); break;
+    case 16 + 12: launch_row_fwd_t<12, 1>(grid, s, a); break;
+    case 32 + 9: launch_row_fwd_t<9, 2>(grid, s, a); break;
+    case 32 + 10: launch_row_fwd_t<10, 2>(grid, s, a); break;
+    case 32 + 11: launch_row_fwd_t<11, 2>(grid, s, a); break;
+    case 32 + 12: launch_row_fwd_t<12, 2>(grid, s, a); break;
+    default: fail(CAT_EINVAL, "row pass size out of range");
+    }
+    CAT_LAUNCH("ntt_row_fwd");
 }
 
 // Remaindering of a batch, specialised by prime set and by the sink's mode
@@ -905,8 +942,19 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     ra.mode = mode;
     ra.tw = c.twiddles;
     ra.scale = make_scale(PS, n);
-    int tok = prof_begin(c, "ntt_row_mul", s);
-    launch_row(PS, P.rrow, nprod, n, s, ra);
+    // broadcast products: y's transform completed once, in its slot, so that
+    // the row pass transforms only the x's
+    const bool pre = mode == PAIR_BROADCAST && nprod >= 2;
+    int tok;
+    if (pre) {
+        RowArgs ya = ra;
+        ya.F = F.get() + nprod * L;
+        tok = prof_begin(c, "ntt_row_fwd", s);
+        launch_row_fwd(PS, P.rrow, n, s, ya);
+        prof_end(c, tok, s, 8.0 * (double)L * kNumPrimes);
+    }
+    tok = prof_begin(c, "ntt_row_mul", s);
+    launch_row(PS, P.rrow, nprod, n, s, ra, pre);
     // the products' own bytes: operands read and products written once
     const double unit = 4.0 * (double)nprod * (double)(x.len + sink.out_len) +
                         (mode == PAIR_SQUARE ? 0.0

@@ -697,13 +697,15 @@ struct RowOut {
 // Last forward pass of both operands (or one, squaring), pointwise product
 // and first inverse pass, on 2^(12-LR) consecutive rows of 2^LR points of
 // product k.  The last forward round, the product and the first inverse round
-// share one register round (their stage bits coincide).
-template <int LR, bool SQ, int PS>
-__global__ void __launch_bounds__(kRowThreads, CAT_ROW_MINB) ntt_row_mul(RowArgs a)
+// share one register round (their stage bits coincide).  YH (broadcast
+// products): the common operand's transform is already complete in its slot
+// (ntt_row_fwd), in the order the product loop reads it, so only x is
+// transformed here.
+template <int LR, bool SQ, int PS, bool YH>
+__device__ __forceinline__ void row_mul_body(const RowArgs &a, uint32_t *sm)
 {
-    extern __shared__ uint32_t sm[];
     constexpr int NR = rounds_of(LR);
-    constexpr int NA = SQ ? 1 : 2;
+    constexpr int NA = (SQ || YH) ? 1 : 2;
     constexpr int EL = round_size(LR, NR - 1);
     constexpr int RB = row_log_rows(LR), C = 1 << RB;
     static_assert(EL == dit_size(LR, 0), "mirrored rounds");
@@ -757,10 +759,20 @@ __global__ void __launch_bounds__(kRowThreads, CAT_ROW_MINB) ntt_row_mul(RowArgs
         uint32_t x[NA][1 << EL];
         sio.template load<EL, 0, NA>(x, base, c);
         dif_stages<EL, 0, NA, PS>(x, 0, T, q);
+        uint32_t yv[1 << EL];
+        if constexpr (YH) {
+            static_assert(EL >= 2, "the common transform is read 16 bytes at a time");
+            const uint4 *y4 = reinterpret_cast<const uint4 *>(fb + (c << LR) + base);
+#pragma unroll
+            for (int j = 0; j < (1 << EL) / 4; j++) {
+                const uint4 v = y4[j];
+                yv[4 * j] = v.x; yv[4 * j + 1] = v.y; yv[4 * j + 2] = v.z; yv[4 * j + 3] = v.w;
+            }
+        }
         uint32_t z[1][1 << EL];
 #pragma unroll
         for (int j = 0; j < (1 << EL); j++)
-            z[0][j] = pmul<PS>(x[0][j], x[NA - 1][j], sc, q, qinv);
+            z[0][j] = pmul<PS>(x[0][j], YH ? yv[j] : x[NA - 1][j], sc, q, qinv);
         dit_stages<EL, 0, 1, PS>(z, 0, Ti, q);
         sio.template store<EL, 0, 1>(z, base, c);
     }
@@ -792,5 +804,76 @@ __global__ void __launch_bounds__(kRowThreads, CAT_ROW_MINB) ntt_row_mul(RowArgs
         __syncthreads();
         round_io<LR, C, dit_base(LR, 2), dit_size(LR, 2), false, 1, false, PS>(sio, RowOut<LR>{g},
                                                                                Ti, q);
+    }
+}
+
+template <int LR, bool SQ, int PS>
+__global__ void __launch_bounds__(kRowThreads, CAT_ROW_MINB) ntt_row_mul(RowArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    row_mul_body<LR, SQ, PS, false>(a, sm);
+}
+
+// Broadcast products x_k y whose y transform ntt_row_fwd has completed.
+template <int LR, int PS>
+__global__ void __launch_bounds__(kRowThreads, CAT_ROW_MINB) ntt_row_mul_bcast(RowArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    row_mul_body<LR, false, PS, true>(a, sm);
+}
+
+// The row pass's forward rounds alone, for the common operand y of broadcast
+// products: a.F points at y's slot, 2^(12-LR) consecutive rows of 2^LR points
+// per block; the last forward round's output goes back to the same rows,
+// point base + j of row c at (c << LR) + base + j (the order in which the
+// product loop of ntt_row_mul_bcast reads it).  Each block reads its rows
+// into shared memory before it writes any of them.
+template <int LR, int PS>
+__global__ void __launch_bounds__(kRowThreads, CAT_ROW_MINB) ntt_row_fwd(RowArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    constexpr int NR = rounds_of(LR);
+    constexpr int EL = round_size(LR, NR - 1);
+    constexpr int RB = row_log_rows(LR), C = 1 << RB;
+    static_assert(EL >= 2, "rows are written 16 bytes at a time");
+    const int p = blockIdx.y;
+    const uint32_t q = c_q[PS][p];
+    const size_t off = (size_t)blockIdx.x << (LR + RB);
+    uint32_t *fy = const_cast<uint32_t *>(a.F) + p * a.fpstride + off;
+    const TwRef T{tw_table(a.tw, PS, p, 0), p};
+    const SmemIO<LR, C, false> sio{sm};
+    constexpr int CF = C / 2 > 0 ? C / 2 : 1;
+    constexpr bool kPairFwd =
+        CAT_ROW_PAIR_FWD && C >= 2 && CF * ((1 << LR) >> round_size(LR, 0)) >= kRowThreads &&
+        (NR == 2 || CF * ((1 << LR) >> round_size(LR, 1)) >= kRowThreads);
+    if constexpr (kPairFwd) {
+        const SmemIO<LR, CF, false> sp{sm};
+        round_io<LR, CF, dif_base(LR, 0), round_size(LR, 0), true, 2, false, PS>(
+            RowInPair<LR, CF>{fy, fy}, sp, T, q);
+        __syncthreads();
+        if constexpr (NR == 3) {
+            round_io<LR, CF, dif_base(LR, 1), round_size(LR, 1), true, 2, false, PS>(sp, sp, T, q);
+            __syncthreads();
+        }
+    } else {
+        round_io<LR, C, dif_base(LR, 0), round_size(LR, 0), true, 1, false, PS>(
+            RowIn<LR>{fy, fy}, sio, T, q);
+        __syncthreads();
+        if constexpr (NR == 3) {
+            round_io<LR, C, dif_base(LR, 1), round_size(LR, 1), true, 1, false, PS>(sio, sio, T, q);
+            __syncthreads();
+        }
+    }
+    constexpr int NGC = (1 << LR) >> EL;
+    for (int g = threadIdx.x; g < C * NGC; g += blockDim.x) {
+        const int c = g / NGC;
+        const int base = (g & (NGC - 1)) << EL;
+        uint32_t x[1][1 << EL];
+        sio.template load<EL, 0, 1>(x, base, c);
+        dif_stages<EL, 0, 1, PS>(x, 0, T, q);
+        uint4 *o4 = reinterpret_cast<uint4 *>(fy + (c << LR) + base);
+#pragma unroll
+        for (int j = 0; j < (1 << EL) / 4; j++)
+            o4[j] = make_uint4(x[0][4 * j], x[0][4 * j + 1], x[0][4 * j + 2], x[0][4 * j + 3]);
     }
 }
