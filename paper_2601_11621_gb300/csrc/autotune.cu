@@ -124,6 +124,8 @@ void autotune(Ctx &c, cudaStream_t s)
     }
     c.comba_max_slot = cross;
     c.tuning = "measured";
+    // the trials built twiddle tables for plans that are not kept
+    drop_col_twiddles(c);
 }
 
 void save_tuning(const Ctx &c, const char *path)

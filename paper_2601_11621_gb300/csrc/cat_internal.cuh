@@ -377,6 +377,17 @@ struct Ctx {
     // as tuned on this device (cat_autotune); 0 = the default plan
     int row_log[kLogMaxNtt + 1] = {};
     std::string tuning;           // where the tuned values came from ("" = defaults)
+    // twiddle tables of the column passes (built on first use, kept until the
+    // context is released; contexts with a budget compute the twiddles)
+    struct ColTwTable {
+        int ps, m, lr, dir;
+        uint32_t *p;
+    };
+    std::vector<ColTwTable> col_tw;
+    bool col_tw_tables = true;
+    // largest block (log2 points) whose passes read a table: for the first
+    // forward pass (which runs once per operand) and for the others
+    int col_tw_first_max_log = 21, col_tw_max_log = kLogMaxNtt;
     // small read-backs (lengths of results): a pinned host word and a device
     // word, allocated once per context
     uint64_t *host_word = nullptr;
@@ -618,6 +629,9 @@ void copy_to_host(Ctx &c, uint32_t *host, const uint32_t *dev, size_t n, cudaStr
 // Algorithm 2 on a factorisation; returns the result (normalised length).
 // Every prime of f is below 2^leaf_bits (32 when nothing smaller is known).
 Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s, int leaf_bits = 32);
+// Frees the context's column-pass twiddle tables.
+void drop_col_twiddles(Ctx &c);
+
 // Whether the in-core reconstruction of f would exceed the context's HBM
 // budget, and Algorithm 2 within the budget (ooc.cu): copies f's primes to
 // pinned host memory (and, with release, frees f's device arrays), multiplies

@@ -246,6 +246,10 @@ void ctx_init(Ctx &c, int device, size_t budget)
     const std::string tp = default_tuning_path();
     if (!tp.empty()) load_tuning(c, tp.c_str());
     if (const char *e = getenv("CAT_COMBA_MAX_SLOT")) c.comba_max_slot = strtoull(e, nullptr, 10);
+    // column-pass twiddles from tables (default) or computed in the passes
+    if (const char *e = getenv("CAT_COL_TWIDDLE_TABLES")) c.col_tw_tables = atoi(e) != 0;
+    if (const char *e = getenv("CAT_COL_TW_FIRST_MAX_LOG")) c.col_tw_first_max_log = atoi(e);
+    if (const char *e = getenv("CAT_COL_TW_MAX_LOG")) c.col_tw_max_log = atoi(e);
     // a lower single-transform limit sends shorter products through the piece
     // path (used to exercise it at small sizes)
     if (const char *e = getenv("CAT_MAX_TRANSFORM_LOG")) {
@@ -261,6 +265,7 @@ void ctx_init(Ctx &c, int device, size_t budget)
 void ctx_release(Ctx &c)
 {
     cudaSetDevice(c.device);
+    drop_col_twiddles(c);
     if (c.twiddles) {
         cudaFree(c.twiddles);
         c.twiddles = nullptr;

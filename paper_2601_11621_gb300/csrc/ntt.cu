@@ -717,11 +717,65 @@ static void launch_col(bool fwd, dim3 grid, cudaStream_t s, const ColArgs &a)
 }
 
 // ps: the prime set of the transform (set_for)
+// The twiddles of a column pass of 2^r rows over blocks of 2^m points (set
+// ps, direction dir): entry row 2^(m-r) + col = w^((col bitrev_r(row)) << shift)
+// in Montgomery form, the value the pass would otherwise compute for that
+// point (tw_pow_mont, exactly as the stepping reaches it).
+template <int PS>
+__global__ void col_twiddle_table(const uint2 *tw, int m, int r, int dir, uint32_t *tab)
+{
+    const int p = blockIdx.y;
+    const uint32_t q = c_q[PS][p], qinv = c_qinv[PS][p];
+    const uint2 *T = tw_table(tw, PS, p, dir);
+    const int shift = set_log_root(PS) - m;
+    const uint32_t cols = 1u << (m - r);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (1u << m);
+         i += gridDim.x * blockDim.x) {
+        const uint32_t row = i >> (m - r), col = i & (cols - 1);
+        tab[((size_t)p << m) + i] = tw_pow_mont<PS>(T, (col * bitrev(row, r)) << shift, q, qinv);
+    }
+}
+
+// A column pass's twiddle table, built on first use; null when the context
+// computes its twiddles (a budgeted context, or no room for the table).
+static const uint32_t *col_twiddles(Ctx &c, int ps, int m, int r, int dir, cudaStream_t s)
+{
+    if (!c.col_tw_tables || c.budget || c.shared_budget) return nullptr;
+    for (const Ctx::ColTwTable &t : c.col_tw)
+        if (t.ps == ps && t.m == m && t.lr == r && t.dir == dir) return t.p;
+    uint32_t *p = nullptr;
+    if (cudaMalloc(&p, ((size_t)kNumPrimes << m) * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const unsigned blocks = (unsigned)std::min<size_t>(((size_t)1 << m) / 256 + 1, 4096);
+    const dim3 grid(blocks, kNumPrimes);
+    if (ps == 0) col_twiddle_table<0><<<grid, 256, 0, s>>>(c.twiddles, m, r, dir, p);
+    else if (ps == 1) col_twiddle_table<1><<<grid, 256, 0, s>>>(c.twiddles, m, r, dir, p);
+    else col_twiddle_table<2><<<grid, 256, 0, s>>>(c.twiddles, m, r, dir, p);
+    CAT_LAUNCH("col_twiddle_table");
+    c.col_tw.push_back(Ctx::ColTwTable{ps, m, r, dir, p});
+    return p;
+}
+
+void drop_col_twiddles(Ctx &c)
+{
+    if (c.col_tw.empty()) return;
+    cudaDeviceSynchronize();  // no pass still reads them
+    for (const Ctx::ColTwTable &t : c.col_tw) cudaFree(t.p);
+    c.col_tw.clear();
+}
+
 static void col_pass(Ctx &c, int ps, bool fwd, uint32_t *data, size_t pstride, size_t total,
                      int m, int r, const uint32_t *src, size_t src_tstride, size_t src_len,
                      cudaStream_t s)
 {
     ColArgs a;
+    // a table pays where it stays in L2 or replaces work on both operands at
+    // once; the first forward pass runs once per operand and would read a
+    // large table from DRAM each time
+    const int tmax = src ? c.col_tw_first_max_log : c.col_tw_max_log;
+    a.twtab = m <= tmax ? col_twiddles(c, ps, m, r, fwd ? 0 : 1, s) : nullptr;
     a.data = data;
     a.pstride = pstride;
     a.m = m;
@@ -1347,6 +1401,7 @@ static void noalloc_mul(const NoAllocDevice &d, const uint32_t *a, size_t na, co
 {
     Ctx local;  // no device resources: only the twiddle pointer is used
     local.twiddles = d.twiddles;
+    local.col_tw_tables = false;  // the passes compute their twiddles: nothing allocated
     const size_t len = na + nb;
     const int n = std::max(1, ceil_log2(len));
     Operand x{a, 0, na}, y{b, 0, nb};

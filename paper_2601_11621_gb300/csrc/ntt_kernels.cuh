@@ -314,6 +314,10 @@ struct ColArgs {
     size_t src_tstride;    // limbs between consecutive transforms' sources
     size_t src_len;        // valid limbs per transform (rest are zero)
     const uint2 *tw;
+    // the pass's inter-pass twiddles, w^(col bitrev(row)) in the multiplier
+    // form the pass applies, point (row, col) of a 2^m block at row 2^(m-LR) +
+    // col, 2^m per prime; null: the pass computes them
+    const uint32_t *twtab;
 };
 
 // Column tiles hold V adjacent columns per thread group: the group's V
@@ -412,6 +416,9 @@ struct ColTw {
     uint32_t q, qinv;
     int shift;      // log2(root order) - m
     uint32_t u[V];  // U of this thread's columns, when its groups share them
+    // when set, the twiddles are read from this table (row stride S) instead
+    const uint32_t *tab = nullptr;
+    uint32_t S = 0;
     static constexpr int E = round_size(LR, NR - 1, NR);
     static constexpr int CV = (1 << col_log_c(LR)) / V;  // column groups per tile
     static constexpr bool kOneColumn = CV <= THREADS;
@@ -424,7 +431,7 @@ struct ColTw {
     // once per thread and column.
     __device__ __forceinline__ void init(uint32_t col0)
     {
-        if (kOneColumn) {
+        if (kOneColumn && !tab) {
             const uint32_t c0 = col0 + (threadIdx.x & (CV - 1)) * V;
 #pragma unroll
             for (int a = 0; a < V; a++) u[a] = step_of(c0 + a);
@@ -436,6 +443,16 @@ struct ColTw {
     __device__ __forceinline__ void each(uint32_t gcol, int base, F &&f) const
     {
         static_assert(EE == E, "twiddles are applied in the round at stage bits [0, E)");
+        if (tab) {  // one table word per point (V adjacent columns in one access)
+#pragma unroll
+            for (int j = 0; j < (1 << E); j++) {
+                const int k = bitrev_c(j, E);
+                uint32_t w[V];
+                load_v<V>(tab + (uint32_t)(base + k) * S + gcol, w);
+                f(k, w);
+            }
+            return;
+        }
         const uint32_t br = bitrev((uint32_t)base, LR);
         uint32_t v[V], uu[V], up[V];
 #pragma unroll
@@ -537,6 +554,10 @@ __global__ void __launch_bounds__(kColFwdThreads, CAT_COL_FWD_MINB) ntt_col_fwd(
     const ColIn<PS, V, ZT> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, (uint32_t)Sr,
                               (uint32_t)col0, (uint32_t)a.src_len, q, c_wp1[PS][p]};
     ColTw<LR, PS, NR, kColFwdThreads, V> tw{T, q, c_qinv[PS][p], set_log_root(PS) - a.m, {}};
+    if (a.twtab) {
+        tw.tab = a.twtab + ((size_t)p << a.m);
+        tw.S = (uint32_t)Sr;
+    }
     tw.init((uint32_t)col0);
     const ColOutTw<LR, PS, NR, V> out{base, (uint32_t)Sr, (uint32_t)col0, tw};
     if constexpr (NR == 1) {
@@ -578,6 +599,10 @@ __global__ void __launch_bounds__(kColInvThreads, CAT_COL_INV_MINB) ntt_col_inv(
     const uint2 *Ti = tw_table(a.tw, PS, p, 1);
     const TwRef TRi{Ti, p};
     ColTw<LR, PS, NR, kColInvThreads, V> tw{Ti, q, c_qinv[PS][p], set_log_root(PS) - a.m, {}};
+    if (a.twtab) {
+        tw.tab = a.twtab + ((size_t)p << a.m);
+        tw.S = (uint32_t)Sr;
+    }
     tw.init((uint32_t)col0);
     const ColInTw<LR, PS, NR, V> in{base, (uint32_t)Sr, (uint32_t)col0, tw};
     const ColOut<V> out{base, (uint32_t)Sr, (uint32_t)col0};
