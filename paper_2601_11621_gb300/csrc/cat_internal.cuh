@@ -386,8 +386,9 @@ struct Ctx {
     std::vector<ColTwTable> col_tw;
     bool col_tw_tables = true;
     // largest block (log2 points) whose passes read a table: for the first
-    // forward pass (which runs once per operand) and for the others
-    int col_tw_first_max_log = 21, col_tw_max_log = kLogMaxNtt;
+    // forward pass (which runs once per operand) and for the others (all by
+    // default; smaller values are for measurements)
+    int col_tw_first_max_log = kLogMaxNtt, col_tw_max_log = kLogMaxNtt;
     // small read-backs (lengths of results): a pinned host word and a device
     // word, allocated once per context
     uint64_t *host_word = nullptr;

