@@ -141,3 +141,36 @@ def test_product_tree_primes(ctx, cat_lib, orc):
     got = host(cat_lib.product_tree(ctx, pr))
     want = orc.product_tree(pr)
     assert (got == want).all()
+
+
+@pytest.fixture(scope="module")
+def computed_twiddle_ctx(cat_lib):
+    """A context whose column passes compute their inter-pass twiddles (no
+    tables), as budgeted contexts and the no-allocation multiply do."""
+    import os
+    old = os.environ.get("CAT_COL_TWIDDLE_TABLES")
+    os.environ["CAT_COL_TWIDDLE_TABLES"] = "0"
+    try:
+        c = cat_lib.Context(0)
+    finally:
+        if old is None:
+            del os.environ["CAT_COL_TWIDDLE_TABLES"]
+        else:
+            os.environ["CAT_COL_TWIDDLE_TABLES"] = old
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("na,nb", [(5000, 4000), (40000, 30000), (1 << 20, 1 << 20),
+                                   (1 << 24, 1 << 22), (3 << 23, 1 << 25), (1 << 26, 3 << 24)])
+def test_twiddle_tables_match_computed_twiddles(ctx, computed_twiddle_ctx, cat_lib, orc, na, nb):
+    """Column passes with twiddle tables (the default) and with computed
+    twiddles give the same limbs, across the prime sets (products of 2^14 to
+    2^27 points); the smaller sizes also against the oracle."""
+    a = W.random_limbs32(na, seed=na + 3)
+    b = W.random_limbs32(nb, seed=nb + 4)
+    got = host(cat_lib.bigint_mul(ctx, a, b))
+    ref = host(cat_lib.bigint_mul(computed_twiddle_ctx, a, b))
+    assert got.shape == ref.shape and (got == ref).all()
+    if na + nb <= 70000:
+        assert (got == orc.mul(a, b)).all()
