@@ -75,6 +75,11 @@ typedef struct cat_ctx cat_ctx;
  * computed more slowly.  Phase 1 itself runs in-core (about 0.5 bytes per
  * integer up to 2n plus 4 bytes per prime) and fails with CAT_ENOMEM if that
  * does not fit.  The context owns the NTT twiddle tables and the scratch pool.
+ * A context without a cap also keeps, built on first use, a table of the
+ * inter-pass twiddles of every column-pass shape it has run (2^m words per
+ * prime for blocks of 2^m points: about 6 GB after C(2,050,572,903)); it is
+ * not scratch (not counted by cat_ctx_memory) and is freed with the context.
+ * A capped context computes those twiddles instead.
  * Returns CAT_OK and *out, or an error (CAT_EINVAL, CAT_ECUDA). */
 int cat_ctx_create(int device, size_t hbm_budget_bytes, cat_ctx **out);
 
