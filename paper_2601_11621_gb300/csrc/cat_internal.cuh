@@ -381,6 +381,7 @@ struct Ctx {
     // context is released; contexts with a budget compute the twiddles)
     struct ColTwTable {
         int ps, m, lr, dir;
+        bool scaled;  // entries times 2^(32-m): operand b's first forward pass
         uint32_t *p;
     };
     std::vector<ColTwTable> col_tw;

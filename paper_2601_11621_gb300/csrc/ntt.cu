@@ -721,40 +721,57 @@ static void launch_col(bool fwd, dim3 grid, cudaStream_t s, const ColArgs &a)
 // ps, direction dir): entry row 2^(m-r) + col = w^((col bitrev_r(row)) << shift)
 // in Montgomery form, the value the pass would otherwise compute for that
 // point (tw_pow_mont, exactly as the stepping reaches it).
+// With scale (per prime, nonzero), every entry is multiplied by it mod q.
 template <int PS>
-__global__ void col_twiddle_table(const uint2 *tw, int m, int r, int dir, uint32_t *tab)
+__global__ void col_twiddle_table(const uint2 *tw, int m, int r, int dir, uint3 scale,
+                                  uint32_t *tab)
 {
     const int p = blockIdx.y;
     const uint32_t q = c_q[PS][p], qinv = c_qinv[PS][p];
+    const uint32_t sp = p == 0 ? scale.x : (p == 1 ? scale.y : scale.z);
     const uint2 *T = tw_table(tw, PS, p, dir);
     const int shift = set_log_root(PS) - m;
     const uint32_t cols = 1u << (m - r);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (1u << m);
          i += gridDim.x * blockDim.x) {
         const uint32_t row = i >> (m - r), col = i & (cols - 1);
-        tab[((size_t)p << m) + i] = tw_pow_mont<PS>(T, (col * bitrev(row, r)) << shift, q, qinv);
+        uint32_t v = tw_pow_mont<PS>(T, (col * bitrev(row, r)) << shift, q, qinv);
+        if (sp) v = (uint32_t)((uint64_t)v * sp % q);
+        tab[((size_t)p << m) + i] = v;
     }
 }
 
 // A column pass's twiddle table, built on first use; null when the context
 // computes its twiddles (a budgeted context, or no room for the table).
-static const uint32_t *col_twiddles(Ctx &c, int ps, int m, int r, int dir, cudaStream_t s)
+// scaled: the entries times 2^(32-m) mod q, for operand b of a product whose
+// pointwise step then needs no normalisation (forward first passes, m = n).
+static const uint32_t *col_twiddles(Ctx &c, int ps, int m, int r, int dir, cudaStream_t s,
+                                    bool scaled = false)
 {
     if (!c.col_tw_tables || c.budget || c.shared_budget) return nullptr;
     for (const Ctx::ColTwTable &t : c.col_tw)
-        if (t.ps == ps && t.m == m && t.lr == r && t.dir == dir) return t.p;
+        if (t.ps == ps && t.m == m && t.lr == r && t.dir == dir && t.scaled == scaled) return t.p;
     uint32_t *p = nullptr;
     if (cudaMalloc(&p, ((size_t)kNumPrimes << m) * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
+    uint3 sc = make_uint3(0, 0, 0);
+    if (scaled) {
+        uint32_t v[kNumPrimes];
+        for (int i = 0; i < kNumPrimes; i++) {
+            const uint32_t q = ntt_prime(ps, i);
+            v[i] = to_mont_c(powmod_u32((q + 1) / 2, (uint64_t)m, q), q);  // 2^32 2^-m
+        }
+        sc = make_uint3(v[0], v[1], v[2]);
+    }
     const unsigned blocks = (unsigned)std::min<size_t>(((size_t)1 << m) / 256 + 1, 4096);
     const dim3 grid(blocks, kNumPrimes);
-    if (ps == 0) col_twiddle_table<0><<<grid, 256, 0, s>>>(c.twiddles, m, r, dir, p);
-    else if (ps == 1) col_twiddle_table<1><<<grid, 256, 0, s>>>(c.twiddles, m, r, dir, p);
-    else col_twiddle_table<2><<<grid, 256, 0, s>>>(c.twiddles, m, r, dir, p);
+    if (ps == 0) col_twiddle_table<0><<<grid, 256, 0, s>>>(c.twiddles, m, r, dir, sc, p);
+    else if (ps == 1) col_twiddle_table<1><<<grid, 256, 0, s>>>(c.twiddles, m, r, dir, sc, p);
+    else col_twiddle_table<2><<<grid, 256, 0, s>>>(c.twiddles, m, r, dir, sc, p);
     CAT_LAUNCH("col_twiddle_table");
-    c.col_tw.push_back(Ctx::ColTwTable{ps, m, r, dir, p});
+    c.col_tw.push_back(Ctx::ColTwTable{ps, m, r, dir, scaled, p});
     return p;
 }
 
@@ -766,16 +783,30 @@ void drop_col_twiddles(Ctx &c)
     c.col_tw.clear();
 }
 
-static void col_pass(Ctx &c, int ps, bool fwd, uint32_t *data, size_t pstride, size_t total,
+// scaled (first forward passes): 1 = every transform of the call is an
+// operand b, 2 = the odd ones are (adjacent pairs); their twiddles then carry
+// the pointwise step's normalisation.  Returns whether they did (the scaled
+// table exists), i.e. whether the row pass must skip the normalisation.
+static bool col_pass(Ctx &c, int ps, bool fwd, uint32_t *data, size_t pstride, size_t total,
                      int m, int r, const uint32_t *src, size_t src_tstride, size_t src_len,
-                     cudaStream_t s)
+                     cudaStream_t s, int scaled = 0)
 {
     ColArgs a;
+    a.twtab_odd = nullptr;
     // (measured per C(2,050,572,903): tables in every pass beat computed
     // twiddles at every block size, the first forward passes' large tables
     // included, once the table loads go through the read-only path)
     const int tmax = src ? c.col_tw_first_max_log : c.col_tw_max_log;
     a.twtab = m <= tmax ? col_twiddles(c, ps, m, r, fwd ? 0 : 1, s) : nullptr;
+    bool prescaled = false;
+    if (scaled && a.twtab) {
+        const uint32_t *sct = col_twiddles(c, ps, m, r, 0, s, true);
+        if (sct) {
+            if (scaled == 1) a.twtab = sct;
+            else a.twtab_odd = sct;
+            prescaled = true;
+        }
+    }
     a.data = data;
     a.pstride = pstride;
     a.m = m;
@@ -832,12 +863,17 @@ static void col_pass(Ctx &c, int ps, bool fwd, uint32_t *data, size_t pstride, s
     }
     CAT_LAUNCH(fwd ? "ntt_col_fwd" : "ntt_col_inv");
     prof_end(c, tok, s, bytes);
+    return prescaled;
 }
 
 template <int LR, int PS>
 static void launch_row_t(dim3 grid, cudaStream_t s, const RowArgs &a, bool pre)
 {
-    if (pre) {  // broadcast products, the common transform complete
+    if (a.prescaled && a.mode != PAIR_SQUARE && !pre) {  // operand b carries the scale
+        const size_t smem = ((size_t)2 << kRowMaxLog) * sizeof(uint32_t);
+        set_smem(ntt_row_mul_ns<LR, PS>, smem);
+        ntt_row_mul_ns<LR, PS><<<grid, kRowThreads, smem, s>>>(a);
+    } else if (pre) {  // broadcast products, the common transform complete
         const size_t smem = ((size_t)1 << kRowMaxLog) * sizeof(uint32_t);
         set_smem(ntt_row_mul_bcast<LR, PS>, smem);
         ntt_row_mul_bcast<LR, PS><<<grid, kRowThreads, smem, s>>>(a);
@@ -969,15 +1005,18 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
                                                 : 2;
     const size_t fp = ntf * L;
     DevBuf<uint32_t> F(c, fp * kNumPrimes, s);
-    // forward column passes
+    // forward column passes (operand b's first pass takes the pointwise
+    // step's normalisation into its twiddles when it has a table)
+    bool prescaled = false;
     if (mode == PAIR_FIRST_TWO) {
         col_pass(c, PS, true, F.get(), fp, L, n, P.rcol[0], x.p, 0, x.len, s);
-        col_pass(c, PS, true, F.get() + L, fp, L, n, P.rcol[0], y.p, 0, y.len, s);
+        prescaled = col_pass(c, PS, true, F.get() + L, fp, L, n, P.rcol[0], y.p, 0, y.len, s, 1);
     } else if (mode == PAIR_BROADCAST) {
         col_pass(c, PS, true, F.get(), fp, nprod * L, n, P.rcol[0], x.p, x.tstride, x.len, s);
         col_pass(c, PS, true, F.get() + nprod * L, fp, L, n, P.rcol[0], y.p, 0, y.len, s);
     } else {
-        col_pass(c, PS, true, F.get(), fp, fp, n, P.rcol[0], x.p, x.tstride, x.len, s);
+        prescaled = col_pass(c, PS, true, F.get(), fp, fp, n, P.rcol[0], x.p, x.tstride, x.len, s,
+                             mode == PAIR_ADJACENT ? 2 : 0);
     }
     int m = n - P.rcol[0];
     for (int i = 1; i < P.ncol; i++) {
@@ -994,6 +1033,7 @@ static void ntt_mul_multipass(Ctx &c, int n, int mode, size_t nprod, Operand x, 
     ra.gpstride = gp;
     ra.n = n;
     ra.mode = mode;
+    ra.prescaled = prescaled ? 1 : 0;
     ra.tw = c.twiddles;
     ra.scale = make_scale(PS, n);
     // broadcast products: y's transform completed once, in its slot, so that
@@ -1429,6 +1469,7 @@ static void noalloc_mul(const NoAllocDevice &d, const uint32_t *a, size_t na, co
     ra.gpstride = gp;
     ra.n = n;
     ra.mode = PAIR_FIRST_TWO;
+    ra.prescaled = 0;  // computed twiddles: the row pass normalises
     ra.tw = d.twiddles;
     ra.scale = make_scale(0, n);
     launch_row(0, P.rrow, 1, n, s, ra);

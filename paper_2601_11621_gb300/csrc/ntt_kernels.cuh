@@ -318,6 +318,10 @@ struct ColArgs {
     // form the pass applies, point (row, col) of a 2^m block at row 2^(m-LR) +
     // col, 2^m per prime; null: the pass computes them
     const uint32_t *twtab;
+    // first forward pass of adjacent pairs: the odd transforms' (operand b's)
+    // table, its entries times 2^(32-m) (the pointwise product's 2^-m
+    // normalisation taken in advance), or null
+    const uint32_t *twtab_odd;
 };
 
 // Column tiles hold V adjacent columns per thread group: the group's V
@@ -570,8 +574,9 @@ __global__ void __launch_bounds__(kColFwdThreads, CAT_COL_FWD_MINB) ntt_col_fwd(
     const ColIn<PS, V, ZT> in{base, a.src ? a.src + blk * a.src_tstride : nullptr, (uint32_t)Sr,
                               (uint32_t)col0, (uint32_t)a.src_len, q, c_wp1[PS][p]};
     ColTw<LR, PS, NR, kColFwdThreads, V> tw{T, q, c_qinv[PS][p], set_log_root(PS) - a.m, {}};
-    if (a.twtab) {
-        tw.tab = a.twtab + ((size_t)p << a.m);
+    const uint32_t *tt = ((blk & 1) && a.twtab_odd) ? a.twtab_odd : a.twtab;
+    if (tt) {
+        tw.tab = tt + ((size_t)p << a.m);
         tw.S = (uint32_t)Sr;
     }
     tw.init((uint32_t)col0);
@@ -659,6 +664,7 @@ struct RowArgs {
     size_t gpstride;
     int n;              // log2 L
     int mode;           // which transforms product k multiplies
+    int prescaled;      // operand b's transform already carries 2^(32-n): no scale
     const uint2 *tw;
     Scale scale;
 };
@@ -742,7 +748,7 @@ struct RowOut {
 // products): the common operand's transform is already complete in its slot
 // (ntt_row_fwd), in the order the product loop reads it, so only x is
 // transformed here.
-template <int LR, bool SQ, int PS, bool YH>
+template <int LR, bool SQ, int PS, bool YH, bool NS = false>
 __device__ __forceinline__ void row_mul_body(const RowArgs &a, uint32_t *sm)
 {
     constexpr int NR = rounds_of(LR);
@@ -813,7 +819,8 @@ __device__ __forceinline__ void row_mul_body(const RowArgs &a, uint32_t *sm)
         uint32_t z[1][1 << EL];
 #pragma unroll
         for (int j = 0; j < (1 << EL); j++)
-            z[0][j] = pmul<PS>(x[0][j], YH ? yv[j] : x[NA - 1][j], sc, q, qinv);
+            z[0][j] = NS ? mul_mont<PS>(x[0][j], x[NA - 1][j], q, qinv)
+                         : pmul<PS>(x[0][j], YH ? yv[j] : x[NA - 1][j], sc, q, qinv);
         dit_stages<EL, 0, 1, PS>(z, 0, Ti, q);
         sio.template store<EL, 0, 1>(z, base, c);
     }
@@ -853,6 +860,16 @@ __global__ void __launch_bounds__(kRowThreads, CAT_ROW_MINB) ntt_row_mul(RowArgs
 {
     extern __shared__ uint32_t sm[];
     row_mul_body<LR, SQ, PS, false>(a, sm);
+}
+
+// Products whose operand b transform already carries the normalisation
+// 2^(32-n) (its first pass took the scaled twiddle table): the pointwise
+// product is one Montgomery product.
+template <int LR, int PS>
+__global__ void __launch_bounds__(kRowThreads, CAT_ROW_MINB) ntt_row_mul_ns(RowArgs a)
+{
+    extern __shared__ uint32_t sm[];
+    row_mul_body<LR, false, PS, false, true>(a, sm);
 }
 
 // Broadcast products x_k y whose y transform ntt_row_fwd has completed.
