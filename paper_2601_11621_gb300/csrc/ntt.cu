@@ -520,16 +520,20 @@ constexpr int kFusedThreads = 512;
 
 // The one-block multiply's first forward round input: raw limbs (shared
 // memory, unswizzled) reduced into the forward range; column 0 is operand a,
-// column 1 operand b (a again when squaring).
+// column 1 operand b (a again when squaring).  With sb, operand b's limbs are
+// multiplied by sb (the pointwise step's normalisation 2^(32-n), taken in
+// advance) instead of by 1: the same Shoup product.
 struct RawIn {
     const uint32_t *a, *b;
     uint32_t q, wp1;
+    uint2 sb;  // (multiplier, Shoup companion) for operand b, or (1, wp1)
     template <int E, int B, int NA>
     __device__ __forceinline__ void load(uint32_t (&x)[NA][1 << E], int base, int c) const
     {
         const uint32_t *r = c ? b : a;
+        const uint32_t w = c ? sb.x : 1u, wp = c ? sb.y : wp1;
 #pragma unroll
-        for (int k = 0; k < (1 << E); k++) x[0][k] = reduce_in<0>(r[base + (k << B)], q, wp1);
+        for (int k = 0; k < (1 << E); k++) x[0][k] = shoup(r[base + (k << B)], w, wp, q);
     }
 };
 
@@ -572,22 +576,23 @@ __global__ void __launch_bounds__(kFusedThreads, 2) ntt_mul_fused(FusedArgs a)
         uint32_t *Z = Rr[p];
         if constexpr (NR == 1) {
             // up to 16 points: reduce, transform both, multiply, transform back
+            // operand b (when there is one) takes the normalisation in advance
             for (int i = threadIdx.x; i < L; i += blockDim.x) {
                 X[swz(i)] = reduce_in<0>(rawA[i], q, wp1);
-                Y[swz(i)] = reduce_in<0>(gb ? rawB[i] : rawA[i], q, wp1);
+                Y[swz(i)] = gb ? shoup(rawB[i], sc.x, sc.y, q) : reduce_in<0>(rawA[i], q, wp1);
             }
             __syncthreads();
             dif_smem<LR, 2, 0>(X, T, q);  // X and Y as two arrays
             // elementwise in the swizzled space: Z, X, Y share the permutation
             for (int i = threadIdx.x; i < L; i += blockDim.x)
-                Z[i] = pmul<0>(X[i], Y[i], sc, q, qinv);
+                Z[i] = gb ? mul_mont<0>(X[i], Y[i], q, qinv) : pmul<0>(X[i], Y[i], sc, q, qinv);
             __syncthreads();
             dit_smem<LR, 1, 0>(Z, Ti, q);
         } else {
             // The first forward round reads the raw limbs and reduces them; X and
             // Y are two arrays of the round (twice the groups of one pair).
             const SmemIO<LR, 2, false> xy{X};
-            const RawIn ri{rawA, gb ? rawB : rawA, q, wp1};
+            const RawIn ri{rawA, gb ? rawB : rawA, q, wp1, gb ? sc : make_uint2(1u, wp1)};
             round_io<LR, 2, dif_base(LR, 0), round_size(LR, 0), true, 1, false, 0>(ri, xy, T, q);
             __syncthreads();
             if constexpr (NR == 3) {
@@ -609,7 +614,9 @@ __global__ void __launch_bounds__(kFusedThreads, 2) ntt_mul_fused(FusedArgs a)
                 dif_stages<EL, 0, 2, 0>(x, 0, T, q);
                 uint32_t zz[1][1 << EL];
 #pragma unroll
-                for (int j = 0; j < (1 << EL); j++) zz[0][j] = pmul<0>(x[0][j], x[1][j], sc, q, qinv);
+                for (int j = 0; j < (1 << EL); j++)
+                    zz[0][j] = gb ? mul_mont<0>(x[0][j], x[1][j], q, qinv)
+                                  : pmul<0>(x[0][j], x[1][j], sc, q, qinv);
                 dit_stages<EL, 0, 1, 0>(zz, 0, Ti, q);
                 zs.template store<EL, 0, 1>(zz, base, 0);
             }
