@@ -77,7 +77,7 @@ typedef struct cat_ctx cat_ctx;
  * does not fit.  The context owns the NTT twiddle tables and the scratch pool.
  * A context without a cap also keeps, built on first use, a table of the
  * inter-pass twiddles of every column-pass shape it has run (2^m words per
- * prime for blocks of 2^m points: about 6 GB after C(2,050,572,903)); it is
+ * prime for blocks of 2^m points: about 10 GB after C(2,050,572,903)); it is
  * not scratch (not counted by cat_ctx_memory) and is freed with the context.
  * A capped context computes those twiddles instead.
  * Returns CAT_OK and *out, or an error (CAT_EINVAL, CAT_ECUDA). */

@@ -7,8 +7,10 @@
 //     schoolbook (Comba) kernels finish faster than the transform.
 // Each candidate multiplies a synthetic tree level of 2^24 limbs (one product
 // of 2^n limbs above that; seeded words) and is timed with CUDA events on the
-// context's stream; the fastest wins.  The largest trial holds about 6 GB.  The table is written as text, tagged with the device's name and SM
-// count, and read back by contexts created later on the same kind of device.
+// context's stream; the fastest wins.  The largest trial holds about 6 GB of
+// scratch and 4.5 GB of column twiddle tables (dropped after every trial).
+// The table is written as text, tagged with the device's name and SM count,
+// and read back by contexts created later on the same kind of device.
 #include "cat_internal.cuh"
 
 #include <dlfcn.h>
@@ -99,12 +101,16 @@ void autotune(Ctx &c, cudaStream_t s)
         const int def = default_row(n);
         c.row_log[n] = 0;
         int best = def;
+        // each trial's column twiddle tables (built by its warm-up run) are
+        // dropped after it, so that at most one plan's tables are held
         float best_ms = time_ms(s, [&] { ntt_level(c, in.get(), slot, nprod, out.get(), s); });
+        drop_col_twiddles(c);
         for (int r = 9; r <= 12; r++) {
             if (r == def || !plan_row_ok(n, r)) continue;
             c.row_log[n] = r;
             const float ms =
                 time_ms(s, [&] { ntt_level(c, in.get(), slot, nprod, out.get(), s); });
+            drop_col_twiddles(c);
             if (ms < 0.99f * best_ms) {
                 best = r;
                 best_ms = ms;
@@ -124,7 +130,6 @@ void autotune(Ctx &c, cudaStream_t s)
     }
     c.comba_max_slot = cross;
     c.tuning = "measured";
-    // the trials built twiddle tables for plans that are not kept
     drop_col_twiddles(c);
 }
 
