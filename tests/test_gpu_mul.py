@@ -174,3 +174,22 @@ def test_twiddle_tables_match_computed_twiddles(ctx, computed_twiddle_ctx, cat_l
     assert got.shape == ref.shape and (got == ref).all()
     if na + nb <= 70000:
         assert (got == orc.mul(a, b)).all()
+
+
+@pytest.mark.parametrize("na,nb", [(5001, 4000), (40000, 30001)])
+def test_mul_unaligned_operands(ctx, cat_lib, orc, na, nb):
+    """Operands starting one limb into a buffer (4-byte but not 8-byte
+    aligned) are read word by word; aligned ones two words at a time: both
+    give the oracle's product."""
+    import torch
+    a = W.random_limbs32(na, seed=na + 21)
+    b = W.random_limbs32(nb, seed=nb + 22)
+    want = orc.mul(a, b)
+    ba = torch.zeros(na + 1, dtype=torch.int32, device="cuda")
+    bb = torch.zeros(nb + 1, dtype=torch.int32, device="cuda")
+    ba[1:] = torch.from_numpy(a.view(np.int32)).cuda()
+    bb[1:] = torch.from_numpy(b.view(np.int32)).cuda()
+    got = host(cat_lib.bigint_mul(ctx, ba[1:], bb[1:]))
+    assert got.shape == want.shape and (got == want).all()
+    got = host(cat_lib.bigint_mul(ctx, ba[1:], torch.from_numpy(b.view(np.int32)).cuda()))
+    assert got.shape == want.shape and (got == want).all()
