@@ -14,6 +14,10 @@
     python -m paper_2601_11621_gb300 mul LOG2A [LOG2B] [--repeat K]
         One product of two seeded random operands of 2^LOG2A and 2^LOG2B limbs
         (the product kernels at a chosen size).
+
+    python -m paper_2601_11621_gb300 batch COUNT [--seed S] [--lo A] [--hi B] [--repeat K]
+        COUNT seeded requests (C(n) or C(2n, n), n log-uniform in [A, B]) in one
+        cat_exact_batch call, timed (K times).
 """
 from __future__ import annotations
 
@@ -101,6 +105,20 @@ def cmd_mul(a) -> int:
     return 0
 
 
+def cmd_batch(a) -> int:
+    from . import capi, workloads
+    ctx = capi.Context(0)
+    reqs = workloads.batched_requests(a.count, seed=a.seed, lo=a.lo, hi=a.hi)
+    for _ in range(max(1, a.repeat)):
+        _sync()
+        t = time.perf_counter()
+        out, offs, lens = capi.cat_exact_batch(ctx, reqs)
+        _sync()
+        dt = time.perf_counter() - t
+        print(f"{a.count} requests: {int(lens.sum())} limbs in {dt * 1e3:.2f} ms")
+    return 0
+
+
 def main(argv=None) -> int:
     p = argparse.ArgumentParser(prog="python -m paper_2601_11621_gb300")
     sub = p.add_subparsers(dest="cmd", required=True)
@@ -121,8 +139,14 @@ def main(argv=None) -> int:
     m.add_argument("log2a", type=int)
     m.add_argument("log2b", type=int, nargs="?")
     m.add_argument("--repeat", type=int, default=1)
+    b = sub.add_parser("batch")
+    b.add_argument("count", type=int)
+    b.add_argument("--seed", type=int, default=0)
+    b.add_argument("--lo", type=float, default=1e3)
+    b.add_argument("--hi", type=float, default=1e6)
+    b.add_argument("--repeat", type=int, default=1)
     a = p.parse_args(argv)
-    return {"exact": cmd_exact, "ratio": cmd_ratio, "mul": cmd_mul}[a.cmd](a)
+    return {"exact": cmd_exact, "ratio": cmd_ratio, "mul": cmd_mul, "batch": cmd_batch}[a.cmd](a)
 
 
 if __name__ == "__main__":

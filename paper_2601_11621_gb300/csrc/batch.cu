@@ -276,6 +276,7 @@ void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> 
         size_t slot;
         uint64_t padded, nodes;  // padded multiplying nodes; all nodes of the buffer
         size_t job0, njobs;      // pads and root copies of this level's buffer
+        uint64_t maxcap;         // the longest of them (limbs), which sizes the launch
         uint64_t prod0;          // first product (all levels numbered in turn)
         size_t run0, nruns;      // runs of this level's products
     };
@@ -326,7 +327,7 @@ void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> 
             jobs.push_back(LevelJob{kOne, 0, d, 1, cap});
         }
     for (size_t slot = kBatchLeafSlot;; slot *= 2) {
-        Level lv{slot, padded, nodes, 0, 0, prod, rs.size() - 1, 0};
+        Level lv{slot, padded, nodes, 0, 0, 0, prod, rs.size() - 1, 0};
         lv.job0 = levels.empty() ? 0 : jobs.size();
         for (size_t r = 0; r < count; r++) {
             if (cnt[r] >= 2 && (cnt[r] & 1))
@@ -339,6 +340,7 @@ void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> 
             }
         }
         lv.njobs = jobs.size() - lv.job0;
+        for (size_t j = lv.job0; j < jobs.size(); j++) lv.maxcap = std::max(lv.maxcap, jobs[j].cap);
         if (padded == 0) {
             levels.push_back(lv);
             break;
@@ -396,7 +398,11 @@ void segmented_tree(Ctx &c, const uint32_t *leaves, const std::vector<uint64_t> 
     for (size_t li = 0; li < levels.size(); li++) {
         const Level &lv = levels[li];
         if (lv.njobs) {
-            batch_copy_level<<<dim3(64, (unsigned)std::min<size_t>(lv.njobs, 4096)), 256, 0, s>>>(
+            // blocks per job by the longest job (2,048 limbs a block), jobs
+            // spread over the grid's second dimension
+            const unsigned gx = (unsigned)std::min<uint64_t>(64, (lv.maxcap + 2047) / 2048);
+            batch_copy_level<<<dim3(std::max(1u, gx), (unsigned)std::min<size_t>(lv.njobs, 65535)),
+                               256, 0, s>>>(
                 d_jobs + lv.job0, (int)lv.njobs, cur.get(), cur.get());
             CAT_LAUNCH("batch_copy_level");
         }
