@@ -115,13 +115,14 @@ __global__ void batch_leaves(const uint32_t *primes, const uint64_t *pre, int co
     for (; at < end; at++) leaves[at] = p;
 }
 
-// leaf segment start of every request (flat index pre[r] -> its position)
+// leaf segment start of every request (flat index pre[r] -> its position
+// after the scan; pos[pre[count]] is the total leaf count)
 __global__ void batch_seg_starts(const uint64_t *pre, int count, const uint32_t *pos,
-                                 uint32_t total_leaves, uint64_t *seg)
+                                 uint64_t *seg)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r > count) return;
-    seg[r] = (r < count && pre[r] < pre[count]) ? pos[pre[r]] : total_leaves;
+    seg[r] = (r < count && pre[r] < pre[count]) ? pos[pre[r]] : pos[pre[count]];
 }
 
 // node j of segment r = product of its leaves [lpn j, lpn j + lpn) (missing
@@ -470,25 +471,24 @@ static void batch_core(Ctx &c, const cat_request *reqs, size_t count, uint32_t *
     prof_end(c, tok, s, 8.0 * (double)F);
     // exclusive scan over F + 1 entries: pos[F] becomes the total leaf count
     exclusive_scan_u32(c, pos.get(), F + 1, s);
-    uint32_t total_leaves = 0;
+    // the segment starts (the last one the total leaf count) and the sign
+    // flag in one read-back
+    DevBuf<uint64_t> d_seg(c, count + 1, s);
+    batch_seg_starts<<<(nr + 256) / 256, 256, 0, s>>>(d_pre.get(), nr, pos.get(), d_seg.get());
+    CAT_LAUNCH("batch_seg_starts");
+    std::vector<uint64_t> seg(count + 1);
     unsigned int hneg = 0;
-    CAT_CUDA(cudaMemcpyAsync(&total_leaves, pos.get() + F, 4, cudaMemcpyDeviceToHost, s));
+    CAT_CUDA(cudaMemcpyAsync(seg.data(), d_seg.get(), 8 * (count + 1), cudaMemcpyDeviceToHost, s));
     CAT_CUDA(cudaMemcpyAsync(&hneg, neg.get(), 4, cudaMemcpyDeviceToHost, s));
     CAT_CUDA(cudaStreamSynchronize(s));
     if (hneg) fail(CAT_ENOTINTEGRAL, "a prime exponent is negative");
+    const uint32_t total_leaves = (uint32_t)seg[count];
     DevBuf<uint32_t> leaves(c, total_leaves ? total_leaves : 1, s);
     tok = prof_begin(c, "batch_leaves", s);
     if (F) batch_leaves<<<fb, 256, 0, s>>>(primes.get(), d_pre.get(), nr, pos.get(),
                                            leaves.get());
     CAT_LAUNCH("batch_leaves");
     prof_end(c, tok, s, 8.0 * (double)F + 4.0 * total_leaves);
-    DevBuf<uint64_t> d_seg(c, count + 1, s);
-    batch_seg_starts<<<(nr + 256) / 256, 256, 0, s>>>(d_pre.get(), nr, pos.get(), total_leaves,
-                                                      d_seg.get());
-    CAT_LAUNCH("batch_seg_starts");
-    std::vector<uint64_t> seg(count + 1);
-    CAT_CUDA(cudaMemcpyAsync(seg.data(), d_seg.get(), 8 * (count + 1), cudaMemcpyDeviceToHost, s));
-    CAT_CUDA(cudaStreamSynchronize(s));
     primes.reset();
     pos.reset();
 
