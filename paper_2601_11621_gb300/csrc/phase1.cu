@@ -127,25 +127,31 @@ __global__ void __launch_bounds__(kSieveThreads) sieve_segments(SieveArgs a)
         bm[w] = m;
     }
     __syncthreads();
-    const uint64_t lo_num = 2ull * ibase + 1;  // smallest odd number here
+    // smallest odd number here (below the limit, so below 2^32)
+    const uint32_t lo_num = 2u * ibase + 1u;
+    const uint32_t ubits = (uint32_t)used_bits;
+    // bit index of the first odd multiple of p at or above max(lo_num, p^2),
+    // or ubits when there is none in this segment (32-bit remainder: lo_num
+    // and p < 2^16 fit 32 bits; the sums in 64 bits)
+    auto first_bit = [&](uint32_t p) -> uint32_t {
+        const uint32_t r = lo_num % p;
+        uint64_t x0 = (uint64_t)lo_num + (r ? p - r : 0u);
+        if (x0 < (uint64_t)p * p) x0 = (uint64_t)p * p;
+        if (!(x0 & 1)) x0 += p;
+        const uint64_t f = (x0 - 1) / 2 - ibase;
+        return f < ubits ? (uint32_t)f : ubits;
+    };
     // medium primes: one warp per prime, one multiple per lane
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (uint32_t j = a.i_med + wid; j < a.i_large; j += nw) {
-        const uint64_t p = a.seeds[j];
-        uint64_t x0 = (lo_num + p - 1) / p * p;
-        if (x0 < p * p) x0 = p * p;
-        if (!(x0 & 1)) x0 += p;
-        const uint64_t first = (x0 - 1) / 2 - ibase;
-        for (uint64_t i = first + (uint64_t)lane * p; i < used_bits; i += 32 * p)
+        const uint32_t p = a.seeds[j];
+        for (uint32_t i = first_bit(p) + (uint32_t)lane * p; i < ubits; i += 32 * p)
             atomicOr(&bm[i >> 5], 1u << (i & 31));
     }
     // large primes: one thread per prime
     for (uint32_t j = a.i_large + threadIdx.x; j < a.nseeds; j += blockDim.x) {
-        const uint64_t p = a.seeds[j];
-        uint64_t x0 = (lo_num + p - 1) / p * p;
-        if (x0 < p * p) x0 = p * p;
-        if (!(x0 & 1)) x0 += p;
-        for (uint64_t i = (x0 - 1) / 2 - ibase; i < used_bits; i += p)
+        const uint32_t p = a.seeds[j];
+        for (uint32_t i = first_bit(p); i < ubits; i += p)
             atomicOr(&bm[i >> 5], 1u << (i & 31));
     }
     __syncthreads();
