@@ -113,16 +113,22 @@ __global__ void __launch_bounds__(kSieveThreads) sieve_segments(SieveArgs a)
     const uint64_t used_bits = 32ull * used;
     // primes 3..31: bit b of word w is odd number x = 2(ibase + 32 w + b) + 1;
     // p | x  <=>  ibase + 32 w + b = (p - 1)/2 (mod p)
+    // (the primes are compile-time constants, so i0 mod p is a multiply and a
+    // shift; the word's bits b0, b0 + p, ... are one shift of the pattern
+    // of p's multiples below 64)
+    constexpr uint32_t kSmall[10] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
     for (int w = threadIdx.x; w < (int)used; w += blockDim.x) {
         const uint32_t i0 = ibase + 32u * w;
         uint32_t m = 0;
 #pragma unroll
         for (int k = 0; k < 10; k++) {
-            const uint32_t p = c_small_primes[k];
-            const uint32_t b0 = ((p - 1) / 2 + p - i0 % p) % p;
-            uint64_t pat = 0;
-            for (uint32_t b = b0; b < 32; b += p) pat |= 1ull << b;
-            m |= (uint32_t)pat;
+            const uint32_t p = kSmall[k];
+            uint64_t multiples = 0;
+            for (uint32_t b = 0; b < 64; b += p) multiples |= 1ull << b;
+            const uint32_t r = i0 % p;
+            uint32_t b0 = (p - 1) / 2 + p - r;  // in (0, 2p)
+            if (b0 >= p) b0 -= p;
+            m |= (uint32_t)(multiples << b0);
         }
         bm[w] = m;
     }
