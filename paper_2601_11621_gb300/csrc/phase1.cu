@@ -180,13 +180,23 @@ __global__ void __launch_bounds__(kSieveThreads) sieve_segments(SieveArgs a)
         else if (i0 + 31 > a.imax) v &= (uint32_t)((2ull << (a.imax - i0)) - 1);
         if (a.unit_kind >= 0) {
             all += __popc(v);
-            uint32_t keep = 0;
-            for (uint32_t m = v; m; m &= m - 1) {
-                const int b = __ffs(m) - 1;
-                const uint32_t p = (uint32_t)(2 * (i0 + b) + 1);
-                if (p > a.root && unit_exponent(p, a.unit_n, a.unit_kind)) keep |= 1u << b;
+            if (2 * i0 + 1 > a.unit_n) {
+                // every number of the word is above n (so above root): a prime
+                // p in (n, 2n] has e_p = 1 (floor(2n/p) = 1, floor(n/p) = 0),
+                // except p = n + 1 for C(n), which divides n + 1
+                if (a.unit_kind == CAT_CATALAN && ((a.unit_n + 1) & 1)) {
+                    const uint64_t j = (uint64_t)a.unit_n / 2;  // odd index of n + 1
+                    if (j >= i0 && j < i0 + 32) v &= ~(1u << (j - i0));
+                }
+            } else {
+                uint32_t keep = 0;
+                for (uint32_t m = v; m; m &= m - 1) {
+                    const int b = __ffs(m) - 1;
+                    const uint32_t p = (uint32_t)(2 * (i0 + b) + 1);
+                    if (p > a.root && unit_exponent(p, a.unit_n, a.unit_kind)) keep |= 1u << b;
+                }
+                v = keep;
             }
-            v = keep;
         }
         out[w] = v;
         cnt += __popc(v);
