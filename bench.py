@@ -528,11 +528,13 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = capi.cat_launch_count()
     ev0.record(stream)
     for _ in range(args.steps):
         capi.catalan_exact(ctx, n, out=out)
     ev1.record(stream)
     torch.cuda.synchronize()
+    timed_launches = capi.cat_launch_count() - launches0
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
@@ -628,7 +630,7 @@ def main():
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(4 * hres.size)},
-            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "gpu_launches": int(timed_launches),
             "autotune": tuning,
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -116,6 +116,11 @@ int cat_ctx_tuning(const cat_ctx *ctx, size_t *comba_max_slot, int *row_log, siz
 /* Bytes of scratch currently held / the high-water mark since creation. */
 int cat_ctx_memory(const cat_ctx *ctx, size_t *in_use, size_t *peak);
 
+/* The number of kernels this library has launched in this process, over all
+ * contexts and threads, each counted when it is issued (a measurement aid:
+ * the difference across a call is that call's launches). */
+unsigned long long cat_launch_count(void);
+
 /* Per-kernel device timing (tracing aid, not part of the method).  When on,
  * every kernel launch is bracketed by CUDA events on its stream; each entry
  * point resolves them before returning.  Turning it on or off clears the

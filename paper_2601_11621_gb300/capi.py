@@ -27,6 +27,7 @@ CAT_OK, CAT_EINVAL, CAT_ENOMEM, CAT_ERANGE = 0, -1, -2, -3
 CAT_ENOTINTEGRAL, CAT_ETIMEOUT, CAT_ECUDA, CAT_EBUSY = -4, -5, -6, -7
 
 EXPORTED = ["cat_ctx_create", "cat_ctx_destroy", "cat_last_error", "cat_ctx_memory",
+            "cat_launch_count",
             "cat_autotune", "cat_ctx_load_tuning", "cat_ctx_tuning",
             "cat_ctx_set_profiling", "cat_ctx_profile",
             "catalan_factor", "cat_factor_free", "cat_factor_copy_primes", "bigint_mul",
@@ -94,6 +95,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.cat_ctx_tuning.restype = i32
     L.cat_ctx_memory.argtypes = [vp, szp, szp]
     L.cat_ctx_memory.restype = i32
+    L.cat_launch_count.argtypes = []
+    L.cat_launch_count.restype = ctypes.c_ulonglong
     L.cat_ctx_set_profiling.argtypes = [vp, i32]
     L.cat_ctx_set_profiling.restype = i32
     L.cat_ctx_profile.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_char_p),
@@ -266,6 +269,11 @@ def _limbs_tensor(x, device):
 def _empty(n, device):
     import torch
     return torch.empty(max(n, 1), dtype=torch.int32, device=device)
+
+
+def cat_launch_count() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(load().cat_launch_count())
 
 
 def cat_bound_limbs(n: int, kind: int = CAT_CATALAN) -> int:

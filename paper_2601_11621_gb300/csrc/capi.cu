@@ -151,6 +151,8 @@ int cat_ctx_memory(const cat_ctx *ctx, size_t *in_use, size_t *peak)
     return CAT_OK;
 }
 
+unsigned long long cat_launch_count(void) { return cat::launch_count(); }
+
 int cat_ctx_set_profiling(cat_ctx *ctx, int on)
 {
     if (!ctx) return CAT_EINVAL;

@@ -29,8 +29,10 @@ struct Error {
 
 [[noreturn]] void fail(int code, const std::string &msg);
 void check_cuda(cudaError_t e, const char *what);
+// after every kernel launch: counts it (cat_launch_count) and checks it
+void launched(const char *what);
 #define CAT_CUDA(call) ::cat::check_cuda((call), #call)
-#define CAT_LAUNCH(what) ::cat::check_cuda(cudaGetLastError(), what)
+#define CAT_LAUNCH(what) ::cat::launched(what)
 
 // ------------------------------------------------------------- constants
 
@@ -631,6 +633,9 @@ void copy_to_host(Ctx &c, uint32_t *host, const uint32_t *dev, size_t n, cudaStr
 // Algorithm 2 on a factorisation; returns the result (normalised length).
 // Every prime of f is below 2^leaf_bits (32 when nothing smaller is known).
 Big reconstruct(Ctx &c, const cat_factorization *f, cudaStream_t s, int leaf_bits = 32);
+// Kernels launched by the library so far (every CAT_LAUNCH).
+unsigned long long launch_count();
+
 // Frees the context's column-pass twiddle tables.
 void drop_col_twiddles(Ctx &c);
 

@@ -22,6 +22,17 @@ void check_cuda(cudaError_t e, const char *what)
     }
 }
 
+// kernels launched by this library in this process
+static std::atomic<unsigned long long> g_launches{0};
+
+void launched(const char *what)
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    check_cuda(cudaGetLastError(), what);
+}
+
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 // ------------------------------------------------------------------ memory
 
 namespace {

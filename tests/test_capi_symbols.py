@@ -14,8 +14,8 @@ HEADER = os.path.join(ROOT, "include", "catalan.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:int|void|size_t|const\s+char\s*\*)\s*\*?\s*(\w+)\s*\(", text,
-                       flags=re.M)
+    names = re.findall(r"^\s*(?:int|void|size_t|unsigned\s+long\s+long|const\s+char\s*\*)"
+                       r"\s*\*?\s*(\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 

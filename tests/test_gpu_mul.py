@@ -193,3 +193,17 @@ def test_mul_unaligned_operands(ctx, cat_lib, orc, na, nb):
     assert got.shape == want.shape and (got == want).all()
     got = host(cat_lib.bigint_mul(ctx, ba[1:], torch.from_numpy(b.view(np.int32)).cuda()))
     assert got.shape == want.shape and (got == want).all()
+
+
+def test_launch_count_grows_with_work(ctx, cat_lib):
+    """cat_launch_count counts the library's kernel launches: a multi-pass
+    product launches several kernels, a call that fails its argument check
+    launches none."""
+    a = W.random_limbs32(20000, seed=31)
+    n0 = cat_lib.cat_launch_count()
+    cat_lib.bigint_mul(ctx, a, a)
+    n1 = cat_lib.cat_launch_count()
+    assert n1 - n0 >= 5
+    with pytest.raises(cat_lib.CatError):
+        cat_lib.cat_exact_batch(ctx, [(5, 10)])  # unknown kind
+    assert cat_lib.cat_launch_count() == n1
